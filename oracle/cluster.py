@@ -80,11 +80,10 @@ def build_tree(xyz, tri, n_min: int = 32) -> ClusterTree:
         nl = int(np.count_nonzero(left))
         if nl == 0 or nl == n:
             order = np.lexsort((idx, cen[idx, axis]))
-            new = idx[order]
             nl = n // 2
-            perm[begin:end] = np.concatenate([new[:nl], new[nl:]])
-        else:
-            perm[begin:end] = np.concatenate([idx[left], idx[~left]])
+            left = np.zeros(n, dtype=bool)
+            left[order[:nl]] = True
+        perm[begin:end] = np.concatenate([idx[left], idx[~left]])
         a = rec(begin, begin + nl, level + 1, me)
         b = rec(begin + nl, end, level + 1, me)
         nodes[me][6] = [a, b]
