@@ -10,7 +10,9 @@ specified for the CUDA path):
   edge, 1 -> common vertex (Sauter-Schwab, g_sing^4 points per region);
 * a pair with no shared vertex is near-singular when the distance of the
   centroids is below near_ratio * max(longest edge of tau_i, of tau_j): the
-  collapsed Gauss rule with g_near^2 points on each triangle;
+  collapsed Gauss rule with g_near^2 points on each triangle (centroids as
+  ((P0 + P1) + P2) / 3, lengths as sqrt((x^2 + y^2) + z^2), so that the
+  decision is reproducible bit for bit);
 * otherwise regular: Radon's 7-point rule on each triangle (49 points).
 Vertex order used by the singular rules (pair i = test, j = trial):
 * identical: the stored order (v0, v1, v2) on both sides;
@@ -45,11 +47,16 @@ def element_geometry(xyz, tri):
     cr = np.cross(e01, e02)
     area = 0.5 * np.sqrt(np.sum(cr * cr, axis=1))
     cen = (P[:, 0] + P[:, 1] + P[:, 2]) / 3.0
-    l0 = np.linalg.norm(P[:, 1] - P[:, 0], axis=1)
-    l1 = np.linalg.norm(P[:, 2] - P[:, 1], axis=1)
-    l2 = np.linalg.norm(P[:, 0] - P[:, 2], axis=1)
+    l0 = _length(P[:, 1] - P[:, 0])
+    l1 = _length(P[:, 2] - P[:, 1])
+    l2 = _length(P[:, 0] - P[:, 2])
     diam = np.maximum(np.maximum(l0, l1), l2)
     return P, area, cen, diam
+
+
+def _length(d):
+    """Euclidean length with the sum formed as ((x^2 + y^2) + z^2)."""
+    return np.sqrt((d[..., 0] * d[..., 0] + d[..., 1] * d[..., 1]) + d[..., 2] * d[..., 2])
 
 
 def classify(tri, I, J, cen, diam, qp: QuadParams):
@@ -62,7 +69,7 @@ def classify(tri, I, J, cen, diam, qp: QuadParams):
         for b in range(3):
             shared += (A[:, a] == B[:, b])
     case = np.zeros(len(I), dtype=np.int64)
-    d = np.linalg.norm(cen[I] - cen[J], axis=1)
+    d = _length(cen[I] - cen[J])
     near = d < qp.near_ratio * np.maximum(diam[I], diam[J])
     case[(shared == 0) & near] = 1
     case[shared == 1] = 2
