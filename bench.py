@@ -1,0 +1,353 @@
+#!/usr/bin/env python
+"""Throughput of the compressed CQM-BEM single-layer solve on GB300.
+
+Metric: triangle * frequency / s (M * L per step, L = N + 1 CQM frequencies)
+of one full pass of the hot path -- geometry, cluster tree, partition,
+Chebyshev bases, MACA of every block, plane-wave data, forward R-scaled DFT,
+batched GMRES over the solved frequencies, inverse DFT -- on the 5120-triangle
+unit sphere, BDF2, N = 256, dt = 0.1, eta = 1, m = 4, leaf 32, MACA tolerance
+1e-6, FP64.  Synthetic input: seeded icosphere and Gaussian plane-wave pulse.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs one independent replica per GPU (the method does not shard across
+GPUs here); value = all ranks' units / max over ranks of the timed region.
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload on the host cores (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(name="sphere5120_N256", level=4, N=256, dt=0.1, bdf=2, eta=1.0, cheb_m=4,
+                n_min=32, aca_eps=1e-6)
+METRIC = "CQM-BEM solve throughput (triangle·freq/s), p50/p99 latency at rel err ≤1e-6"
+UNIT = "triangle*freq/s"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# FP64 peak of a GB300 (recipe's nominal dense FP64 rate, TFLOP/s); the FP64
+# FMA probe measured 1.19 TFLOP/s on this machine.
+FP64_PEAK_TFLOPS = 1.25
+
+
+def dist_init(ngpus):
+    import torch
+    import torch.distributed as dist
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    return rank, world
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    """Max of a host float over the ranks (NCCL on GPUs, gloo on CPU)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(units_per_step, steps, my_seconds, world):
+    """Whole-job throughput: units of all ranks / max over ranks of the timed region."""
+    tmax = max_over_ranks(my_seconds, world)
+    return world * units_per_step * steps / tmax, tmax
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def algorithmic_flops(info, Ls, p):
+    """FP64 flops of one far-field coupling launch: 8 per complex multiply-add,
+    sum over far blocks of rank * p^2 * Ls."""
+    return 8.0 * info["rank_sum_far"] * p * p * Ls
+
+
+def run_ours(args):
+    import torch
+    from paper_2006_05186_gb300 import CqmBem, synth
+    rank, world = dist_init(args.gpus)
+    W = WORKLOAD
+    m = synth.icosphere(W["level"])
+    pulse = synth.plane_wave_pulse(seed=synth.SEED_BASE + rank)
+    N, dt = W["N"], W["dt"]
+    L = N + 1
+    Ls = L // 2 + 1
+    M = m.nt
+    params = dict(mode="h2maca", eta=W["eta"], cheb_m=W["cheb_m"], n_min=W["n_min"],
+                  aca_eps=W["aca_eps"], profile=1)
+    stream = torch.cuda.current_stream()
+    rhs = torch.empty((L, M), dtype=torch.float64, device="cuda")
+    q = torch.empty((L, M), dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def step():
+        op = CqmBem(m.xyz, m.tri, dt, N, W["bdf"], **params)
+        op.rhs_plane_wave(pulse.direction, pulse.width, pulse.delay, out=rhs)
+        op.solve(rhs, out=q)
+        return op
+
+    for _ in range(args.warmup):
+        step().close()
+    torch.cuda.synchronize()
+    barrier(world)
+    times, prof, infos, sinfos = [], {}, [], []
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            op = step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1) / 1e3)
+            for k, (n, ms) in op.profile_read().items():
+                a = prof.setdefault(k, [0, 0.0])
+                a[0] += n
+                a[1] += ms
+            infos.append(op.info())
+            sinfos.append(op.last_solve_info)
+            op.close()
+    torch.cuda.synchronize()
+    barrier(world)
+    total = sum(times)
+    value, tmax = whole_job_value(M * L, args.steps, total, world)
+
+    # end to end through the public API with host buffers
+    rhs_host = torch.empty((L, M), dtype=torch.float64, pin_memory=True)
+    rhs_host.copy_(rhs.cpu())
+    q_host = torch.empty((L, M), dtype=torch.float64, pin_memory=True)
+    e2e_times = []
+    barrier(world)
+    for _ in range(max(1, args.steps)):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        op = CqmBem(m.xyz, m.tri, dt, N, W["bdf"], **params)
+        op.solve(rhs_host.numpy(), out=q_host.numpy())
+        op.close()
+        torch.cuda.synchronize()
+        e2e_times.append(time.perf_counter() - t0)
+    e2e_value, _ = whole_job_value(M * L, len(e2e_times), sum(e2e_times), world)
+
+    if rank != 0:
+        return
+    peaks, src = _peaks()
+    inf = infos[-1]
+    dom = max(prof.items(), key=lambda kv: kv[1][1])
+    p = W["cheb_m"] ** 3
+    fc_launches, fc_ms = prof.get("far_coupling", (0, 0.0))
+    fc_flops = algorithmic_flops(inf, Ls, p)
+    achieved = fc_flops / (fc_ms / fc_launches / 1e3) / 1e12 if fc_launches else None
+    lat = sorted(times)
+    clocks = clk.summary()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": W["name"], "triangles": M, "N": N, "L": L, "Ls": Ls, "dt": dt,
+                   "bdf": 2, "eta": W["eta"], "cheb_m": W["cheb_m"], "leaf": W["n_min"],
+                   "aca_eps": W["aca_eps"], "mode": "h2maca", "parallelism": f"replicas{world}",
+                   "l2": "256 MB buffer written between timed steps; working set "
+                         f"{inf['device_bytes'] / 2**30:.1f} GiB > L2"},
+        "latency_ms": {"p50": 1e3 * lat[len(lat) // 2],
+                       "p99": 1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))]},
+        "accuracy": {"gmres_max_rel_residual": max(s["max_rel_residual"] for s in sinfos),
+                     "converged_frequencies": min(s["converged"] for s in sinfos), "Ls": Ls},
+        "roofline": {"bound": "alu", "kernel": "far_coupling (FP64 complex MAC)",
+                     "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None,
+                     "traffic": None, "peak_source": "recipe nominal FP64"},
+        "dominant_kernel": {"name": dom[0], "launches": dom[1][0], "ms": dom[1][1]},
+        "kernel_ms": {k: round(v[1], 3) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1]) if v[0]},
+        "gpu_launches": int(sum(v[0] for v in prof.values())),
+        "setup": {k: inf[k] for k in ("n_nodes", "n_near", "n_far", "rank_sum_near", "rank_sum_far",
+                                      "rank_max", "t_tree_ms", "t_bases_ms", "t_assembly_ms")},
+        "solve": {k: sinfos[-1][k] for k in ("iterations", "restarts", "t_gmres_ms")},
+        "clocks": clocks,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(L * M * 8 + m.xyz.nbytes + m.tri.nbytes),
+                "d2h_bytes_per_step": int(L * M * 8)},
+        "peaks_source": src,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(max_seconds=args.cpu_seconds)
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(max_seconds=20.0):
+    """The FP64 oracle as it stands on a bounded sample of the same workload:
+    H^2-expanded Galerkin assembly of a random sample of the near-field pairs
+    and of the far blocks at one frequency, plus one dense LU solve, scaled to
+    all pairs and all solved frequencies."""
+    from oracle import cluster, cqm, galerkin as G, h2
+    from paper_2006_05186_gb300 import synth
+    W = WORKLOAD
+    m = synth.icosphere(W["level"])
+    M = m.nt
+    N = W["N"]
+    L = N + 1
+    Ls = L // 2 + 1
+    t = cluster.build_tree(m.xyz, m.tri, W["n_min"])
+    near, far = cluster.partition(t, W["eta"])
+    s = cqm.frequencies(N, W["dt"], 2)[[Ls // 2]]
+    sizes = t.end - t.begin
+    n_pairs = int(sum(sizes[r] * sizes[c] for r, c in near))
+    rng = np.random.default_rng(0)
+    I, J = [], []
+    for r, c in near:
+        a, b = np.meshgrid(t.indices(r), t.indices(c), indexing="ij")
+        I.append(a.ravel())
+        J.append(b.ravel())
+    I = np.concatenate(I)
+    J = np.concatenate(J)
+    budget = max_seconds / 3
+    k = 2048
+    t0 = time.perf_counter()
+    sel = rng.choice(n_pairs, k, replace=False)
+    G.pair_entries(m.xyz, m.tri, I[sel], J[sel], s)
+    t_near = (time.perf_counter() - t0) * n_pairs / k
+    fb = far[rng.choice(len(far), 64, replace=False)]
+    t0 = time.perf_counter()
+    cache = {}
+    for r, c in fb:
+        S = h2.coupling(t, r, c, s, W["cheb_m"])
+        for x in (r, c):
+            if x not in cache:
+                cache[x] = h2.cluster_basis(m.xyz, m.tri, t, x, W["cheb_m"])
+        np.einsum("im,lmn,jn->lij", cache[r], S, cache[c])
+    t_far = (time.perf_counter() - t0) * len(far) / len(fb)
+    A = rng.standard_normal((M, M)) + 1j * rng.standard_normal((M, M))
+    bvec = rng.standard_normal(M) + 0j
+    t0 = time.perf_counter()
+    np.linalg.solve(A, bvec)
+    t_lu = time.perf_counter() - t0
+    per_freq = t_near + t_far + t_lu
+    est = Ls * per_freq
+    return {"value": M * L / est, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": (f"one frequency of the {W['name']} workload: {k} of {n_pairs} near-field "
+                       f"pairs and 64 of {len(far)} far blocks (H^2-expanded assembly) plus one "
+                       f"{M}x{M} LU; scaled to all pairs and {Ls} solved frequencies; est. "
+                       f"{est:.0f} s per job")}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    times = []
+    cb = None
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        cb = cpu_baseline(max_seconds=args.cpu_seconds)
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    W = WORKLOAD
+    M = 20 * 4 ** W["level"]
+    L = W["N"] + 1
+    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT,
+            "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sum(times) / max(1, len(times)), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": W["name"], "triangles": M, "N": W["N"], "L": L,
+                       "mode": "oracle H^2-expanded + LU (sampled)"},
+            "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,258 @@
+/*
+ * cqm_bem.h -- C ABI of libcqmbem, a GB300 (sm_103a) implementation of the
+ * frequency-domain convolution-quadrature boundary element method for the
+ * acoustic single layer.
+ *
+ * The method (D. Seibel, "Boundary Element Methods for the Wave Equation based
+ * on Hierarchical Matrices and Adaptive Cross Approximation"):
+ *   - CQM frequencies s_l = chi(R zeta^l) / dt, zeta = exp(2 pi i / L),
+ *     L = N + 1 (Sec. 3.1, eq. cqm_freq);
+ *   - per frequency, the P0 Galerkin single layer
+ *     V_l[i,j] = int_{tau_i} int_{tau_j} exp(-s_l |x-y|) / (4 pi |x-y|)
+ *     (Sec. 3.2, eq. fundsol);
+ *   - optionally compressed as an H^2 matrix with Chebyshev interpolation
+ *     (Sec. 4, Alg. 1) and, block by block, in frequency by multivariate
+ *     adaptive cross approximation (Sec. 5.1, Alg. 2; Alg. 3, eq. lrfinal);
+ *   - the decoupled solve of the Remark in Sec. 6.2: transform the data to
+ *     the frequencies, solve V_l qhat_l = ghat_l for every l (GMRES on the
+ *     GPU), transform back with the R-scaled inverse DFT (eq. omega_n).
+ *
+ * Conventions shared by every call:
+ *   - All arrays are plain pointers.  Arrays that cross the boundary as
+ *     complex numbers are interleaved (re, im) float64 pairs.
+ *   - Where a call takes `mem`, CQM_MEM_HOST means the pointers are host
+ *     memory (pinned or pageable) and CQM_MEM_DEVICE means device memory of
+ *     the handle's device.  Host buffers are copied inside the call.
+ *   - The caller owns every buffer it passes; the handle owns all device
+ *     state it allocates (geometry, tree, bases, compressed blocks, solver
+ *     workspace) and frees it in cqm_bem_destroy.
+ *   - Calls on one handle must not run concurrently (a handle is bound to
+ *     one CUDA stream).  Different handles are independent.
+ *   - Every call returns a status code; nothing aborts, exits or traps.
+ *     cqm_bem_strerror() names a code; cqm_bem_last_error() gives the
+ *     detail message of the most recent failure on the calling thread.
+ *   - Calls that return host data synchronise the handle's stream.
+ */
+#ifndef CQM_BEM_H
+#define CQM_BEM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define CQM_OK        0
+#define CQM_EINVAL    1   /* bad argument: N < 1, dt <= 0, bdf not 1/2, bad indices, degenerate triangle, NULL */
+#define CQM_ENOMEM    2   /* device allocation failed (HBM admission) */
+#define CQM_ENOCONV   3   /* GMRES reached its iteration cap; outputs and info are still written */
+#define CQM_ETIMEOUT  4   /* a bounded device wait gave up */
+#define CQM_ECUDA     5   /* a CUDA runtime error; see cqm_bem_last_error() */
+#define CQM_ECAPACITY 6   /* a fixed device capacity (rank slots, block lists) was exceeded */
+
+/* Operator representations. */
+#define CQM_MODE_DENSE  0 /* dense V_l for every solved frequency (Sec. 3.2) */
+#define CQM_MODE_H2MACA 1 /* near field + H^2 far field, both MACA-compressed in frequency (eq. lrfinal) */
+
+/* Memory kinds of caller buffers. */
+#define CQM_MEM_HOST   0
+#define CQM_MEM_DEVICE 1
+
+/* Surface mesh: nv vertices (xyz, nv x 3, float64) and nt flat triangles
+ * (tri, nt x 3, int32 vertex indices, outward counter-clockwise).  Copied at
+ * setup; the caller's arrays may be freed afterwards. */
+typedef struct cqm_mesh {
+  int32_t nv;
+  const double* xyz;
+  int32_t nt;
+  const int32_t* tri;
+} cqm_mesh;
+
+/* Optional device allocator.  alloc returns device memory of at least `bytes`
+ * bytes usable on `stream` (NULL on failure); free releases it.  When absent,
+ * the library uses cudaMallocAsync / cudaFreeAsync on the handle's stream. */
+typedef struct cqm_allocator {
+  void* ctx;
+  void* (*alloc)(size_t bytes, void* stream, void* ctx);
+  void (*free)(void* ptr, size_t bytes, void* stream, void* ctx);
+} cqm_allocator;
+
+/* Parameters (cqm_params_default fills the values in brackets). */
+typedef struct cqm_params {
+  int32_t mode;           /* CQM_MODE_*                                   [CQM_MODE_H2MACA] */
+  double R;               /* CQM radius; <= 0 means (1e-10)^(1/(2L))      [0]   */
+  int32_t g_sing;         /* Gauss points per direction, singular pairs    [5]   */
+  int32_t g_near;         /* Gauss points per direction, near-singular     [5]   */
+  double near_ratio;      /* near-singular iff centroid distance < ratio * max longest edge [2.0] */
+  int32_t n_min;          /* cluster leaf size                             [32]  */
+  double eta;             /* admissibility parameter (eq. qadm)            [1.0] */
+  int32_t cheb_m;         /* Chebyshev points per axis, p = m^3 (m <= 4)   [4]   */
+  double aca_eps;         /* MACA stopping tolerance (Alg. 2)              [1e-6] */
+  int32_t rank_cap;       /* rank slots reserved per block                 [32]  */
+  int32_t gmres_restart;  /* Krylov dimension per cycle                    [50]  */
+  int32_t gmres_max_iter; /* total Arnoldi steps cap                       [3000] */
+  double gmres_tol;       /* relative residual target ||r_l|| <= tol ||ghat_l|| [1e-13] */
+  int32_t profile;        /* nonzero: time every kernel launch with CUDA events [0] */
+  const cqm_allocator* allocator; /* NULL: stream-ordered CUDA pool        [NULL] */
+} cqm_params;
+
+/* Setup product summary. */
+typedef struct cqm_setup_info {
+  int32_t nt, nv, N, L, Ls;     /* triangles, vertices, steps, frequencies, solved frequencies */
+  int32_t mode;
+  int32_t n_nodes, n_leaves;    /* cluster tree (0 in dense mode) */
+  int32_t n_near, n_far;        /* blocks of the partition (0 in dense mode) */
+  int64_t near_entries;         /* sum #r #c over near blocks */
+  int64_t far_coupling;         /* sum p^2 over far blocks */
+  int64_t rank_sum_near, rank_sum_far;
+  int32_t rank_max;
+  double R;
+  int64_t device_bytes;         /* device memory held by the handle */
+  double t_geometry_ms, t_tree_ms, t_bases_ms, t_assembly_ms; /* stage times (CUDA events) */
+} cqm_setup_info;
+
+/* Per-solve summary. */
+typedef struct cqm_solve_info {
+  int32_t iterations;           /* Arnoldi steps taken (lockstep over frequencies) */
+  int32_t restarts;
+  int32_t converged;            /* frequencies meeting gmres_tol */
+  int32_t Ls;
+  double max_rel_residual;      /* max_l ||ghat_l - V_l qhat_l|| / ||ghat_l|| (true residual, FP64) */
+  double max_imag;              /* max |Im q_n[i]| before taking the real part */
+  double t_forward_ms, t_gmres_ms, t_inverse_ms;
+} cqm_solve_info;
+
+typedef struct cqm_handle cqm_handle;
+
+/* Fill `p` with the defaults above.  Returns CQM_EINVAL for p == NULL. */
+int cqm_params_default(cqm_params* p);
+
+/* Build the operator for a mesh (Alg. 3: cluster, cluster bases, partition,
+ * MACA per block -- or the dense V_l in CQM_MODE_DENSE).
+ * dt > 0 time step, N >= 1 steps (L = N + 1 frequencies), bdf_order 1 or 2
+ * (chi of BDF-k: sum_{j=1..k} (1 - z)^j / j).  cuda_stream is a cudaStream_t
+ * (NULL: the legacy default stream).  On success *out owns the device state.
+ * Errors: CQM_EINVAL (arguments, mesh indices, zero-area triangles),
+ * CQM_ENOMEM, CQM_ECAPACITY (rank_cap exceeded), CQM_ECUDA. */
+int cqm_bem_setup(const cqm_mesh* mesh, double dt, int32_t N, int32_t bdf_order,
+                  const cqm_params* params, void* cuda_stream, cqm_handle** out);
+
+/* Solve for the time-step densities.
+ * rhs:     (N+1) x nt float64, row n = b_n[i] = int_{tau_i} u_inc(x, t_n) dS
+ *          (Galerkin data of V q = u_inc).
+ * density: (N+1) x nt float64, row n = q_n.
+ * Both in `mem` memory.  info may be NULL.  Steps: forward R-scaled DFT,
+ * batched GMRES over the floor(L/2)+1 solved frequencies (conjugate symmetry
+ * gives the rest), inverse R-scaled DFT (eq. omega_n).
+ * Errors: CQM_EINVAL, CQM_ENOCONV (results still written), CQM_ECUDA. */
+int cqm_bem_solve(cqm_handle* h, const double* rhs, double* density, int32_t mem,
+                  cqm_solve_info* info);
+
+/* Galerkin data of the plane-wave pulse u(x,t) = exp(-((t - delay - d.x)/width)^2)
+ * at t_n = n dt, n = 0..N, with Radon's 7-point rule per triangle.
+ * dir: 3 doubles (host, normalised inside).  rhs: (N+1) x nt float64 in `mem`. */
+int cqm_bem_rhs_plane_wave(cqm_handle* h, const double dir[3], double width, double delay,
+                           double* rhs, int32_t mem);
+
+/* Release everything the handle owns.  NULL is accepted. */
+int cqm_bem_destroy(cqm_handle* h);
+
+/* Static description of a status code. */
+const char* cqm_bem_strerror(int status);
+
+/* Detail of the last failure on this thread ("" if none). */
+const char* cqm_bem_last_error(void);
+
+/* ---- Inspection calls (host outputs; used to check each step) ---------- */
+
+/* Summary of the setup product. */
+int cqm_bem_get_info(const cqm_handle* h, cqm_setup_info* out);
+
+/* The L frequencies s_l (eq. cqm_freq): out = 2 L doubles (re, im). */
+int cqm_bem_get_frequencies(const cqm_handle* h, double* out);
+
+/* Cluster tree (Def. 2), nodes numbered breadth-first.  Any output may be
+ * NULL.  perm: nt int32 (triangle at each position); begin/end/son0/son1/level:
+ * n_nodes int32 (son = -1 for leaves); lo/hi: n_nodes x 3 float64 boxes. */
+int cqm_bem_get_tree(const cqm_handle* h, int32_t* perm, int32_t* begin, int32_t* end,
+                     int32_t* son0, int32_t* son1, int32_t* level, double* lo, double* hi);
+
+/* Block partition (Defs. 3-4): near (n_near x 2) and far (n_far x 2) cluster
+ * pairs sorted by (row, column); ranks of their MACA factors. Any may be NULL. */
+int cqm_bem_get_blocks(const cqm_handle* h, int32_t* near_rc, int32_t* far_rc,
+                       int32_t* near_rank, int32_t* far_rank);
+
+/* MACA factors of one block (eq. maca): kind 0 = near, 1 = far; b = index in
+ * the sorted list.  C: rank x rows x cols complex (rows/cols in tree order:
+ * triangles perm[begin..end) for near blocks, Chebyshev multi-indices for far
+ * blocks); D: rank x Ls complex (D[t][l] = d_t[l]).  Either may be NULL. */
+int cqm_bem_get_block_factors(const cqm_handle* h, int32_t kind, int32_t b,
+                              int32_t* rank, int32_t* rows, int32_t* cols,
+                              double* C, double* D);
+
+/* Galerkin entries V_l[I[k], J[k]] computed directly by the quadrature
+ * kernel at the frequencies l = freq[f] (0 <= freq[f] < L).
+ * out: npairs x nfreq complex.  I, J, freq, out in `mem` memory. */
+int cqm_bem_entries(cqm_handle* h, int64_t npairs, const int32_t* I, const int32_t* J,
+                    int32_t nfreq, const int32_t* freq, double* out, int32_t mem);
+
+/* Apply the handle's operator: y_l = V_l x_l for the Ls solved frequencies.
+ * x, y: Ls x nt complex in `mem` memory (row l = frequency l). */
+int cqm_bem_apply(cqm_handle* h, const double* x, double* y, int32_t mem);
+
+/* Solve V_l qhat_l = ghat_l for the Ls solved frequencies (batched GMRES).
+ * ghat, qhat: Ls x nt complex in `mem` memory. */
+int cqm_bem_solve_frequencies(cqm_handle* h, const double* ghat, double* qhat, int32_t mem,
+                              cqm_solve_info* info);
+
+/* R-scaled transforms alone: forward ghat_l = sum_n R^n b_n zeta^{n l}
+ * ((N+1) x nt real -> Ls x nt complex) and inverse (eq. omega_n, with
+ * conjugate symmetry; Ls x nt complex -> (N+1) x nt real). */
+int cqm_bem_forward_transform(cqm_handle* h, const double* b, double* ghat, int32_t mem);
+int cqm_bem_inverse_transform(cqm_handle* h, const double* qhat, double* q, int32_t mem);
+
+/* ---- Kernel timing ------------------------------------------------------ */
+
+/* Kernel classes timed by the profiler (index into cqm_bem_profile_read). */
+#define CQM_K_GEOMETRY       0
+#define CQM_K_TREE           1
+#define CQM_K_PARTITION      2
+#define CQM_K_BASES          3
+#define CQM_K_DENSE_ASSEMBLE 4
+#define CQM_K_ENTRIES        5
+#define CQM_K_MACA_SLICE     6
+#define CQM_K_MACA_PIVOT     7
+#define CQM_K_MACA_FIBRE     8
+#define CQM_K_MACA_FINALIZE  9
+#define CQM_K_NEAR_APPLY     10
+#define CQM_K_LEAF_FORWARD   11
+#define CQM_K_UPSWEEP        12
+#define CQM_K_FAR_COUPLING   13
+#define CQM_K_DOWNSWEEP      14
+#define CQM_K_LEAF_BACKWARD  15
+#define CQM_K_DENSE_APPLY    16
+#define CQM_K_ARNOLDI        17
+#define CQM_K_GMRES_OTHER    18
+#define CQM_K_FORWARD_DFT    19
+#define CQM_K_INVERSE_DFT    20
+#define CQM_K_RHS            21
+#define CQM_K_COUNT          22
+
+/* Turn per-launch event timing on (nonzero) or off; either way the counters
+ * are reset.  Timing adds one event pair per launch on the handle's stream. */
+int cqm_bem_profile(cqm_handle* h, int32_t enable);
+
+/* Launch counts and summed device time (ms, CUDA events on the launching
+ * stream) of the first n kernel classes since the last reset; synchronises
+ * the stream.  launches and total_ms hold n entries each. */
+int cqm_bem_profile_read(cqm_handle* h, int32_t n, int64_t* launches, double* total_ms);
+
+/* Name of a kernel class ("" when out of range). */
+const char* cqm_bem_kernel_name(int32_t id);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CQM_BEM_H */

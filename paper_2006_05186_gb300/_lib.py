@@ -1,0 +1,364 @@
+"""Thin ctypes binding of libcqmbem (include/cqm_bem.h).
+
+Argument marshalling only: every step of the method runs in the CUDA library.
+numpy arrays are passed as host memory (CQM_MEM_HOST); torch CUDA tensors as
+device memory (CQM_MEM_DEVICE).  Complex data are complex128 (interleaved
+re/im float64).  Device memory of a handle comes from PyTorch's caching
+allocator through the library's allocator callback; the handle runs on the
+current PyTorch CUDA stream unless another stream is given.
+
+Importing this module does not need a GPU; loading the library does need the
+built libcqmbem.so and fails loudly when it is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+CQM_OK, CQM_EINVAL, CQM_ENOMEM, CQM_ENOCONV, CQM_ETIMEOUT, CQM_ECUDA, CQM_ECAPACITY = range(7)
+MODE_DENSE, MODE_H2MACA = 0, 1
+MEM_HOST, MEM_DEVICE = 0, 1
+
+EXPORTED = [
+    "cqm_params_default", "cqm_bem_setup", "cqm_bem_solve", "cqm_bem_rhs_plane_wave",
+    "cqm_bem_destroy", "cqm_bem_strerror", "cqm_bem_last_error", "cqm_bem_get_info",
+    "cqm_bem_get_frequencies", "cqm_bem_get_tree", "cqm_bem_get_blocks",
+    "cqm_bem_get_block_factors", "cqm_bem_entries", "cqm_bem_apply",
+    "cqm_bem_solve_frequencies", "cqm_bem_forward_transform", "cqm_bem_inverse_transform",
+    "cqm_bem_profile", "cqm_bem_profile_read", "cqm_bem_kernel_name",
+]
+K_COUNT = 22
+
+
+class cqm_mesh(C.Structure):
+    _fields_ = [("nv", C.c_int32), ("xyz", C.c_void_p), ("nt", C.c_int32), ("tri", C.c_void_p)]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+
+
+class cqm_allocator(C.Structure):
+    _fields_ = [("ctx", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN)]
+
+
+class cqm_params(C.Structure):
+    _fields_ = [
+        ("mode", C.c_int32), ("R", C.c_double), ("g_sing", C.c_int32), ("g_near", C.c_int32),
+        ("near_ratio", C.c_double), ("n_min", C.c_int32), ("eta", C.c_double),
+        ("cheb_m", C.c_int32), ("aca_eps", C.c_double), ("rank_cap", C.c_int32),
+        ("gmres_restart", C.c_int32), ("gmres_max_iter", C.c_int32), ("gmres_tol", C.c_double),
+        ("profile", C.c_int32), ("allocator", C.POINTER(cqm_allocator)),
+    ]
+
+
+class cqm_setup_info(C.Structure):
+    _fields_ = [
+        ("nt", C.c_int32), ("nv", C.c_int32), ("N", C.c_int32), ("L", C.c_int32), ("Ls", C.c_int32),
+        ("mode", C.c_int32), ("n_nodes", C.c_int32), ("n_leaves", C.c_int32),
+        ("n_near", C.c_int32), ("n_far", C.c_int32), ("near_entries", C.c_int64),
+        ("far_coupling", C.c_int64), ("rank_sum_near", C.c_int64), ("rank_sum_far", C.c_int64),
+        ("rank_max", C.c_int32), ("R", C.c_double), ("device_bytes", C.c_int64),
+        ("t_geometry_ms", C.c_double), ("t_tree_ms", C.c_double), ("t_bases_ms", C.c_double),
+        ("t_assembly_ms", C.c_double),
+    ]
+
+
+class cqm_solve_info(C.Structure):
+    _fields_ = [
+        ("iterations", C.c_int32), ("restarts", C.c_int32), ("converged", C.c_int32),
+        ("Ls", C.c_int32), ("max_rel_residual", C.c_double), ("max_imag", C.c_double),
+        ("t_forward_ms", C.c_double), ("t_gmres_ms", C.c_double), ("t_inverse_ms", C.c_double),
+    ]
+
+
+def _struct_dict(s):
+    return {k: getattr(s, k) for k, _ in s._fields_}
+
+
+_LIB = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load libcqmbem.so; raise if it is missing (there is no fallback)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = lib_path()
+    if not os.path.exists(path):
+        if build_if_missing:
+            _build.build()
+        else:
+            raise RuntimeError(f"libcqmbem.so not built ({path}); run __graft_entry__.build()")
+    lib = C.CDLL(path)
+    vp, i32, i64, dp = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+    sig = {
+        "cqm_params_default": (C.c_int, [C.POINTER(cqm_params)]),
+        "cqm_bem_setup": (C.c_int, [C.POINTER(cqm_mesh), dp, i32, i32, C.POINTER(cqm_params), vp,
+                                    C.POINTER(vp)]),
+        "cqm_bem_solve": (C.c_int, [vp, vp, vp, i32, C.POINTER(cqm_solve_info)]),
+        "cqm_bem_rhs_plane_wave": (C.c_int, [vp, C.POINTER(C.c_double), dp, dp, vp, i32]),
+        "cqm_bem_destroy": (C.c_int, [vp]),
+        "cqm_bem_strerror": (C.c_char_p, [C.c_int]),
+        "cqm_bem_last_error": (C.c_char_p, []),
+        "cqm_bem_get_info": (C.c_int, [vp, C.POINTER(cqm_setup_info)]),
+        "cqm_bem_get_frequencies": (C.c_int, [vp, vp]),
+        "cqm_bem_get_tree": (C.c_int, [vp] + [vp] * 8),
+        "cqm_bem_get_blocks": (C.c_int, [vp, vp, vp, vp, vp]),
+        "cqm_bem_get_block_factors": (C.c_int, [vp, i32, i32, vp, vp, vp, vp, vp]),
+        "cqm_bem_entries": (C.c_int, [vp, i64, vp, vp, i32, vp, vp, i32]),
+        "cqm_bem_apply": (C.c_int, [vp, vp, vp, i32]),
+        "cqm_bem_solve_frequencies": (C.c_int, [vp, vp, vp, i32, C.POINTER(cqm_solve_info)]),
+        "cqm_bem_forward_transform": (C.c_int, [vp, vp, vp, i32]),
+        "cqm_bem_inverse_transform": (C.c_int, [vp, vp, vp, i32]),
+        "cqm_bem_profile": (C.c_int, [vp, i32]),
+        "cqm_bem_profile_read": (C.c_int, [vp, i32, vp, vp]),
+        "cqm_bem_kernel_name": (C.c_char_p, [i32]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _LIB = lib
+    return lib
+
+
+class CqmError(RuntimeError):
+    def __init__(self, code, where):
+        lib = load()
+        msg = lib.cqm_bem_strerror(code).decode()
+        detail = lib.cqm_bem_last_error().decode()
+        super().__init__(f"{where}: {msg} ({code}) {detail}")
+        self.code = code
+
+
+def _check(code, where, allow=()):
+    if code != CQM_OK and code not in allow:
+        raise CqmError(code, where)
+    return code
+
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x):
+    """(pointer, mem kind) of a numpy array or a torch CUDA tensor."""
+    if x is None:
+        return None, MEM_HOST
+    if _is_torch(x):
+        if not x.is_cuda:
+            raise ValueError("torch tensors must be on the GPU; pass numpy arrays for host data")
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return C.c_void_p(x.data_ptr()), MEM_DEVICE
+    if not x.flags["C_CONTIGUOUS"]:
+        raise ValueError("array must be C-contiguous")
+    return C.c_void_p(x.ctypes.data), MEM_HOST
+
+
+def _torch_allocator(device):
+    import torch
+
+    def alloc(nbytes, stream, ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), device, int(stream or 0))
+        except Exception:
+            return None
+
+    def free(ptr, nbytes, stream, ctx):
+        try:
+            torch.cuda.caching_allocator_delete(int(ptr))
+        except Exception:
+            pass
+
+    a, f = ALLOC_FN(alloc), FREE_FN(free)
+    return cqm_allocator(None, a, f), (a, f)
+
+
+def default_params(**kw) -> cqm_params:
+    p = cqm_params()
+    _check(load().cqm_params_default(C.byref(p)), "cqm_params_default")
+    for k, v in kw.items():
+        if k == "mode" and isinstance(v, str):
+            v = {"dense": MODE_DENSE, "h2maca": MODE_H2MACA}[v]
+        setattr(p, k, v)
+    return p
+
+
+class CqmBem:
+    """One scatterer: setup product (operator) resident on the GPU."""
+
+    def __init__(self, xyz, tri, dt: float, N: int, bdf: int = 2, stream=None,
+                 use_torch_allocator: bool = True, **params):
+        import torch
+        lib = load()
+        self._lib = lib
+        self.device = torch.cuda.current_device()
+        self._stream = stream if stream is not None else torch.cuda.current_stream()
+        self._xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+        self._tri = np.ascontiguousarray(tri, dtype=np.int32)
+        mesh = cqm_mesh(len(self._xyz), self._xyz.ctypes.data, len(self._tri), self._tri.ctypes.data)
+        p = default_params(**params)
+        self._keep = None
+        if use_torch_allocator:
+            self._alloc, self._keep = _torch_allocator(self.device)
+            p.allocator = C.pointer(self._alloc)
+        h = C.c_void_p()
+        _check(lib.cqm_bem_setup(C.byref(mesh), float(dt), int(N), int(bdf), C.byref(p),
+                                 C.c_void_p(self._stream.cuda_stream), C.byref(h)), "cqm_bem_setup")
+        self._h = h
+        self.N, self.M = int(N), len(self._tri)
+        self.L = self.N + 1
+        self.Ls = self.L // 2 + 1
+        self.params = p
+
+    # -- lifecycle ---------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.cqm_bem_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- inspection --------------------------------------------------------
+    def info(self) -> dict:
+        s = cqm_setup_info()
+        _check(self._lib.cqm_bem_get_info(self._h, C.byref(s)), "get_info")
+        return _struct_dict(s)
+
+    def frequencies(self) -> np.ndarray:
+        out = np.zeros(self.L, dtype=np.complex128)
+        _check(self._lib.cqm_bem_get_frequencies(self._h, out.ctypes.data), "get_frequencies")
+        return out
+
+    def tree(self) -> dict:
+        inf = self.info()
+        n = inf["n_nodes"]
+        perm = np.zeros(self.M, np.int32)
+        arr = {k: np.zeros(n, np.int32) for k in ("begin", "end", "son0", "son1", "level")}
+        lo = np.zeros((n, 3))
+        hi = np.zeros((n, 3))
+        _check(self._lib.cqm_bem_get_tree(self._h, perm.ctypes.data, arr["begin"].ctypes.data,
+                                          arr["end"].ctypes.data, arr["son0"].ctypes.data,
+                                          arr["son1"].ctypes.data, arr["level"].ctypes.data,
+                                          lo.ctypes.data, hi.ctypes.data), "get_tree")
+        return dict(perm=perm, lo=lo, hi=hi, **arr)
+
+    def blocks(self) -> dict:
+        inf = self.info()
+        near = np.zeros((inf["n_near"], 2), np.int32)
+        far = np.zeros((inf["n_far"], 2), np.int32)
+        nr = np.zeros(inf["n_near"], np.int32)
+        fr = np.zeros(inf["n_far"], np.int32)
+        _check(self._lib.cqm_bem_get_blocks(self._h, near.ctypes.data, far.ctypes.data,
+                                            nr.ctypes.data, fr.ctypes.data), "get_blocks")
+        return dict(near=near, far=far, near_rank=nr, far_rank=fr)
+
+    def block_factors(self, kind: int, b: int):
+        rank, rows, cols = C.c_int32(), C.c_int32(), C.c_int32()
+        _check(self._lib.cqm_bem_get_block_factors(self._h, kind, b, C.byref(rank), C.byref(rows),
+                                                   C.byref(cols), None, None), "block_factors")
+        Cm = np.zeros((rank.value, rows.value, cols.value), np.complex128)
+        D = np.zeros((rank.value, self.Ls), np.complex128)
+        _check(self._lib.cqm_bem_get_block_factors(self._h, kind, b, C.byref(rank), C.byref(rows),
+                                                   C.byref(cols), Cm.ctypes.data, D.ctypes.data),
+               "block_factors")
+        return Cm, D
+
+    def profile(self, enable: bool = True):
+        """Reset the kernel timers; time every launch from now on if enable."""
+        _check(self._lib.cqm_bem_profile(self._h, 1 if enable else 0), "profile")
+
+    def profile_read(self) -> dict:
+        """{kernel name: (launches, total device ms)} since the last reset."""
+        n = K_COUNT
+        launches = np.zeros(n, np.int64)
+        ms = np.zeros(n, np.float64)
+        _check(self._lib.cqm_bem_profile_read(self._h, n, launches.ctypes.data, ms.ctypes.data),
+               "profile_read")
+        return {self._lib.cqm_bem_kernel_name(k).decode(): (int(launches[k]), float(ms[k]))
+                for k in range(n)}
+
+    # -- steps ---------------------------------------------------------------
+    def entries(self, I, J, freq):
+        I = np.ascontiguousarray(I, np.int32)
+        J = np.ascontiguousarray(J, np.int32)
+        F = np.ascontiguousarray(freq, np.int32)
+        out = np.zeros((len(I), len(F)), np.complex128)
+        _check(self._lib.cqm_bem_entries(self._h, len(I), I.ctypes.data, J.ctypes.data, len(F),
+                                         F.ctypes.data, out.ctypes.data, MEM_HOST), "entries")
+        return out
+
+    def rhs_plane_wave(self, direction, width, delay, out=None):
+        d = (C.c_double * 3)(*[float(v) for v in direction])
+        if out is None:
+            out = np.zeros((self.L, self.M))
+        p, mem = _ptr(out)
+        _check(self._lib.cqm_bem_rhs_plane_wave(self._h, d, float(width), float(delay), p, mem),
+               "rhs_plane_wave")
+        return out
+
+    def forward_transform(self, b):
+        out = _like(b, (self.Ls, self.M), complex_=True)
+        pb, mem = _ptr(b)
+        po, _ = _ptr(out)
+        _check(self._lib.cqm_bem_forward_transform(self._h, pb, po, mem), "forward_transform")
+        return out
+
+    def inverse_transform(self, qhat):
+        out = _like(qhat, (self.L, self.M), complex_=False)
+        pq, mem = _ptr(qhat)
+        po, _ = _ptr(out)
+        _check(self._lib.cqm_bem_inverse_transform(self._h, pq, po, mem), "inverse_transform")
+        return out
+
+    def apply(self, x):
+        out = _like(x, (self.Ls, self.M), complex_=True)
+        px, mem = _ptr(x)
+        po, _ = _ptr(out)
+        _check(self._lib.cqm_bem_apply(self._h, px, po, mem), "apply")
+        return out
+
+    def solve_frequencies(self, ghat, allow_noconv=False):
+        out = _like(ghat, (self.Ls, self.M), complex_=True)
+        pg, mem = _ptr(ghat)
+        po, _ = _ptr(out)
+        inf = cqm_solve_info()
+        _check(self._lib.cqm_bem_solve_frequencies(self._h, pg, po, mem, C.byref(inf)),
+               "solve_frequencies", allow=(CQM_ENOCONV,) if allow_noconv else ())
+        return out, _struct_dict(inf)
+
+    def solve(self, rhs, out=None, allow_noconv=False):
+        """Densities q_n, (N+1) x M, for Galerkin data rhs (same kind of memory)."""
+        if out is None:
+            out = _like(rhs, (self.L, self.M), complex_=False)
+        pr, mem = _ptr(rhs)
+        po, mem2 = _ptr(out)
+        if mem != mem2:
+            raise ValueError("rhs and density must both be host or both device")
+        inf = cqm_solve_info()
+        _check(self._lib.cqm_bem_solve(self._h, pr, po, mem, C.byref(inf)), "solve",
+               allow=(CQM_ENOCONV,) if allow_noconv else ())
+        self.last_solve_info = _struct_dict(inf)
+        return out
+
+
+def _like(x, shape, complex_: bool):
+    if _is_torch(x):
+        import torch
+        return torch.empty(shape, dtype=torch.complex128 if complex_ else torch.float64,
+                           device=x.device)
+    return np.zeros(shape, dtype=np.complex128 if complex_ else np.float64)

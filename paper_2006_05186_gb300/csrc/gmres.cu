@@ -1,0 +1,344 @@
+// Batched restarted GMRES over the solved CQM frequencies: for every l < Ls,
+// V_l qhat_l = ghat_l (Remark in Sec. 6.2; the paper factorises instead and
+// names iterative solvers as the way to avoid the O(M^2) factorisation).
+// All frequencies advance in lockstep; a frequency whose residual estimate
+// meets the tolerance stops contributing to the cycle, and every restart
+// recomputes the true FP64 residual b - V x.
+// Orthogonalisation: classical Gram-Schmidt applied twice (CGS2).
+// Layouts: vectors Ls x M complex (row l); basis (m+1) x Ls x M.
+#include <algorithm>
+#include <vector>
+
+#include "handle.cuh"
+
+namespace cqm {
+
+struct GmresWork {
+  int m = 0;
+  DArray<double2> Vb, r, H, sn, g, y;
+  DArray<double> cs, bnorm, beta;
+  DArray<int> active, kdim, converged, counters;
+  int* h_counters = nullptr;  // pinned
+};
+
+// r = b - y (y = V x) or r = b when y == nullptr; beta_l = ||r_l||,
+// bnorm_l = ||b_l|| on the first call; sets active/converged, v0 = r/beta,
+// g = (beta, 0, ...).
+__global__ void k_restart(int M, int m, const double2* __restrict__ b, const double2* y,
+                          double2* __restrict__ r, double2* __restrict__ V0, double* bnorm,
+                          double* beta, int* active, int* converged, double2* g, double tol,
+                          int first, int* counters) {
+  __shared__ double sh[32];
+  const int l = blockIdx.x;
+  const double2* bl = b + (size_t)l * M;
+  double2* rl = r + (size_t)l * M;
+  double s = 0.0, sb = 0.0;
+  for (int i = threadIdx.x; i < M; i += blockDim.x) {
+    double2 v = bl[i];
+    if (y) v = csub(v, y[(size_t)l * M + i]);
+    rl[i] = v;
+    s += cabs2(v);
+    if (first) sb += cabs2(bl[i]);
+  }
+  s = block_sum(s, sh);
+  if (first) {
+    sb = block_sum(sb, sh);
+    if (threadIdx.x == 0) bnorm[l] = sqrt(sb);
+    __syncthreads();
+  }
+  const double bt = sqrt(s);
+  const double bn = bnorm[l];
+  const bool done = !(bt > tol * bn) || bn == 0.0;
+  if (threadIdx.x == 0) {
+    beta[l] = bt;
+    converged[l] = done ? 1 : 0;
+    active[l] = done ? 0 : 1;
+    if (!done) atomicAdd(&counters[0], 1);
+    g[(size_t)l * (m + 1)] = make_double2(done ? 0.0 : bt, 0.0);
+    for (int k = 1; k <= m; ++k) g[(size_t)l * (m + 1) + k] = make_double2(0.0, 0.0);
+  }
+  if (done) return;
+  const double inv = 1.0 / bt;
+  double2* v0 = V0 + (size_t)l * M;
+  for (int i = threadIdx.x; i < M; i += blockDim.x) v0[i] = cscale(rl[i], inv);
+}
+
+// One Arnoldi step j for every active frequency (one block per l): w = basis
+// slot j+1 (already holds V v_j), CGS2 against v_0..v_j, normalise, Givens.
+template <int KB>
+__global__ void k_arnoldi(int M, int Ls, int m, int j, double2* __restrict__ Vb,
+                          double2* __restrict__ H, double* __restrict__ cs,
+                          double2* __restrict__ sn, double2* __restrict__ g,
+                          const double* __restrict__ bnorm, int* active, int* kdim, double tol,
+                          int* counters) {
+  __shared__ double sh[32];
+  __shared__ double2 hloc[64];
+  const int l = blockIdx.x;
+  if (!active[l]) return;
+  const size_t stride = (size_t)Ls * M;  // between basis vectors
+  double2* w = Vb + (size_t)(j + 1) * stride + (size_t)l * M;
+  const double2* v = Vb + (size_t)l * M;
+  double2* Hl = H + (size_t)l * (m + 1) * m;  // column-major (m+1) x m
+  for (int k = threadIdx.x; k <= j; k += blockDim.x) hloc[k] = make_double2(0.0, 0.0);
+  __syncthreads();
+  for (int pass = 0; pass < 2; ++pass) {
+    // h_k = <v_k, w>, KB at a time
+    for (int k0 = 0; k0 <= j; k0 += KB) {
+      double2 acc[KB];
+#pragma unroll
+      for (int t = 0; t < KB; ++t) acc[t] = make_double2(0.0, 0.0);
+      for (int i = threadIdx.x; i < M; i += blockDim.x) {
+        const double2 wi = w[i];
+#pragma unroll
+        for (int t = 0; t < KB; ++t)
+          if (k0 + t <= j) {
+            double2 vk = v[(size_t)(k0 + t) * stride + i];
+            acc[t].x += vk.x * wi.x + vk.y * wi.y;
+            acc[t].y += vk.x * wi.y - vk.y * wi.x;
+          }
+      }
+#pragma unroll
+      for (int t = 0; t < KB; ++t) {
+        if (k0 + t <= j) {
+          double re = block_sum(acc[t].x, sh);
+          double im = block_sum(acc[t].y, sh);
+          if (threadIdx.x == 0) hloc[k0 + t] = make_double2(re, im);
+        }
+      }
+    }
+    __syncthreads();
+    // w -= sum_k h_k v_k
+    for (int i = threadIdx.x; i < M; i += blockDim.x) {
+      double2 wi = w[i];
+      for (int k = 0; k <= j; ++k) {
+        double2 vk = v[(size_t)k * stride + i];
+        double2 hk = hloc[k];
+        wi.x -= hk.x * vk.x - hk.y * vk.y;
+        wi.y -= hk.x * vk.y + hk.y * vk.x;
+      }
+      w[i] = wi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+      for (int k = 0; k <= j; ++k) Hl[(size_t)j * (m + 1) + k] = pass == 0 ? hloc[k] : cadd(Hl[(size_t)j * (m + 1) + k], hloc[k]);
+    __syncthreads();
+  }
+  double s2 = 0.0;
+  for (int i = threadIdx.x; i < M; i += blockDim.x) s2 += cabs2(w[i]);
+  const double hn = sqrt(block_sum(s2, sh));
+  if (hn > 0.0) {
+    const double inv = 1.0 / hn;
+    for (int i = threadIdx.x; i < M; i += blockDim.x) w[i] = cscale(w[i], inv);
+  }
+  if (threadIdx.x == 0) {
+    double2* col = Hl + (size_t)j * (m + 1);
+    col[j + 1] = make_double2(hn, 0.0);
+    double* csl = cs + (size_t)l * m;
+    double2* snl = sn + (size_t)l * m;
+    for (int k = 0; k < j; ++k) {  // previous rotations
+      double2 a = col[k], b = col[k + 1];
+      col[k] = cadd(cscale(a, csl[k]), cmul(snl[k], b));
+      col[k + 1] = csub(cscale(b, csl[k]), cmulc(snl[k], a));  // -conj(s) a + c b
+    }
+    double2 a = col[j], b = col[j + 1];
+    double aa = sqrt(cabs2(a)), bb = sqrt(cabs2(b));
+    double c;
+    double2 s;
+    if (bb == 0.0) {
+      c = 1.0;
+      s = make_double2(0.0, 0.0);
+    } else if (aa == 0.0) {
+      c = 0.0;
+      s = make_double2(1.0, 0.0);
+    } else {
+      double t = hypot(aa, bb);
+      c = aa / t;
+      double2 ph = cscale(a, 1.0 / aa);
+      s = cscale(cmul(ph, make_double2(b.x, -b.y)), 1.0 / t);
+    }
+    csl[j] = c;
+    snl[j] = s;
+    col[j] = cadd(cscale(a, c), cmul(s, b));
+    col[j + 1] = make_double2(0.0, 0.0);
+    double2* gl = g + (size_t)l * (m + 1);
+    double2 gj = gl[j];
+    gl[j] = cscale(gj, c);
+    gl[j + 1] = make_double2(-(s.x * gj.x + s.y * gj.y), -(s.x * gj.y - s.y * gj.x));  // -conj(s) g_j
+    kdim[l] = j + 1;
+    const double res = sqrt(cabs2(gl[j + 1]));
+    if (!(res > tol * bnorm[l]) || hn == 0.0) {
+      active[l] = 0;
+      atomicSub(&counters[0], 1);
+    }
+  }
+}
+
+// Back substitution R y = g (k = kdim[l]) and x_l += V y; one block per l.
+__global__ void k_update_x(int M, int Ls, int m, const double2* __restrict__ Vb,
+                           const double2* __restrict__ H, const double2* __restrict__ g,
+                           const int* __restrict__ kdim, const int* __restrict__ converged,
+                           double2* __restrict__ y, double2* __restrict__ x) {
+  const int l = blockIdx.x;
+  const int k = kdim[l];
+  if (converged[l] || k == 0) return;
+  const double2* Hl = H + (size_t)l * (m + 1) * m;
+  double2* yl = y + (size_t)l * m;
+  if (threadIdx.x == 0) {
+    for (int i = k - 1; i >= 0; --i) {
+      double2 acc = g[(size_t)l * (m + 1) + i];
+      for (int c = i + 1; c < k; ++c) acc = csub(acc, cmul(Hl[(size_t)c * (m + 1) + i], yl[c]));
+      yl[i] = cdiv(acc, Hl[(size_t)i * (m + 1) + i]);
+    }
+  }
+  __syncthreads();
+  const size_t stride = (size_t)Ls * M;
+  for (int i = threadIdx.x; i < M; i += blockDim.x) {
+    double2 xi = x[(size_t)l * M + i];
+    for (int c = 0; c < k; ++c) cfma(xi, yl[c], Vb[(size_t)c * stride + (size_t)l * M + i]);
+    x[(size_t)l * M + i] = xi;
+  }
+}
+
+__global__ void k_true_residual(int M, const double2* __restrict__ b, const double2* __restrict__ Ax,
+                                const double* __restrict__ bnorm, double* rel) {
+  __shared__ double sh[32];
+  const int l = blockIdx.x;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < M; i += blockDim.x)
+    s += cabs2(csub(b[(size_t)l * M + i], Ax[(size_t)l * M + i]));
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) rel[l] = bnorm[l] > 0 ? sqrt(s) / bnorm[l] : 0.0;
+}
+
+int gmres_solve(cqm_handle* h, const double2* d_b, double2* d_x, cqm_solve_info* info) {
+  const int M = h->M, Ls = h->Ls;
+  const int m = std::max(1, std::min(h->params.gmres_restart, 64));
+  const double tol = h->params.gmres_tol;
+  Allocator& A = h->alloc;
+  GmresWork W;
+  int st = CQM_OK;
+  auto cleanup = [&]() {
+    W.Vb.free(A); W.r.free(A); W.H.free(A); W.sn.free(A); W.g.free(A); W.y.free(A);
+    W.cs.free(A); W.bnorm.free(A); W.beta.free(A); W.active.free(A); W.kdim.free(A);
+    W.converged.free(A); W.counters.free(A);
+    if (W.h_counters) cudaFreeHost(W.h_counters);
+  };
+#define GM_TRY(e) do { st = (e); if (st != CQM_OK) { cleanup(); return st; } } while (0)
+  GM_TRY(W.Vb.allocate(A, (size_t)(m + 1) * Ls * M));
+  GM_TRY(W.r.allocate(A, (size_t)Ls * M));
+  GM_TRY(W.H.allocate(A, (size_t)Ls * (m + 1) * m));
+  GM_TRY(W.sn.allocate(A, (size_t)Ls * m));
+  GM_TRY(W.g.allocate(A, (size_t)Ls * (m + 1)));
+  GM_TRY(W.y.allocate(A, (size_t)Ls * m));
+  GM_TRY(W.cs.allocate(A, (size_t)Ls * m));
+  GM_TRY(W.bnorm.allocate(A, Ls));
+  GM_TRY(W.beta.allocate(A, Ls));
+  GM_TRY(W.active.allocate(A, Ls));
+  GM_TRY(W.kdim.allocate(A, Ls));
+  GM_TRY(W.converged.allocate(A, Ls));
+  GM_TRY(W.counters.allocate(A, 4));
+  if (cudaMallocHost(&W.h_counters, 4 * sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    W.h_counters = nullptr;
+    cleanup();
+    set_last_error("cudaMallocHost failed");
+    return CQM_ENOMEM;
+  }
+  cudaStream_t S = h->stream;
+  auto cu = [&](cudaError_t e) -> int {
+    if (e != cudaSuccess) {
+      set_last_error(std::string("gmres: ") + cudaGetErrorString(e));
+      return CQM_ECUDA;
+    }
+    return CQM_OK;
+  };
+  GM_TRY(cu(cudaMemsetAsync(d_x, 0, sizeof(double2) * Ls * M, S)));
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, S);
+  int iters = 0, restarts = 0;
+  bool first = true;
+  const int maxit = std::max(1, h->params.gmres_max_iter);
+  int status = CQM_OK;
+  while (true) {
+    double2* Ax = W.Vb.p + (size_t)1 * Ls * M;  // scratch: basis slot 1
+    if (!first) GM_TRY(apply_operator(h, d_x, Ax));
+    GM_TRY(cu(cudaMemsetAsync(W.counters.p, 0, 4 * sizeof(int), S)));
+    {
+      ProfScope ps_(h, CQM_K_GMRES_OTHER);
+      k_restart<<<Ls, 256, 0, S>>>(M, m, d_b, first ? nullptr : Ax, W.r.p, W.Vb.p, W.bnorm.p,
+                                   W.beta.p, W.active.p, W.converged.p, W.g.p, tol, first ? 1 : 0,
+                                   W.counters.p);
+    }
+    GM_TRY(cu(cudaGetLastError()));
+    GM_TRY(cu(cudaMemsetAsync(W.kdim.p, 0, sizeof(int) * Ls, S)));
+    first = false;
+    GM_TRY(cu(cudaMemcpyAsync(W.h_counters, W.counters.p, sizeof(int), cudaMemcpyDeviceToHost, S)));
+    GM_TRY(cu(cudaStreamSynchronize(S)));
+    if (W.h_counters[0] == 0) break;
+    if (iters >= maxit) {
+      status = CQM_ENOCONV;
+      break;
+    }
+    for (int j = 0; j < m && iters < maxit; ++j) {
+      GM_TRY(apply_operator(h, W.Vb.p + (size_t)j * Ls * M, W.Vb.p + (size_t)(j + 1) * Ls * M));
+      {
+        ProfScope ps_(h, CQM_K_ARNOLDI);
+        k_arnoldi<8><<<Ls, 256, 0, S>>>(M, Ls, m, j, W.Vb.p, W.H.p, W.cs.p, W.sn.p, W.g.p,
+                                        W.bnorm.p, W.active.p, W.kdim.p, tol, W.counters.p);
+      }
+      GM_TRY(cu(cudaGetLastError()));
+      ++iters;
+      if ((j % 4) == 3 || j == m - 1) {
+        GM_TRY(cu(cudaMemcpyAsync(W.h_counters, W.counters.p, sizeof(int), cudaMemcpyDeviceToHost, S)));
+        GM_TRY(cu(cudaStreamSynchronize(S)));
+        if (W.h_counters[0] == 0) break;
+      }
+    }
+    {
+      ProfScope ps_(h, CQM_K_GMRES_OTHER);
+      k_update_x<<<Ls, 256, 0, S>>>(M, Ls, m, W.Vb.p, W.H.p, W.g.p, W.kdim.p, W.converged.p, W.y.p,
+                                    d_x);
+    }
+    GM_TRY(cu(cudaGetLastError()));
+    ++restarts;
+  }
+  cudaEventRecord(e1, S);
+  // final true residual
+  double2* Ax = W.Vb.p;
+  GM_TRY(apply_operator(h, d_x, Ax));
+  {
+    ProfScope ps_(h, CQM_K_GMRES_OTHER);
+    k_true_residual<<<Ls, 256, 0, S>>>(M, d_b, Ax, W.bnorm.p, W.beta.p);
+  }
+  GM_TRY(cu(cudaGetLastError()));
+  std::vector<double> rel(Ls);
+  std::vector<int> conv(Ls);
+  GM_TRY(cu(cudaMemcpyAsync(rel.data(), W.beta.p, sizeof(double) * Ls, cudaMemcpyDeviceToHost, S)));
+  GM_TRY(cu(cudaMemcpyAsync(conv.data(), W.converged.p, sizeof(int) * Ls, cudaMemcpyDeviceToHost, S)));
+  GM_TRY(cu(cudaStreamSynchronize(S)));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (info) {
+    info->iterations = iters;
+    info->restarts = restarts;
+    info->Ls = Ls;
+    int c = 0;
+    double mx = 0.0;
+    for (int l = 0; l < Ls; ++l) {
+      c += conv[l];
+      mx = std::max(mx, rel[l]);
+    }
+    info->converged = c;
+    info->max_rel_residual = mx;
+    info->t_gmres_ms = ms;
+  }
+  cleanup();
+#undef GM_TRY
+  return status;
+}
+
+}  // namespace cqm

@@ -1,0 +1,126 @@
+// Internal state of a cqm_handle and the entry points of each module.
+#pragma once
+
+#include <vector>
+
+#include "common.cuh"
+#include "quad.cuh"
+
+struct cqm_handle {
+  cqm::Allocator alloc;
+  cudaStream_t stream = nullptr;
+  cqm_params params{};
+  int M = 0, nv = 0, N = 0, L = 0, Ls = 0, bdf = 2;
+  double dt = 0.0, R = 0.0;
+
+  // geometry (Sec. 3.2: flat triangles)
+  cqm::DArray<int> tri;
+  cqm::DArray<double> xyz, P, area, cen, diam;
+  cqm::DArray<int> flag;  // device status word (degenerate input, capacity, ...)
+
+  // quadrature tables
+  cqm::DArray<double4> near_pt, ss_pt[3];
+  cqm::DArray<double> ss_w[3];
+  cqm::Quad quad{};
+
+  // CQM frequencies s_l, l = 0..L-1 (eq. cqm_freq)
+  cqm::DArray<double2> s;
+  std::vector<double2> s_host;
+
+  // dense representation: V[l][i][j], l < Ls
+  cqm::DArray<double2> Vd;
+
+  // cluster tree (Def. 2), breadth-first numbering
+  int n_nodes = 0, n_leaves = 0, depth = 0;
+  cqm::DArray<int> perm, node_begin, node_end, node_son0, node_son1, node_parent, node_level;
+  cqm::DArray<double> node_lo, node_hi;  // n_nodes x 3
+  std::vector<int> level_begin;          // host: first node of each level (+ sentinel)
+  std::vector<int> h_begin, h_end, h_son0, h_son1, h_level;
+
+  // block partition (Defs. 3-4), sorted by (row, column)
+  int n_near = 0, n_far = 0;
+  cqm::DArray<int2> near_rc, far_rc;
+  cqm::DArray<int> near_rowptr, far_rowptr;  // CSR over row clusters (n_nodes + 1)
+  std::vector<int2> h_near, h_far;
+
+  // cluster bases (Sec. 4.2, Alg. 1): Chebyshev nodes, leaf matrices, transfers
+  int m = 4, p = 64;
+  cqm::DArray<double> cheb;      // n_nodes x 3 x m
+  cqm::DArray<double> Uleaf;     // per position i (tree order): p values -> M x p
+  cqm::DArray<double> Etr;       // per node (non-root): 3 x m x m 1-D transfer factors
+
+  // MACA factors (Alg. 2, eq. lrfinal); rank slots of capacity rank_cap per block
+  int rank_cap = 32;
+  cqm::DArray<int> near_rank, far_rank;
+  cqm::DArray<int64_t> near_off;      // C slot base per near block (complex entries)
+  cqm::DArray<double2> nearC, nearD;  // C: sum_b cap * #r #c ; D: n_near x cap x Ls
+  cqm::DArray<double2> farC, farD;    // C: n_far x cap x p x p ; D: n_far x cap x Ls
+  std::vector<int> h_near_rank, h_far_rank;
+  std::vector<int64_t> h_near_off;
+
+  // apply plan: leaf clusters and row clusters owning far blocks
+  std::vector<int> h_leaves, h_far_rows;
+  cqm::DArray<int> d_leaves, d_far_rows;
+
+  // solver workspace
+  cqm::DArray<double2> xhat, yhat;  // n_nodes x p x Ls (far field transforms)
+
+  cqm_setup_info info{};
+
+  // per-launch kernel timing (cqm_bem_profile)
+  bool prof_on = false;
+  struct ProfRec { int id; cudaEvent_t a, b; };
+  std::vector<ProfRec> prof_recs;
+  std::vector<cudaEvent_t> prof_pool;
+  int64_t prof_launch[CQM_K_COUNT] = {};
+  double prof_ms[CQM_K_COUNT] = {};
+};
+
+namespace cqm {
+
+// geometry.cu
+int build_geometry(cqm_handle* h, const cqm_mesh* mesh);
+int build_frequencies(cqm_handle* h);
+int rhs_plane_wave(cqm_handle* h, const double dir[3], double width, double delay, double* d_rhs);
+
+// transform.cu
+int forward_transform(cqm_handle* h, const double* d_b, double2* d_ghat);
+int inverse_transform(cqm_handle* h, const double2* d_qhat, double* d_q);
+
+// entries.cu
+int build_quad_tables(cqm_handle* h);
+int entries_list(cqm_handle* h, int64_t npairs, const int* d_I, const int* d_J, int nfreq,
+                 const int* d_freq, double2* d_out);
+int assemble_dense(cqm_handle* h);
+int apply_dense(cqm_handle* h, const double2* x, double2* y);
+
+// cluster.cu
+int build_tree(cqm_handle* h);
+int build_partition(cqm_handle* h);
+
+// h2.cu
+int build_bases(cqm_handle* h);
+int apply_compressed(cqm_handle* h, const double2* x, double2* y);
+
+// maca.cu
+int build_maca(cqm_handle* h);
+
+// gmres.cu
+int gmres_solve(cqm_handle* h, const double2* d_b, double2* d_x, cqm_solve_info* info);
+
+// Kernel timing scope: records an event pair around the launches it encloses.
+struct ProfScope {
+  cqm_handle* h;
+  int idx = -1;
+  ProfScope(cqm_handle* hh, int id);
+  ~ProfScope();
+};
+void prof_resolve(cqm_handle* h);
+void prof_release(cqm_handle* h);
+
+// operator dispatch
+inline int apply_operator(cqm_handle* h, const double2* x, double2* y) {
+  return h->params.mode == CQM_MODE_DENSE ? apply_dense(h, x, y) : apply_compressed(h, x, y);
+}
+
+}  // namespace cqm

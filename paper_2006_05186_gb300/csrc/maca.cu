@@ -1,0 +1,455 @@
+// Multivariate adaptive cross approximation of every block of the tensor
+// partition over the solved frequencies (Sec. 5.1, Alg. 2; Alg. 3):
+//   G^(l) = sum_{t<l} C_t x_3 d_t,  C_l = G[:,:,k_l] - G^(l-1)[:,:,k_l],
+//   (i_l, j_l) = first argmax |C_l| (row-major), d_l = (G[i_l,j_l,:] -
+//   G^(l-1)[i_l,j_l,:]) / C_l[i_l,j_l], k_{l+1} = argmax over unused k of
+//   |d_l[k]| (ties: smallest k), k_1 = 0; stop when ||C_l||_F ||d_l||_2 <=
+//   eps ||G^(l)||_F (norm from the Gram identity of Sec. 5.1), on a zero pivot
+//   (|pivot| <= 1e-300) or when every frequency is used; every computed update
+//   is kept.
+// Near blocks take entries from the Galerkin quadrature (Alg. 3 NEAR), far
+// blocks from the kernel at the Chebyshev points (Alg. 3 FAR).
+// All blocks advance one rank step per round of four launches:
+//   slice -> residual update + pivot + Gram(C) -> fibre -> finalize.
+#include <algorithm>
+#include <vector>
+
+#include "handle.cuh"
+
+namespace cqm {
+
+struct MacaBlocks {
+  int n;            // blocks
+  int kind;         // 0 near, 1 far
+  int Ls, cap, p, m;
+  const int2* rc;   // (row, col) clusters
+  const int* begin;
+  const int* end;
+  const int* perm;
+  const double* cheb;  // far: Chebyshev nodes
+  const int64_t* off;  // near: C slot base per block
+  double2* C;
+  double2* D;          // (b * cap + t) * Ls
+  int* rank;
+  int* active;
+  int* kcur;
+  int2* piv;
+  double2* pval;
+  double* cn2;
+  double* norm2;
+  double2* gramc;      // b * cap + t
+  unsigned* used;      // b * words
+  int words;
+  int* counters;       // [0] active blocks, [1] capacity overflow
+  double eps;
+};
+
+__device__ __forceinline__ int rows_of(const MacaBlocks& B, int b) {
+  return B.kind == 0 ? B.end[B.rc[b].x] - B.begin[B.rc[b].x] : B.p;
+}
+__device__ __forceinline__ int cols_of(const MacaBlocks& B, int b) {
+  return B.kind == 0 ? B.end[B.rc[b].y] - B.begin[B.rc[b].y] : B.p;
+}
+__device__ __forceinline__ double2* slot(const MacaBlocks& B, int b, int t, int nr, int nc) {
+  return B.kind == 0 ? B.C + B.off[b] + (size_t)t * nr * nc
+                     : B.C + ((size_t)b * B.cap + t) * (size_t)B.p * B.p;
+}
+
+// Chebyshev point mu of cluster r.
+__device__ __forceinline__ void cheb_point(const double* cheb, int r, int m, int mu, double* x) {
+  const double* nd = cheb + (size_t)r * 3 * m;
+  x[0] = nd[mu % m];
+  x[1] = nd[m + (mu / m) % m];
+  x[2] = nd[2 * m + mu / (m * m)];
+}
+
+__device__ __forceinline__ double2 kernel_value(double r, double2 s) {
+  const double e = exp(-s.x * r) / (CQM_FOUR_PI * r);
+  double sn, cs;
+  sincos(s.y * r, &sn, &cs);
+  return make_double2(e * cs, -e * sn);
+}
+
+// Slice G[:,:,k] of every active block into slot rank[b].
+__global__ void __launch_bounds__(256) k_maca_slice(MacaBlocks B, Geom g, Quad q,
+                                                    const double2* __restrict__ s) {
+  const int b = blockIdx.x;
+  if (!B.active[b]) return;
+  const int nr = rows_of(B, b), nc = cols_of(B, b);
+  const int t = B.rank[b];
+  double2* out = slot(B, b, t, nr, nc);
+  const double2 sk = s[B.kcur[b]];
+  const int2 rc = B.rc[b];
+  if (B.kind == 1) {
+    for (int e = threadIdx.x; e < nr * nc; e += blockDim.x) {
+      const int mu = e / nc, nu = e - mu * nc;
+      double xr[3], xc[3];
+      cheb_point(B.cheb, rc.x, B.m, mu, xr);
+      cheb_point(B.cheb, rc.y, B.m, nu, xc);
+      const double d0 = xc[0] - xr[0], d1 = xc[1] - xr[1], d2 = xc[2] - xr[2];
+      out[e] = kernel_value(sqrt(d0 * d0 + d1 * d1 + d2 * d2), sk);
+    }
+    return;
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int rb = B.begin[rc.x], cb = B.begin[rc.y];
+  double2 sv[1] = {sk};
+  for (int e = w; e < nr * nc; e += nw) {
+    const int i = e / nc, j = e - i * nc;
+    const int I = B.perm[rb + i], J = B.perm[cb + j];
+    double2 acc[1] = {make_double2(0.0, 0.0)};
+    const int cse = pair_case(g, q, I, J);
+    pair_accumulate<1>(g, q, I, J, cse, lane, 32, sv, 1, acc);
+    acc[0] = warp_sum2(acc[0]);
+    if (lane == 0) out[e] = acc[0];
+  }
+}
+
+// Residual update of the new slice, pivot search, ||C_l||^2 and <C_t, C_l>.
+__global__ void __launch_bounds__(256) k_maca_pivot(MacaBlocks B) {
+  __shared__ double sh[32];
+  __shared__ double s_best[32];
+  __shared__ int s_bidx[32];
+  __shared__ double2 dk[64];
+  const int b = blockIdx.x;
+  if (!B.active[b]) return;
+  const int nr = rows_of(B, b), nc = cols_of(B, b), n = nr * nc;
+  const int l = B.rank[b];
+  const int k = B.kcur[b];
+  for (int t = threadIdx.x; t < l; t += blockDim.x) dk[t] = B.D[((size_t)b * B.cap + t) * B.Ls + k];
+  __syncthreads();
+  double2* Cl = slot(B, b, l, nr, nc);
+  double best = -1.0, nrm = 0.0;
+  int bidx = 0x7fffffff;
+  for (int e = threadIdx.x; e < n; e += blockDim.x) {
+    double2 v = Cl[e];
+    for (int t = 0; t < l; ++t) {
+      const double2 c = slot(B, b, t, nr, nc)[e];
+      v = csub(v, cmul(c, dk[t]));
+    }
+    Cl[e] = v;
+    const double a = cabs2(v);
+    nrm += a;
+    if (a > best) { best = a; bidx = e; }
+  }
+  // block argmax: largest |v|^2, smallest index on ties
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, bidx, o);
+    if (ob > best || (ob == best && oi < bidx)) { best = ob; bidx = oi; }
+  }
+  if (lane == 0) { s_best[warp] = best; s_bidx[warp] = bidx; }
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = blockDim.x >> 5;
+    best = lane < nw ? s_best[lane] : -1.0;
+    bidx = lane < nw ? s_bidx[lane] : 0x7fffffff;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bidx, o);
+      if (ob > best || (ob == best && oi < bidx)) { best = ob; bidx = oi; }
+    }
+    if (lane == 0) { s_best[0] = best; s_bidx[0] = bidx; }
+  }
+  __syncthreads();
+  nrm = block_sum(nrm, sh);
+  const int pi = s_bidx[0];
+  if (threadIdx.x == 0) {
+    const double2 pv = Cl[pi];
+    B.piv[b] = make_int2(pi / nc, pi - (pi / nc) * nc);
+    B.pval[b] = pv;
+    B.cn2[b] = nrm;
+    if (!(sqrt(cabs2(pv)) > 1e-300)) {
+      B.active[b] = 0;
+      atomicSub(&B.counters[0], 1);
+    }
+  }
+  // Gram products <C_t, C_l> = sum conj(C_t) C_l
+  for (int t = 0; t < l; ++t) {
+    const double2* Ct = slot(B, b, t, nr, nc);
+    double re = 0.0, im = 0.0;
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+      const double2 a = Ct[e], c = Cl[e];
+      re += a.x * c.x + a.y * c.y;
+      im += a.x * c.y - a.y * c.x;
+    }
+    re = block_sum(re, sh);
+    im = block_sum(im, sh);
+    if (threadIdx.x == 0) B.gramc[(size_t)b * B.cap + t] = make_double2(re, im);
+  }
+}
+
+// Fibre G[i_l, j_l, :] of every active block into D slot rank[b] (raw).
+__global__ void __launch_bounds__(256) k_maca_fibre(MacaBlocks B, Geom g, Quad q,
+                                                    const double2* __restrict__ s) {
+  const int b = blockIdx.x;
+  if (!B.active[b]) return;
+  const int l = B.rank[b];
+  double2* out = B.D + ((size_t)b * B.cap + l) * B.Ls;
+  const int2 rc = B.rc[b];
+  const int2 pv = B.piv[b];
+  if (B.kind == 1) {
+    double xr[3], xc[3];
+    cheb_point(B.cheb, rc.x, B.m, pv.x, xr);
+    cheb_point(B.cheb, rc.y, B.m, pv.y, xc);
+    const double d0 = xc[0] - xr[0], d1 = xc[1] - xr[1], d2 = xc[2] - xr[2];
+    const double r = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+    for (int k = threadIdx.x; k < B.Ls; k += blockDim.x) out[k] = kernel_value(r, s[k]);
+    return;
+  }
+  const int I = B.perm[B.begin[rc.x] + pv.x], J = B.perm[B.begin[rc.y] + pv.y];
+  const int cse = pair_case(g, q, I, J);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  constexpr int NF = 8;
+  for (int f0 = w * NF; f0 < B.Ls; f0 += nw * NF) {
+    const int nf = min(NF, B.Ls - f0);
+    double2 sv[NF], acc[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      sv[f] = f < nf ? s[f0 + f] : make_double2(0.0, 0.0);
+      acc[f] = make_double2(0.0, 0.0);
+    }
+    pair_accumulate<NF>(g, q, I, J, cse, lane, 32, sv, nf, acc);
+#pragma unroll
+    for (int f = 0; f < NF; ++f) acc[f] = warp_sum2(acc[f]);
+    if (lane == 0)
+      for (int f = 0; f < nf; ++f) out[f0 + f] = acc[f];
+  }
+}
+
+// d_l = (fibre - sum_t C_t[i,j] d_t) / pivot, Gram <d_t, d_l>, norm update,
+// stopping test and the next slice.
+__global__ void __launch_bounds__(256) k_maca_finalize(MacaBlocks B) {
+  __shared__ double sh[32];
+  __shared__ double2 cij[64];
+  __shared__ double s_best[32];
+  __shared__ int s_bidx[32];
+  const int b = blockIdx.x;
+  if (!B.active[b]) return;
+  const int nr = rows_of(B, b), nc = cols_of(B, b);
+  const int l = B.rank[b];
+  const int2 pv = B.piv[b];
+  const double2 piv = B.pval[b];
+  const int pe = pv.x * nc + pv.y;
+  for (int t = threadIdx.x; t < l; t += blockDim.x) cij[t] = slot(B, b, t, nr, nc)[pe];
+  __syncthreads();
+  double2* dl = B.D + ((size_t)b * B.cap + l) * B.Ls;
+  double dn = 0.0;
+  for (int k = threadIdx.x; k < B.Ls; k += blockDim.x) {
+    double2 v = dl[k];
+    for (int t = 0; t < l; ++t) v = csub(v, cmul(cij[t], B.D[((size_t)b * B.cap + t) * B.Ls + k]));
+    v = cdiv(v, piv);
+    dl[k] = v;
+    dn += cabs2(v);
+  }
+  dn = block_sum(dn, sh);
+  double cross = 0.0;  // 2 Re sum_t <C_t,C_l> <d_t,d_l>
+  for (int t = 0; t < l; ++t) {
+    const double2* dt = B.D + ((size_t)b * B.cap + t) * B.Ls;
+    double re = 0.0, im = 0.0;
+    for (int k = threadIdx.x; k < B.Ls; k += blockDim.x) {
+      const double2 a = dt[k], c = dl[k];
+      re += a.x * c.x + a.y * c.y;
+      im += a.x * c.y - a.y * c.x;
+    }
+    re = block_sum(re, sh);
+    im = block_sum(im, sh);
+    const double2 gc = B.gramc[(size_t)b * B.cap + t];
+    cross += 2.0 * (gc.x * re - gc.y * im);
+  }
+  // next slice: argmax |d_l[k]| over unused k, smallest k on ties
+  unsigned* used = B.used + (size_t)b * B.words;
+  const int kc = B.kcur[b];
+  double best = -1.0;
+  int bidx = 0x7fffffff;
+  for (int k = threadIdx.x; k < B.Ls; k += blockDim.x) {
+    const bool u = (k == kc) || ((used[k >> 5] >> (k & 31)) & 1u);
+    if (u) continue;
+    const double a = cabs2(dl[k]);
+    if (a > best || (a == best && k < bidx)) { best = a; bidx = k; }
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, bidx, o);
+    if (ob > best || (ob == best && oi < bidx)) { best = ob; bidx = oi; }
+  }
+  if (lane == 0) { s_best[warp] = best; s_bidx[warp] = bidx; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int nw = blockDim.x >> 5;
+    for (int w2 = 1; w2 < nw; ++w2)
+      if (s_best[w2] > best || (s_best[w2] == best && s_bidx[w2] < bidx)) { best = s_best[w2]; bidx = s_bidx[w2]; }
+    used[kc >> 5] |= 1u << (kc & 31);
+    const double n2 = B.norm2[b] + cross + B.cn2[b] * dn;
+    B.norm2[b] = n2;
+    const int r = l + 1;
+    B.rank[b] = r;
+    const bool small = sqrt(B.cn2[b]) * sqrt(dn) <= B.eps * sqrt(fmax(n2, 0.0));
+    const bool all = (r >= B.Ls) || bidx == 0x7fffffff;
+    bool done = small || all;
+    if (!done && r >= B.cap) {
+      atomicAdd(&B.counters[1], 1);
+      done = true;
+    }
+    if (done) {
+      B.active[b] = 0;
+      atomicSub(&B.counters[0], 1);
+    } else {
+      B.kcur[b] = bidx;
+    }
+  }
+}
+
+__global__ void k_maca_init(int n, int words, int* rank, int* active, int* kcur, double* norm2,
+                            unsigned* used) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= n) return;
+  rank[b] = 0;
+  active[b] = 1;
+  kcur[b] = 0;
+  norm2[b] = 0.0;
+  for (int w = 0; w < words; ++w) used[(size_t)b * words + w] = 0u;
+}
+
+static Geom geom_from(const cqm_handle* h) {
+  Geom g;
+  g.M = h->M; g.tri = h->tri.p; g.P = h->P.p; g.area = h->area.p; g.cen = h->cen.p; g.diam = h->diam.p;
+  return g;
+}
+
+// Runs MACA on one list of blocks; fills rank (device and host).
+static int run_maca(cqm_handle* h, int kind, int n, const int2* rc, DArray<double2>& C,
+                    DArray<double2>& D, DArray<int>& rank, const int64_t* d_off, size_t c_entries,
+                    std::vector<int>& h_rank) {
+  h_rank.assign(n, 0);
+  if (n == 0) return CQM_OK;
+  const int Ls = h->Ls, cap = h->rank_cap;
+  CQM_TRY(C.allocate(h->alloc, c_entries));
+  CQM_TRY(D.allocate(h->alloc, (size_t)n * cap * Ls));
+  CQM_TRY(rank.allocate(h->alloc, n));
+  DArray<int> active, kcur, counters;
+  DArray<int2> piv;
+  DArray<double2> pval, gramc;
+  DArray<double> cn2, norm2;
+  DArray<unsigned> used;
+  const int words = (Ls + 31) / 32;
+  auto release = [&]() {
+    active.free(h->alloc); kcur.free(h->alloc); counters.free(h->alloc); piv.free(h->alloc);
+    pval.free(h->alloc); gramc.free(h->alloc); cn2.free(h->alloc); norm2.free(h->alloc);
+    used.free(h->alloc);
+  };
+  int st = CQM_OK;
+#define MT(e) do { if ((st = (e)) != CQM_OK) { release(); return st; } } while (0)
+  MT(active.allocate(h->alloc, n));
+  MT(kcur.allocate(h->alloc, n));
+  MT(counters.allocate(h->alloc, 4));
+  MT(piv.allocate(h->alloc, n));
+  MT(pval.allocate(h->alloc, n));
+  MT(gramc.allocate(h->alloc, (size_t)n * cap));
+  MT(cn2.allocate(h->alloc, n));
+  MT(norm2.allocate(h->alloc, n));
+  MT(used.allocate(h->alloc, (size_t)n * words));
+  MacaBlocks B;
+  B.n = n; B.kind = kind; B.Ls = Ls; B.cap = cap; B.p = h->p; B.m = h->m;
+  B.rc = rc; B.begin = h->node_begin.p; B.end = h->node_end.p; B.perm = h->perm.p;
+  B.cheb = h->cheb.p; B.off = d_off; B.C = C.p; B.D = D.p; B.rank = rank.p;
+  B.active = active.p; B.kcur = kcur.p; B.piv = piv.p; B.pval = pval.p; B.cn2 = cn2.p;
+  B.norm2 = norm2.p; B.gramc = gramc.p; B.used = used.p; B.words = words;
+  B.counters = counters.p; B.eps = h->params.aca_eps;
+  cudaStream_t S = h->stream;
+  const Geom g = geom_from(h);
+  {
+    ProfScope ps_(h, CQM_K_MACA_FINALIZE);
+    k_maca_init<<<grid_for(n, 256), 256, 0, S>>>(n, words, rank.p, active.p, kcur.p, norm2.p, used.p);
+  }
+  int hc[2] = {n, 0};
+  cudaMemcpyAsync(counters.p, hc, 2 * sizeof(int), cudaMemcpyHostToDevice, S);
+  for (int step = 0; step < cap; ++step) {
+    {
+      ProfScope ps_(h, CQM_K_MACA_SLICE);
+      k_maca_slice<<<n, 256, 0, S>>>(B, g, h->quad, h->s.p);
+    }
+    {
+      ProfScope ps_(h, CQM_K_MACA_PIVOT);
+      k_maca_pivot<<<n, 256, 0, S>>>(B);
+    }
+    {
+      ProfScope ps_(h, CQM_K_MACA_FIBRE);
+      k_maca_fibre<<<n, 256, 0, S>>>(B, g, h->quad, h->s.p);
+    }
+    {
+      ProfScope ps_(h, CQM_K_MACA_FINALIZE);
+      k_maca_finalize<<<n, 256, 0, S>>>(B);
+    }
+    if (cudaGetLastError() != cudaSuccess) {
+      set_last_error("maca launch failed");
+      release();
+      return CQM_ECUDA;
+    }
+    if ((step & 3) == 3 || step == cap - 1) {
+      cudaMemcpyAsync(hc, counters.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, S);
+      if (cudaStreamSynchronize(S) != cudaSuccess) {
+        set_last_error("maca failed");
+        release();
+        return CQM_ECUDA;
+      }
+      if (hc[0] == 0) break;
+    }
+  }
+  cudaMemcpyAsync(hc, counters.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, S);
+  cudaMemcpyAsync(h_rank.data(), rank.p, sizeof(int) * n, cudaMemcpyDeviceToHost, S);
+  cudaError_t e = cudaStreamSynchronize(S);
+  release();
+  if (e != cudaSuccess) {
+    set_last_error(std::string("maca: ") + cudaGetErrorString(e));
+    return CQM_ECUDA;
+  }
+  if (hc[1] > 0) {
+    set_last_error(std::to_string(hc[1]) + " blocks need more than rank_cap = " +
+                   std::to_string(cap) + " MACA terms");
+    return CQM_ECAPACITY;
+  }
+  return CQM_OK;
+#undef MT
+}
+
+int build_maca(cqm_handle* h) {
+  // near C slots: cap entries of #r x #c per block
+  h->h_near_off.resize(h->n_near);
+  int64_t total = 0;
+  for (int b = 0; b < h->n_near; ++b) {
+    h->h_near_off[b] = total;
+    const int2 rc = h->h_near[b];
+    total += (int64_t)h->rank_cap * (h->h_end[rc.x] - h->h_begin[rc.x]) * (h->h_end[rc.y] - h->h_begin[rc.y]);
+  }
+  CQM_TRY(h->near_off.allocate(h->alloc, std::max(1, h->n_near)));
+  CQM_CUDA_TRY(cudaMemcpyAsync(h->near_off.p, h->h_near_off.data(), sizeof(int64_t) * h->n_near,
+                               cudaMemcpyHostToDevice, h->stream));
+  CQM_TRY(run_maca(h, 0, h->n_near, h->near_rc.p, h->nearC, h->nearD, h->near_rank, h->near_off.p,
+                   (size_t)std::max<int64_t>(total, 1), h->h_near_rank));
+  CQM_TRY(run_maca(h, 1, h->n_far, h->far_rc.p, h->farC, h->farD, h->far_rank, nullptr,
+                   (size_t)h->n_far * h->rank_cap * h->p * h->p, h->h_far_rank));
+  cqm_setup_info& I = h->info;
+  I.near_entries = 0;
+  I.rank_sum_near = I.rank_sum_far = 0;
+  I.rank_max = 0;
+  for (int b = 0; b < h->n_near; ++b) {
+    const int2 rc = h->h_near[b];
+    I.near_entries += (int64_t)(h->h_end[rc.x] - h->h_begin[rc.x]) * (h->h_end[rc.y] - h->h_begin[rc.y]);
+    I.rank_sum_near += h->h_near_rank[b];
+    I.rank_max = std::max(I.rank_max, h->h_near_rank[b]);
+  }
+  for (int b = 0; b < h->n_far; ++b) {
+    I.rank_sum_far += h->h_far_rank[b];
+    I.rank_max = std::max(I.rank_max, h->h_far_rank[b]);
+  }
+  I.far_coupling = (int64_t)h->n_far * h->p * h->p;
+  return CQM_OK;
+}
+
+}  // namespace cqm
