@@ -95,6 +95,16 @@ typedef struct cqm_params {
   int32_t gmres_max_iter; /* total Arnoldi steps cap                       [3000] */
   double gmres_tol;       /* relative residual target ||r_l|| <= tol ||ghat_l|| [1e-13] */
   int32_t profile;        /* nonzero: time every kernel launch with CUDA events [0] */
+  int32_t precond;        /* H2MACA: right-precondition GMRES with the inverses of the
+                             leaf diagonal near blocks, per frequency     [1]   */
+  int32_t inner_fp32;     /* H2MACA: Arnoldi steps apply an FP32 copy of the operator;
+                             every restart recomputes the FP64 residual,
+                             so results keep FP64 accuracy                [1]   */
+  double inner_rtol;      /* with inner_fp32: a cycle ends once its residual
+                             estimate fell by this factor                 [1e-5] */
+  int32_t exact_ff;       /* H2MACA: the FP64-accurate apply (residuals) runs its
+                             near-field and coupling contractions in float-float
+                             arithmetic (~48 bits) on the FP32 pipes; 0 = FP64 [1] */
   const cqm_allocator* allocator; /* NULL: stream-ordered CUDA pool        [NULL] */
 } cqm_params;
 
@@ -111,6 +121,7 @@ typedef struct cqm_setup_info {
   double R;
   int64_t device_bytes;         /* device memory held by the handle */
   double t_geometry_ms, t_tree_ms, t_bases_ms, t_assembly_ms; /* stage times (CUDA events) */
+  int64_t near_rank_entries;    /* sum over near blocks of rank * #r * #c */
 } cqm_setup_info;
 
 /* Per-solve summary. */
@@ -226,10 +237,10 @@ int cqm_bem_inverse_transform(cqm_handle* h, const double* qhat, double* q, int3
 #define CQM_K_MACA_PIVOT     7
 #define CQM_K_MACA_FIBRE     8
 #define CQM_K_MACA_FINALIZE  9
-#define CQM_K_NEAR_APPLY     10
+#define CQM_K_NEAR_APPLY     10   /* near field of the inner (FP32) apply, or of the FP64 apply without inner_fp32 */
 #define CQM_K_LEAF_FORWARD   11
 #define CQM_K_UPSWEEP        12
-#define CQM_K_FAR_COUPLING   13
+#define CQM_K_FAR_COUPLING   13   /* far coupling of the inner (FP32) apply, or of the FP64 apply without inner_fp32 */
 #define CQM_K_DOWNSWEEP      14
 #define CQM_K_LEAF_BACKWARD  15
 #define CQM_K_DENSE_APPLY    16
@@ -238,7 +249,10 @@ int cqm_bem_inverse_transform(cqm_handle* h, const double* qhat, double* q, int3
 #define CQM_K_FORWARD_DFT    19
 #define CQM_K_INVERSE_DFT    20
 #define CQM_K_RHS            21
-#define CQM_K_COUNT          22
+#define CQM_K_PRECOND        22
+#define CQM_K_NEAR_EXACT     23   /* near field of the FP64-accurate apply (residuals) */
+#define CQM_K_FAR_EXACT      24   /* far coupling of the FP64-accurate apply (residuals) */
+#define CQM_K_COUNT          25
 
 /* Turn per-launch event timing on (nonzero) or off; either way the counters
  * are reset.  Timing adds one event pair per launch on the handle's stream. */

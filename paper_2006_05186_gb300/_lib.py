@@ -31,7 +31,7 @@ EXPORTED = [
     "cqm_bem_solve_frequencies", "cqm_bem_forward_transform", "cqm_bem_inverse_transform",
     "cqm_bem_profile", "cqm_bem_profile_read", "cqm_bem_kernel_name",
 ]
-K_COUNT = 22
+K_COUNT = 25
 
 
 class cqm_mesh(C.Structure):
@@ -52,7 +52,9 @@ class cqm_params(C.Structure):
         ("near_ratio", C.c_double), ("n_min", C.c_int32), ("eta", C.c_double),
         ("cheb_m", C.c_int32), ("aca_eps", C.c_double), ("rank_cap", C.c_int32),
         ("gmres_restart", C.c_int32), ("gmres_max_iter", C.c_int32), ("gmres_tol", C.c_double),
-        ("profile", C.c_int32), ("allocator", C.POINTER(cqm_allocator)),
+        ("profile", C.c_int32), ("precond", C.c_int32), ("inner_fp32", C.c_int32),
+        ("inner_rtol", C.c_double), ("exact_ff", C.c_int32),
+        ("allocator", C.POINTER(cqm_allocator)),
     ]
 
 
@@ -64,7 +66,7 @@ class cqm_setup_info(C.Structure):
         ("far_coupling", C.c_int64), ("rank_sum_near", C.c_int64), ("rank_sum_far", C.c_int64),
         ("rank_max", C.c_int32), ("R", C.c_double), ("device_bytes", C.c_int64),
         ("t_geometry_ms", C.c_double), ("t_tree_ms", C.c_double), ("t_bases_ms", C.c_double),
-        ("t_assembly_ms", C.c_double),
+        ("t_assembly_ms", C.c_double), ("near_rank_entries", C.c_int64),
     ]
 
 

@@ -59,6 +59,10 @@ int cqm_params_default(cqm_params* p) {
   p->gmres_max_iter = 3000;
   p->gmres_tol = 1e-13;
   p->profile = 0;
+  p->precond = 1;
+  p->inner_fp32 = 1;
+  p->inner_rtol = 1e-5;
+  p->exact_ff = 1;
   p->allocator = nullptr;
   return CQM_OK;
 }
@@ -93,6 +97,9 @@ int cqm_bem_destroy(cqm_handle* h) {
   h->near_rank.free(A); h->far_rank.free(A); h->near_off.free(A);
   h->nearC.free(A); h->nearD.free(A); h->farC.free(A); h->farD.free(A);
   h->xhat.free(A); h->yhat.free(A); h->d_leaves.free(A); h->d_far_rows.free(A);
+  h->Pinv.free(A);
+  h->nearC_f.free(A); h->nearD_f.free(A); h->farC_f.free(A); h->farD_f.free(A);
+  h->xhat_f.free(A); h->yhat_f.free(A); h->Uleaf_f.free(A); h->Etr_f.free(A);
   cudaStreamSynchronize(h->stream);
   prof_release(h);
   delete h;
@@ -132,7 +139,8 @@ int cqm_bem_setup(const cqm_mesh* mesh, double dt, int32_t N, int32_t bdf_order,
       p.g_near < 1 || p.g_near > 12 || !(p.near_ratio >= 0.0) || p.n_min < 1 || !(p.eta > 0.0) ||
       p.cheb_m < 1 || p.cheb_m > 4 || !(p.aca_eps > 0.0) || p.rank_cap < 1 ||
       (p.mode == CQM_MODE_H2MACA && p.n_min > 32) ||
-      p.gmres_restart < 1 || p.gmres_max_iter < 1 || !(p.gmres_tol > 0.0)) {
+      p.gmres_restart < 1 || p.gmres_max_iter < 1 || !(p.gmres_tol > 0.0) ||
+      !(p.inner_rtol >= 0.0 && p.inner_rtol < 1.0)) {
     set_last_error("parameter out of range");
     return CQM_EINVAL;
   }
@@ -173,6 +181,11 @@ int cqm_bem_setup(const cqm_mesh* mesh, double dt, int32_t N, int32_t bdf_order,
       if ((st = build_bases(h)) != CQM_OK) break;
       cudaEventRecord(ev[3], h->stream);
       if ((st = build_maca(h)) != CQM_OK) break;
+      if (p.precond && (st = build_precond(h)) != CQM_OK) break;
+      if (p.inner_fp32) {
+        if ((st = build_f32_copy(h)) != CQM_OK) break;
+        h->use_f32 = true;
+      }
     }
     cudaEventRecord(ev[4], h->stream);
     cudaError_t e = cudaStreamSynchronize(h->stream);
@@ -535,7 +548,7 @@ static const char* k_names[CQM_K_COUNT] = {
     "geometry", "tree", "partition", "bases", "dense_assemble", "entries", "maca_slice",
     "maca_pivot", "maca_fibre", "maca_finalize", "near_apply", "leaf_forward", "upsweep",
     "far_coupling", "downsweep", "leaf_backward", "dense_apply", "arnoldi", "gmres_other",
-    "forward_dft", "inverse_dft", "rhs"};
+    "forward_dft", "inverse_dft", "rhs", "precond", "near_exact", "far_exact"};
 
 const char* cqm_bem_kernel_name(int32_t id) {
   return (id >= 0 && id < CQM_K_COUNT) ? k_names[id] : "";

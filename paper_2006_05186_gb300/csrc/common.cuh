@@ -65,6 +65,32 @@ __device__ __forceinline__ void cfma(double2& a, double2 b, double2 c) {
   a.y = fma(b.x, c.y, fma(b.y, c.x, a.y));
 }
 
+// float2 versions (storage and arithmetic of the FP32 inner operator)
+__host__ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ __forceinline__ float2 cadd(float2 a, float2 b) {
+  return make_float2(a.x + b.x, a.y + b.y);
+}
+__device__ __forceinline__ void cfma(float2& a, float2 b, float2 c) {
+  a.x = fmaf(b.x, c.x, fmaf(-b.y, c.y, a.x));
+  a.y = fmaf(b.x, c.y, fmaf(b.y, c.x, a.y));
+}
+
+// Complex type of a real type.
+template <class R> struct Cplx;
+template <> struct Cplx<double> { using type = double2; };
+template <> struct Cplx<float> { using type = float2; };
+
+template <class T> __device__ __forceinline__ T cz();
+template <> __device__ __forceinline__ double2 cz<double2>() { return make_double2(0.0, 0.0); }
+template <> __device__ __forceinline__ float2 cz<float2>() { return make_float2(0.f, 0.f); }
+
+__device__ __forceinline__ double2 to_c(double2 v, double2*) { return v; }
+__device__ __forceinline__ float2 to_c(double2 v, float2*) { return make_float2((float)v.x, (float)v.y); }
+__device__ __forceinline__ double2 to_d(double2 v) { return v; }
+__device__ __forceinline__ double2 to_d(float2 v) { return make_double2(v.x, v.y); }
+
 // ------------------------------------------------------------ reductions ----
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll

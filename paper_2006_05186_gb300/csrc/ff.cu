@@ -1,0 +1,214 @@
+// FP64-accurate application of the compressed operator in float-float
+// arithmetic on the FP32 pipes (GB300 runs FP32 about 60x faster than FP64).
+// A float-float number is an unevaluated sum hi + lo of two floats; products
+// use the FMA-based exact product (the error of hi*hi is fma(a, b, -a*b)) and
+// sums Knuth's error-free TwoSum, which together keep about 48 significant
+// bits.  The near-field and far-field coupling contractions (the bulk of the
+// flops of eq. lrfinal) run this way; the H^2 transforms, which are cheap,
+// stay in FP64.  Inputs and outputs are FP64; the factors are read from their
+// FP64 storage and split while they are staged in shared memory.
+#include <algorithm>
+#include <vector>
+
+#include "handle.cuh"
+
+namespace cqm {
+
+struct ffc {  // complex float-float: (re_hi, im_hi, re_lo, im_lo)
+  float rh, ih, rl, il;
+};
+
+__device__ __forceinline__ ffc ffc_zero() { return {0.f, 0.f, 0.f, 0.f}; }
+
+__device__ __forceinline__ ffc ffc_from(double2 v) {
+  const float rh = (float)v.x, ih = (float)v.y;
+  return {rh, ih, (float)(v.x - (double)rh), (float)(v.y - (double)ih)};
+}
+
+__device__ __forceinline__ double2 ffc_to(const ffc& a) {
+  return make_double2((double)a.rh + (double)a.rl, (double)a.ih + (double)a.il);
+}
+
+// (sh, sl) += (ah, al) * (bh, bl)
+__device__ __forceinline__ void ff_mac(float& sh, float& sl, float ah, float al, float bh, float bl) {
+  const float p = __fmul_rn(ah, bh);
+  float e = fmaf(ah, bh, -p);  // exact low part of ah*bh
+  e = fmaf(ah, bl, e);
+  e = fmaf(al, bh, e);
+  const float t = __fadd_rn(sh, p);  // TwoSum(sh, p)
+  const float bb = __fsub_rn(t, sh);
+  const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bb)), __fsub_rn(p, bb));
+  sl = __fadd_rn(sl, __fadd_rn(err, e));
+  sh = t;
+}
+
+// z += a * b (complex)
+__device__ __forceinline__ void ffc_mac(ffc& z, const ffc& a, const ffc& b) {
+  ff_mac(z.rh, z.rl, a.rh, a.rl, b.rh, b.rl);
+  ff_mac(z.rh, z.rl, -a.ih, -a.il, b.ih, b.il);
+  ff_mac(z.ih, z.il, a.rh, a.rl, b.ih, b.il);
+  ff_mac(z.ih, z.il, a.ih, a.il, b.rh, b.rl);
+}
+
+// keep |lo| below half an ulp of hi (FastTwoSum)
+__device__ __forceinline__ void ffc_renorm(ffc& z) {
+  float t = __fadd_rn(z.rh, z.rl);
+  z.rl = __fsub_rn(z.rl, __fsub_rn(t, z.rh));
+  z.rh = t;
+  t = __fadd_rn(z.ih, z.il);
+  z.il = __fsub_rn(z.il, __fsub_rn(t, z.ih));
+  z.ih = t;
+}
+
+constexpr int LCF = 32;
+constexpr int PMAX = 64;
+
+// Near field in float-float: one block per leaf row cluster.
+__global__ void __launch_bounds__(256) k_near_apply_ff(
+    int M, int Ls, int cap, const int* __restrict__ leaves, const int* __restrict__ rowptr,
+    const int2* __restrict__ blocks, const int* __restrict__ rank, const int64_t* __restrict__ off,
+    const double2* __restrict__ Cn, const double2* __restrict__ Dn, const int* __restrict__ begin,
+    const int* __restrict__ end, const int* __restrict__ perm, const double2* __restrict__ X,
+    double2* __restrict__ Y) {
+  __shared__ ffc Xs[32][LCF];
+  __shared__ ffc Cs[32 * 32];
+  __shared__ ffc Ds[LCF];
+  const int r = leaves[blockIdx.x];
+  const int rb = begin[r], nr = end[r] - rb;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int l0 = 0; l0 < Ls; l0 += LCF) {
+    ffc acc[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) acc[k] = ffc_zero();
+    for (int bi = rowptr[r]; bi < rowptr[r + 1]; ++bi) {
+      const int c = blocks[bi].y;
+      const int cb = begin[c], nc = end[c] - cb;
+      __syncthreads();
+      for (int t = threadIdx.x; t < nc * LCF; t += blockDim.x) {
+        const int j = t / LCF, l = t - j * LCF;
+        Xs[j][l] = (l0 + l < Ls) ? ffc_from(X[(size_t)(l0 + l) * M + perm[cb + j]]) : ffc_zero();
+      }
+      const int rk = rank[bi];
+      for (int tt = 0; tt < rk; ++tt) {
+        __syncthreads();
+        const double2* Ct = Cn + off[bi] + (size_t)tt * nr * nc;
+        for (int t = threadIdx.x; t < nr * nc; t += blockDim.x) Cs[t] = ffc_from(Ct[t]);
+        if (threadIdx.x < LCF)
+          Ds[threadIdx.x] = (l0 + threadIdx.x < Ls)
+                                ? ffc_from(Dn[((size_t)bi * cap + tt) * Ls + l0 + threadIdx.x])
+                                : ffc_zero();
+        __syncthreads();
+        const ffc d = Ds[lane];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int i = w + 8 * k;
+          if (i < nr) {
+            ffc z = ffc_zero();
+            for (int j = 0; j < nc; ++j) ffc_mac(z, Cs[i * nc + j], Xs[j][lane]);
+            ffc_renorm(z);
+            ffc_mac(acc[k], d, z);
+          }
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) ffc_renorm(acc[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int i = w + 8 * k;
+      if (i < nr && l0 + lane < Ls) Y[(size_t)(l0 + lane) * M + perm[rb + i]] = ffc_to(acc[k]);
+    }
+  }
+}
+
+// Far coupling in float-float: one block per row cluster owning far blocks;
+// yhat_r (FP64) += sum_b sum_t D_b[t] C_{b,t} xhat_c.
+__global__ void __launch_bounds__(256) k_far_coupling_ff(int Ls, int p, int cap,
+                                                         const int* __restrict__ rows,
+                                                         const int* __restrict__ rowptr,
+                                                         const int2* __restrict__ blocks,
+                                                         const int* __restrict__ rank,
+                                                         const double2* __restrict__ Cf,
+                                                         const double2* __restrict__ Df,
+                                                         const double2* __restrict__ xhat,
+                                                         double2* __restrict__ yhat) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  ffc* Xs = (ffc*)smraw;        // p x LCF
+  ffc* Cs = Xs + PMAX * LCF;    // p x p
+  __shared__ ffc Ds[LCF];
+  const int r = rows[blockIdx.x];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int l0 = 0; l0 < Ls; l0 += LCF) {
+    ffc acc[PMAX / 8];
+#pragma unroll
+    for (int k = 0; k < PMAX / 8; ++k) acc[k] = ffc_zero();
+    for (int bi = rowptr[r]; bi < rowptr[r + 1]; ++bi) {
+      const int c = blocks[bi].y;
+      __syncthreads();
+      for (int t = threadIdx.x; t < p * LCF; t += blockDim.x) {
+        const int nu = t / LCF, l = t - nu * LCF;
+        Xs[t] = (l0 + l < Ls) ? ffc_from(xhat[((size_t)c * p + nu) * Ls + l0 + l]) : ffc_zero();
+      }
+      const int rk = rank[bi];
+      for (int tt = 0; tt < rk; ++tt) {
+        __syncthreads();
+        const double2* Ct = Cf + ((size_t)bi * cap + tt) * p * p;
+        for (int t = threadIdx.x; t < p * p; t += blockDim.x) Cs[t] = ffc_from(Ct[t]);
+        if (threadIdx.x < LCF)
+          Ds[threadIdx.x] = (l0 + threadIdx.x < Ls)
+                                ? ffc_from(Df[((size_t)bi * cap + tt) * Ls + l0 + threadIdx.x])
+                                : ffc_zero();
+        __syncthreads();
+        const ffc d = Ds[lane];
+#pragma unroll
+        for (int k = 0; k < (int)(sizeof(acc) / sizeof(acc[0])); ++k) {
+          const int mu = w + 8 * k;
+          if (mu < p) {
+            ffc z = ffc_zero();
+            for (int nu = 0; nu < p; ++nu) ffc_mac(z, Cs[mu * p + nu], Xs[nu * LCF + lane]);
+            ffc_renorm(z);
+            ffc_mac(acc[k], d, z);
+            ffc_renorm(acc[k]);
+          }
+        }
+      }
+    }
+    if (l0 + lane < Ls)
+#pragma unroll
+      for (int k = 0; k < (int)(sizeof(acc) / sizeof(acc[0])); ++k) {
+        const int mu = w + 8 * k;
+        if (mu < p) {
+          double2* o = yhat + ((size_t)r * p + mu) * Ls + l0 + lane;
+          *o = cadd(*o, ffc_to(acc[k]));
+        }
+      }
+  }
+}
+
+static size_t coupling_smem_ff(int p) { return sizeof(ffc) * (PMAX * LCF + (size_t)p * p); }
+
+int setup_ff(cqm_handle* h) {
+  CQM_CUDA_TRY(cudaFuncSetAttribute(k_far_coupling_ff, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)coupling_smem_ff(h->p)));
+  return CQM_OK;
+}
+
+int near_apply_ff(cqm_handle* h, const double2* x, double2* y) {
+  ProfScope ps_(h, CQM_K_NEAR_EXACT);
+  k_near_apply_ff<<<(unsigned)h->h_leaves.size(), 256, 0, h->stream>>>(
+      h->M, h->Ls, h->rank_cap, h->d_leaves.p, h->near_rowptr.p, h->near_rc.p, h->near_rank.p,
+      h->near_off.p, h->nearC.p, h->nearD.p, h->node_begin.p, h->node_end.p, h->perm.p, x, y);
+  CQM_CHECK_LAUNCH();
+  return CQM_OK;
+}
+
+int far_coupling_ff(cqm_handle* h) {
+  ProfScope ps_(h, CQM_K_FAR_EXACT);
+  k_far_coupling_ff<<<(unsigned)h->h_far_rows.size(), 256, coupling_smem_ff(h->p), h->stream>>>(
+      h->Ls, h->p, h->rank_cap, h->d_far_rows.p, h->far_rowptr.p, h->far_rc.p, h->far_rank.p,
+      h->farC.p, h->farD.p, h->xhat.p, h->yhat.p);
+  CQM_CHECK_LAUNCH();
+  return CQM_OK;
+}
+
+}  // namespace cqm

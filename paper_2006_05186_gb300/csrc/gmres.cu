@@ -15,8 +15,8 @@ namespace cqm {
 
 struct GmresWork {
   int m = 0;
-  DArray<double2> Vb, r, H, sn, g, y;
-  DArray<double> cs, bnorm, beta;
+  DArray<double2> Vb, r, H, sn, g, y, Z;
+  DArray<double> cs, bnorm, beta, thr;
   DArray<int> active, kdim, converged, counters;
   int* h_counters = nullptr;  // pinned
 };
@@ -27,7 +27,7 @@ struct GmresWork {
 __global__ void k_restart(int M, int m, const double2* __restrict__ b, const double2* y,
                           double2* __restrict__ r, double2* __restrict__ V0, double* bnorm,
                           double* beta, int* active, int* converged, double2* g, double tol,
-                          int first, int* counters) {
+                          double rtol, double* thr, int first, int* counters) {
   __shared__ double sh[32];
   const int l = blockIdx.x;
   const double2* bl = b + (size_t)l * M;
@@ -51,6 +51,7 @@ __global__ void k_restart(int M, int m, const double2* __restrict__ b, const dou
   const bool done = !(bt > tol * bn) || bn == 0.0;
   if (threadIdx.x == 0) {
     beta[l] = bt;
+    thr[l] = fmax(tol * bn, rtol * bt);  // this cycle stops at thr (FP64 residual decides convergence)
     converged[l] = done ? 1 : 0;
     active[l] = done ? 0 : 1;
     if (!done) atomicAdd(&counters[0], 1);
@@ -69,8 +70,7 @@ template <int KB>
 __global__ void k_arnoldi(int M, int Ls, int m, int j, double2* __restrict__ Vb,
                           double2* __restrict__ H, double* __restrict__ cs,
                           double2* __restrict__ sn, double2* __restrict__ g,
-                          const double* __restrict__ bnorm, int* active, int* kdim, double tol,
-                          int* counters) {
+                          const double* __restrict__ thr, int* active, int* kdim, int* counters) {
   __shared__ double sh[32];
   __shared__ double2 hloc[64];
   const int l = blockIdx.x;
@@ -166,21 +166,26 @@ __global__ void k_arnoldi(int M, int Ls, int m, int j, double2* __restrict__ Vb,
     gl[j + 1] = make_double2(-(s.x * gj.x + s.y * gj.y), -(s.x * gj.y - s.y * gj.x));  // -conj(s) g_j
     kdim[l] = j + 1;
     const double res = sqrt(cabs2(gl[j + 1]));
-    if (!(res > tol * bnorm[l]) || hn == 0.0) {
+    if (!(res > thr[l]) || hn == 0.0) {
       active[l] = 0;
       atomicSub(&counters[0], 1);
     }
   }
 }
 
-// Back substitution R y = g (k = kdim[l]) and x_l += V y; one block per l.
+// Back substitution R y = g (k = kdim[l]); then x_l += V y (add = 1) or
+// x_l = V y (add = 0, zero for frequencies without an update); one block per l.
 __global__ void k_update_x(int M, int Ls, int m, const double2* __restrict__ Vb,
                            const double2* __restrict__ H, const double2* __restrict__ g,
                            const int* __restrict__ kdim, const int* __restrict__ converged,
-                           double2* __restrict__ y, double2* __restrict__ x) {
+                           double2* __restrict__ y, double2* __restrict__ x, int add) {
   const int l = blockIdx.x;
   const int k = kdim[l];
-  if (converged[l] || k == 0) return;
+  if (converged[l] || k == 0) {
+    if (!add)
+      for (int i = threadIdx.x; i < M; i += blockDim.x) x[(size_t)l * M + i] = make_double2(0.0, 0.0);
+    return;
+  }
   const double2* Hl = H + (size_t)l * (m + 1) * m;
   double2* yl = y + (size_t)l * m;
   if (threadIdx.x == 0) {
@@ -193,39 +198,38 @@ __global__ void k_update_x(int M, int Ls, int m, const double2* __restrict__ Vb,
   __syncthreads();
   const size_t stride = (size_t)Ls * M;
   for (int i = threadIdx.x; i < M; i += blockDim.x) {
-    double2 xi = x[(size_t)l * M + i];
+    double2 xi = add ? x[(size_t)l * M + i] : make_double2(0.0, 0.0);
     for (int c = 0; c < k; ++c) cfma(xi, yl[c], Vb[(size_t)c * stride + (size_t)l * M + i]);
     x[(size_t)l * M + i] = xi;
   }
 }
 
-__global__ void k_true_residual(int M, const double2* __restrict__ b, const double2* __restrict__ Ax,
-                                const double* __restrict__ bnorm, double* rel) {
-  __shared__ double sh[32];
-  const int l = blockIdx.x;
-  double s = 0.0;
-  for (int i = threadIdx.x; i < M; i += blockDim.x)
-    s += cabs2(csub(b[(size_t)l * M + i], Ax[(size_t)l * M + i]));
-  s = block_sum(s, sh);
-  if (threadIdx.x == 0) rel[l] = bnorm[l] > 0 ? sqrt(s) / bnorm[l] : 0.0;
+__global__ void k_axpy(int64_t n, const double2* __restrict__ z, double2* __restrict__ x) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) x[i] = cadd(x[i], z[i]);
 }
 
 int gmres_solve(cqm_handle* h, const double2* d_b, double2* d_x, cqm_solve_info* info) {
   const int M = h->M, Ls = h->Ls;
   const int m = std::max(1, std::min(h->params.gmres_restart, 64));
   const double tol = h->params.gmres_tol;
+  // a cycle with an inexact (FP32) inner operator can only gain about that
+  // many digits; the FP64 residual of the next restart continues from there
+  const double rtol = h->use_f32 ? h->params.inner_rtol : 0.0;
   Allocator& A = h->alloc;
   GmresWork W;
   int st = CQM_OK;
   auto cleanup = [&]() {
-    W.Vb.free(A); W.r.free(A); W.H.free(A); W.sn.free(A); W.g.free(A); W.y.free(A);
-    W.cs.free(A); W.bnorm.free(A); W.beta.free(A); W.active.free(A); W.kdim.free(A);
+    W.Vb.free(A); W.r.free(A); W.Z.free(A); W.H.free(A); W.sn.free(A); W.g.free(A); W.y.free(A);
+    W.cs.free(A); W.bnorm.free(A); W.beta.free(A); W.thr.free(A); W.active.free(A); W.kdim.free(A);
     W.converged.free(A); W.counters.free(A);
     if (W.h_counters) cudaFreeHost(W.h_counters);
   };
 #define GM_TRY(e) do { st = (e); if (st != CQM_OK) { cleanup(); return st; } } while (0)
   GM_TRY(W.Vb.allocate(A, (size_t)(m + 1) * Ls * M));
   GM_TRY(W.r.allocate(A, (size_t)Ls * M));
+  const bool pre = h->use_precond;
+  if (pre) GM_TRY(W.Z.allocate(A, (size_t)Ls * M));
   GM_TRY(W.H.allocate(A, (size_t)Ls * (m + 1) * m));
   GM_TRY(W.sn.allocate(A, (size_t)Ls * m));
   GM_TRY(W.g.allocate(A, (size_t)Ls * (m + 1)));
@@ -233,6 +237,7 @@ int gmres_solve(cqm_handle* h, const double2* d_b, double2* d_x, cqm_solve_info*
   GM_TRY(W.cs.allocate(A, (size_t)Ls * m));
   GM_TRY(W.bnorm.allocate(A, Ls));
   GM_TRY(W.beta.allocate(A, Ls));
+  GM_TRY(W.thr.allocate(A, Ls));
   GM_TRY(W.active.allocate(A, Ls));
   GM_TRY(W.kdim.allocate(A, Ls));
   GM_TRY(W.converged.allocate(A, Ls));
@@ -268,8 +273,8 @@ int gmres_solve(cqm_handle* h, const double2* d_b, double2* d_x, cqm_solve_info*
     {
       ProfScope ps_(h, CQM_K_GMRES_OTHER);
       k_restart<<<Ls, 256, 0, S>>>(M, m, d_b, first ? nullptr : Ax, W.r.p, W.Vb.p, W.bnorm.p,
-                                   W.beta.p, W.active.p, W.converged.p, W.g.p, tol, first ? 1 : 0,
-                                   W.counters.p);
+                                   W.beta.p, W.active.p, W.converged.p, W.g.p, tol, rtol, W.thr.p,
+                                   first ? 1 : 0, W.counters.p);
     }
     GM_TRY(cu(cudaGetLastError()));
     GM_TRY(cu(cudaMemsetAsync(W.kdim.p, 0, sizeof(int) * Ls, S)));
@@ -282,11 +287,16 @@ int gmres_solve(cqm_handle* h, const double2* d_b, double2* d_x, cqm_solve_info*
       break;
     }
     for (int j = 0; j < m && iters < maxit; ++j) {
-      GM_TRY(apply_operator(h, W.Vb.p + (size_t)j * Ls * M, W.Vb.p + (size_t)(j + 1) * Ls * M));
+      if (pre) {
+        GM_TRY(apply_precond(h, W.Vb.p + (size_t)j * Ls * M, W.Z.p));
+        GM_TRY(apply_operator_inner(h, W.Z.p, W.Vb.p + (size_t)(j + 1) * Ls * M));
+      } else {
+        GM_TRY(apply_operator_inner(h, W.Vb.p + (size_t)j * Ls * M, W.Vb.p + (size_t)(j + 1) * Ls * M));
+      }
       {
         ProfScope ps_(h, CQM_K_ARNOLDI);
         k_arnoldi<8><<<Ls, 256, 0, S>>>(M, Ls, m, j, W.Vb.p, W.H.p, W.cs.p, W.sn.p, W.g.p,
-                                        W.bnorm.p, W.active.p, W.kdim.p, tol, W.counters.p);
+                                        W.thr.p, W.active.p, W.kdim.p, W.counters.p);
       }
       GM_TRY(cu(cudaGetLastError()));
       ++iters;
@@ -299,25 +309,26 @@ int gmres_solve(cqm_handle* h, const double2* d_b, double2* d_x, cqm_solve_info*
     {
       ProfScope ps_(h, CQM_K_GMRES_OTHER);
       k_update_x<<<Ls, 256, 0, S>>>(M, Ls, m, W.Vb.p, W.H.p, W.g.p, W.kdim.p, W.converged.p, W.y.p,
-                                    d_x);
+                                    pre ? W.r.p : d_x, pre ? 0 : 1);
+    }
+    if (pre) {
+      GM_TRY(apply_precond(h, W.r.p, W.Z.p));
+      ProfScope ps_(h, CQM_K_GMRES_OTHER);
+      k_axpy<<<grid_for((int64_t)Ls * M, 256), 256, 0, S>>>((int64_t)Ls * M, W.Z.p, d_x);
     }
     GM_TRY(cu(cudaGetLastError()));
     ++restarts;
   }
   cudaEventRecord(e1, S);
-  // final true residual
-  double2* Ax = W.Vb.p;
-  GM_TRY(apply_operator(h, d_x, Ax));
-  {
-    ProfScope ps_(h, CQM_K_GMRES_OTHER);
-    k_true_residual<<<Ls, 256, 0, S>>>(M, d_b, Ax, W.bnorm.p, W.beta.p);
-  }
-  GM_TRY(cu(cudaGetLastError()));
-  std::vector<double> rel(Ls);
+  // every exit follows a restart, which computed the true FP64 residual
+  // beta_l = ||ghat_l - V_l qhat_l|| at the returned solution
+  std::vector<double> rel(Ls), bn(Ls);
   std::vector<int> conv(Ls);
   GM_TRY(cu(cudaMemcpyAsync(rel.data(), W.beta.p, sizeof(double) * Ls, cudaMemcpyDeviceToHost, S)));
+  GM_TRY(cu(cudaMemcpyAsync(bn.data(), W.bnorm.p, sizeof(double) * Ls, cudaMemcpyDeviceToHost, S)));
   GM_TRY(cu(cudaMemcpyAsync(conv.data(), W.converged.p, sizeof(int) * Ls, cudaMemcpyDeviceToHost, S)));
   GM_TRY(cu(cudaStreamSynchronize(S)));
+  for (int l = 0; l < Ls; ++l) rel[l] = bn[l] > 0.0 ? rel[l] / bn[l] : 0.0;
   float ms = 0.f;
   cudaEventElapsedTime(&ms, e0, e1);
   cudaEventDestroy(e0);

