@@ -266,6 +266,40 @@ int cqm_bem_profile_read(cqm_handle* h, int32_t n, int64_t* launches, double* to
 /* Name of a kernel class ("" when out of range). */
 const char* cqm_bem_kernel_name(int32_t id);
 
+/* ---- Cluster tree without device allocation ----------------------------- */
+
+/* The paper has no counterpart to this call; it exists for callers of this
+ * library that may not call cudaMalloc (code inside another runtime that
+ * reserved the device memory up front, code on a path where an allocation,
+ * which can synchronise the device, is not allowed, or code whose memory is
+ * partitioned at start-up).
+ *
+ * Builds the same cluster tree as cqm_bem_setup (same splitting rule and
+ * breadth-first numbering) for a mesh already in device memory, without
+ * allocating: the kernel's scratch lives in a fixed array of about 2.3 MB
+ * that the library reserves on every GPU that loads it, for the life of the
+ * process.  Meshes of at most CQM_TREE_NOALLOC_MAX_TRIANGLES triangles;
+ * larger ones are rejected with CQM_EINVAL.
+ *
+ * xyz: nv x 3 float64, tri: nt x 3 int32 (device).  Outputs (device, owned by
+ * the caller): perm (nt), and per node begin, end, son0, son1 (-1 for
+ * leaves), parent (-1 for the root), level, each with room for 2 nt - 1
+ * entries, lo and hi (3 per node).  n_nodes (host) receives the node count.
+ * cuda_stream: a cudaStream_t (NULL: the legacy default stream); the call
+ * synchronises it before returning.
+ *
+ * The first call on a device looks the scratch address up (once per device,
+ * with that device current); make that first call before any stream capture.
+ * Every call shares the one scratch array per device, so calls whose work
+ * overlaps on the GPU (other threads, other streams) race: serialise them.
+ * Errors: CQM_EINVAL (NULL, sizes, vertex indices out of range -- checked on
+ * the device before any indexed read), CQM_ECUDA. */
+#define CQM_TREE_NOALLOC_MAX_TRIANGLES 65536
+int cqm_cluster_tree_noalloc(const double* xyz, int32_t nv, const int32_t* tri, int32_t nt,
+                             int32_t n_min, int32_t* perm, int32_t* begin, int32_t* end,
+                             int32_t* son0, int32_t* son1, int32_t* parent, int32_t* level,
+                             double* lo, double* hi, int32_t* n_nodes, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -30,6 +30,7 @@ EXPORTED = [
     "cqm_bem_get_block_factors", "cqm_bem_entries", "cqm_bem_apply",
     "cqm_bem_solve_frequencies", "cqm_bem_forward_transform", "cqm_bem_inverse_transform",
     "cqm_bem_profile", "cqm_bem_profile_read", "cqm_bem_kernel_name",
+    "cqm_cluster_tree_noalloc",
 ]
 K_COUNT = 25
 
@@ -124,6 +125,7 @@ def load(build_if_missing: bool = False):
         "cqm_bem_profile": (C.c_int, [vp, i32]),
         "cqm_bem_profile_read": (C.c_int, [vp, i32, vp, vp]),
         "cqm_bem_kernel_name": (C.c_char_p, [i32]),
+        "cqm_cluster_tree_noalloc": (C.c_int, [vp, i32, vp, i32, i32] + [vp] * 9 + [C.POINTER(i32), vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)

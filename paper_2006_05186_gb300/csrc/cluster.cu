@@ -471,3 +471,19 @@ int build_partition(cqm_handle* h) {
 }
 
 }  // namespace cqm
+
+namespace cqm {
+
+// The tree kernel on buffers the caller provides (scratch included); used by
+// the entry point that allocates no device memory.
+int launch_tree_kernel(int M, int n_min, int cap, const double* xyz, const int* tri,
+                       const double* cen, int* perm, int* tmp, int* begin, int* end, int* son0,
+                       int* son1, int* parent, int* level, double* lo, double* hi, int* split,
+                       int* counters, cudaStream_t stream) {
+  TreeOut T{perm, tmp, begin, end, son0, son1, parent, level, lo, hi, split, counters};
+  k_build_tree<<<1, 1024, 0, stream>>>(M, n_min, cap, xyz, tri, cen, T);
+  CQM_CHECK_LAUNCH();
+  return CQM_OK;
+}
+
+}  // namespace cqm

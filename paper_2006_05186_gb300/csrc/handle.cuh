@@ -105,6 +105,10 @@ int apply_dense(cqm_handle* h, const double2* x, double2* y);
 
 // cluster.cu
 int build_tree(cqm_handle* h);
+int launch_tree_kernel(int M, int n_min, int cap, const double* xyz, const int* tri,
+                       const double* cen, int* perm, int* tmp, int* begin, int* end, int* son0,
+                       int* son1, int* parent, int* level, double* lo, double* hi, int* split,
+                       int* counters, cudaStream_t stream);
 int build_partition(cqm_handle* h);
 
 // h2.cu
