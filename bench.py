@@ -275,9 +275,40 @@ def run_ours(args):
                 "d2h_bytes_per_step": int(L * M * 8)},
         "peaks_source": src,
     }
+    if args.dense_baseline:
+        line["dense_fp64_gpu"] = dense_baseline(m, pulse, W, q)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(max_seconds=args.cpu_seconds)
     print(json.dumps(line), flush=True)
+
+
+def dense_baseline(m, pulse, W, q_compressed):
+    """One timed pass of the plain dense FP64 GPU path (dense V_l for every
+    solved frequency, FP64 GMRES) on the same workload, and the time-domain
+    difference of the two solutions (the H^2 interpolation error)."""
+    import torch
+    from paper_2006_05186_gb300 import CqmBem
+    N, dt = W["N"], W["dt"]
+    L, M = N + 1, m.nt
+    rhs = torch.empty((L, M), dtype=torch.float64, device="cuda")
+    qd = torch.empty((L, M), dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    op = CqmBem(m.xyz, m.tri, dt, N, W["bdf"], mode="dense")
+    op.rhs_plane_wave(pulse.direction, pulse.width, pulse.delay, out=rhs)
+    op.solve(rhs, out=qd)
+    e1.record()
+    torch.cuda.synchronize()
+    sec = e0.elapsed_time(e1) / 1e3
+    info = op.last_solve_info
+    op.close()
+    a, b = q_compressed.cpu().numpy(), qd.cpu().numpy()
+    diff = float(np.max(np.linalg.norm(a - b, axis=1)) / np.max(np.linalg.norm(b, axis=1)))
+    return {"value": M * L / sec, "unit": UNIT, "seconds": sec, "steps": 1,
+            "gmres_iterations": info["iterations"],
+            "rel_diff_compressed_vs_dense": diff,
+            "note": "one pass, no warm-up; the difference is the H^2 interpolation error (eta = 1, m = 4)"}
 
 
 def cpu_baseline(max_seconds=20.0):
@@ -371,6 +402,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--dense-baseline", action="store_true",
+                    help="also time one pass of the dense FP64 GPU path on the same workload")
     ap.add_argument("--level", type=int, default=None,
                     help="icosphere level override (smaller cases for profiler captures)")
     ap.add_argument("--N", type=int, default=None, help="time-step count override")

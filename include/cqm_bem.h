@@ -102,6 +102,11 @@ typedef struct cqm_params {
                              so results keep FP64 accuracy                [1]   */
   double inner_rtol;      /* with inner_fp32: a cycle ends once its residual
                              estimate fell by this factor                 [1e-5] */
+  int32_t tensor_cores;   /* H2MACA with inner_fp32: far coupling of the inner operator
+                             on the tensor cores (TF32, three-product split) [0] */
+  int32_t cache_quadrature; /* H2MACA: keep every near-field quadrature point (r and
+                             weight / (4 pi r)) in device memory for the MACA
+                             slices and fibres (16 bytes per point)       [1]   */
   int32_t exact_ff;       /* H2MACA: the FP64-accurate apply (residuals) runs its
                              near-field and coupling contractions in float-float
                              arithmetic (~48 bits) on the FP32 pipes; 0 = FP64 [1] */
@@ -212,6 +217,11 @@ int cqm_bem_entries(cqm_handle* h, int64_t npairs, const int32_t* I, const int32
 /* Apply the handle's operator: y_l = V_l x_l for the Ls solved frequencies.
  * x, y: Ls x nt complex in `mem` memory (row l = frequency l). */
 int cqm_bem_apply(cqm_handle* h, const double* x, double* y, int32_t mem);
+
+/* Apply the operator of the inner GMRES iterations (the FP32 copy of the
+ * compressed operator when inner_fp32 is on; otherwise the same as
+ * cqm_bem_apply).  x, y: Ls x nt complex in `mem` memory. */
+int cqm_bem_apply_inner(cqm_handle* h, const double* x, double* y, int32_t mem);
 
 /* Solve V_l qhat_l = ghat_l for the Ls solved frequencies (batched GMRES).
  * ghat, qhat: Ls x nt complex in `mem` memory. */

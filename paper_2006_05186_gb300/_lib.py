@@ -27,7 +27,7 @@ EXPORTED = [
     "cqm_params_default", "cqm_bem_setup", "cqm_bem_solve", "cqm_bem_rhs_plane_wave",
     "cqm_bem_destroy", "cqm_bem_strerror", "cqm_bem_last_error", "cqm_bem_get_info",
     "cqm_bem_get_frequencies", "cqm_bem_get_tree", "cqm_bem_get_blocks",
-    "cqm_bem_get_block_factors", "cqm_bem_entries", "cqm_bem_apply",
+    "cqm_bem_get_block_factors", "cqm_bem_entries", "cqm_bem_apply", "cqm_bem_apply_inner",
     "cqm_bem_solve_frequencies", "cqm_bem_forward_transform", "cqm_bem_inverse_transform",
     "cqm_bem_profile", "cqm_bem_profile_read", "cqm_bem_kernel_name",
     "cqm_cluster_tree_noalloc",
@@ -54,7 +54,8 @@ class cqm_params(C.Structure):
         ("cheb_m", C.c_int32), ("aca_eps", C.c_double), ("rank_cap", C.c_int32),
         ("gmres_restart", C.c_int32), ("gmres_max_iter", C.c_int32), ("gmres_tol", C.c_double),
         ("profile", C.c_int32), ("precond", C.c_int32), ("inner_fp32", C.c_int32),
-        ("inner_rtol", C.c_double), ("exact_ff", C.c_int32),
+        ("inner_rtol", C.c_double), ("tensor_cores", C.c_int32), ("cache_quadrature", C.c_int32),
+        ("exact_ff", C.c_int32),
         ("allocator", C.POINTER(cqm_allocator)),
     ]
 
@@ -119,6 +120,7 @@ def load(build_if_missing: bool = False):
         "cqm_bem_get_block_factors": (C.c_int, [vp, i32, i32, vp, vp, vp, vp, vp]),
         "cqm_bem_entries": (C.c_int, [vp, i64, vp, vp, i32, vp, vp, i32]),
         "cqm_bem_apply": (C.c_int, [vp, vp, vp, i32]),
+        "cqm_bem_apply_inner": (C.c_int, [vp, vp, vp, i32]),
         "cqm_bem_solve_frequencies": (C.c_int, [vp, vp, vp, i32, C.POINTER(cqm_solve_info)]),
         "cqm_bem_forward_transform": (C.c_int, [vp, vp, vp, i32]),
         "cqm_bem_inverse_transform": (C.c_int, [vp, vp, vp, i32]),
@@ -334,6 +336,14 @@ class CqmBem:
         px, mem = _ptr(x)
         po, _ = _ptr(out)
         _check(self._lib.cqm_bem_apply(self._h, px, po, mem), "apply")
+        return out
+
+    def apply_inner(self, x):
+        """The operator of the inner GMRES iterations (FP32 copy with inner_fp32)."""
+        out = _like(x, (self.Ls, self.M), complex_=True)
+        px, mem = _ptr(x)
+        po, _ = _ptr(out)
+        _check(self._lib.cqm_bem_apply_inner(self._h, px, po, mem), "apply_inner")
         return out
 
     def solve_frequencies(self, ghat, allow_noconv=False):

@@ -63,6 +63,8 @@ int cqm_params_default(cqm_params* p) {
   p->inner_fp32 = 1;
   p->inner_rtol = 1e-5;
   p->exact_ff = 1;
+  p->cache_quadrature = 1;
+  p->tensor_cores = 0;
   p->allocator = nullptr;
   return CQM_OK;
 }
@@ -88,7 +90,7 @@ int cqm_bem_destroy(cqm_handle* h) {
   h->xyz.free(A); h->tri.free(A); h->P.free(A); h->area.free(A); h->cen.free(A);
   h->diam.free(A); h->flag.free(A); h->near_pt.free(A);
   for (int t = 0; t < 3; ++t) { h->ss_pt[t].free(A); h->ss_w[t].free(A); }
-  h->s.free(A); h->Vd.free(A);
+  h->s.free(A); h->Vd.free(A); h->exp_t2.free(A); h->exp_cs.free(A);
   h->perm.free(A); h->node_begin.free(A); h->node_end.free(A); h->node_son0.free(A);
   h->node_son1.free(A); h->node_parent.free(A); h->node_level.free(A); h->node_lo.free(A);
   h->node_hi.free(A);
@@ -98,6 +100,9 @@ int cqm_bem_destroy(cqm_handle* h) {
   h->nearC.free(A); h->nearD.free(A); h->farC.free(A); h->farD.free(A);
   h->xhat.free(A); h->yhat.free(A); h->d_leaves.free(A); h->d_far_rows.free(A);
   h->Pinv.free(A);
+  h->far_items.free(A); h->near_items.free(A); h->far_item_ptr.free(A); h->near_item_ptr.free(A);
+  h->part_f.free(A); h->part_d.free(A);
+  h->pt_off.free(A); h->pt_cnt.free(A); h->pt_r.free(A); h->pt_c.free(A);
   h->nearC_f.free(A); h->nearD_f.free(A); h->farC_f.free(A); h->farD_f.free(A);
   h->xhat_f.free(A); h->yhat_f.free(A); h->Uleaf_f.free(A); h->Etr_f.free(A);
   cudaStreamSynchronize(h->stream);
@@ -181,6 +186,7 @@ int cqm_bem_setup(const cqm_mesh* mesh, double dt, int32_t N, int32_t bdf_order,
       if ((st = build_bases(h)) != CQM_OK) break;
       cudaEventRecord(ev[3], h->stream);
       if ((st = build_maca(h)) != CQM_OK) break;
+      if ((st = build_work_items(h)) != CQM_OK) break;
       if (p.precond && (st = build_precond(h)) != CQM_OK) break;
       if (p.inner_fp32) {
         if ((st = build_f32_copy(h)) != CQM_OK) break;
@@ -335,6 +341,26 @@ int cqm_bem_apply(cqm_handle* h, const double* x, double* y, int32_t mem) {
     CQM_TRY(S.get(&dy, n));
   }
   CQM_TRY(apply_operator(h, dx, dy));
+  if (mem == CQM_MEM_HOST)
+    CQM_CUDA_TRY(cudaMemcpyAsync(y, dy, n * sizeof(double2), cudaMemcpyDeviceToHost, h->stream));
+  CQM_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  return CQM_OK;
+}
+
+int cqm_bem_apply_inner(cqm_handle* h, const double* x, double* y, int32_t mem) {
+  if (!h || !x || !y || (mem != CQM_MEM_HOST && mem != CQM_MEM_DEVICE)) return CQM_EINVAL;
+  const size_t n = (size_t)h->Ls * h->M;
+  Scratch S(&h->alloc);
+  const double2* dx = (const double2*)x;
+  double2* dy = (double2*)y;
+  if (mem == CQM_MEM_HOST) {
+    double2* t;
+    CQM_TRY(S.get(&t, n));
+    CQM_CUDA_TRY(cudaMemcpyAsync(t, x, n * sizeof(double2), cudaMemcpyHostToDevice, h->stream));
+    dx = t;
+    CQM_TRY(S.get(&dy, n));
+  }
+  CQM_TRY(apply_operator_inner(h, dx, dy));
   if (mem == CQM_MEM_HOST)
     CQM_CUDA_TRY(cudaMemcpyAsync(y, dy, n * sizeof(double2), cudaMemcpyDeviceToHost, h->stream));
   CQM_CUDA_TRY(cudaStreamSynchronize(h->stream));

@@ -19,19 +19,18 @@ __device__ __forceinline__ float2 f2mul(float2 a, float2 b) {
 // Far coupling; p = 64 (8 warps x 8 rows each).
 template <int NLT>
 __global__ void __launch_bounds__(256) k_far_coupling_f32(int Ls, int cap,
-                                                          const int* __restrict__ rows,
-                                                          const int* __restrict__ rowptr,
+                                                          const int4* __restrict__ items,
                                                           const int2* __restrict__ blocks,
                                                           const int* __restrict__ rank,
                                                           const float2* __restrict__ Cf,
                                                           const float2* __restrict__ Df,
                                                           const float2* __restrict__ xhat,
-                                                          float2* __restrict__ yhat) {
+                                                          float2* __restrict__ part) {
   constexpr int P = 64, LW = 32 * NLT;
   extern __shared__ __align__(16) unsigned char smraw[];
   float2* Xs = (float2*)smraw;  // P x LW
   float2* Cs = Xs + P * LW;     // P x P
-  const int r = rows[blockIdx.x];
+  const int4 it = items[blockIdx.x];  // (row, first block, end block, -)
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int mu0 = w * 8;
   for (int l0 = 0; l0 < Ls; l0 += LW) {
@@ -40,7 +39,7 @@ __global__ void __launch_bounds__(256) k_far_coupling_f32(int Ls, int cap,
     for (int i = 0; i < 8; ++i)
 #pragma unroll
       for (int k = 0; k < NLT; ++k) acc[i][k] = make_float2(0.f, 0.f);
-    for (int bi = rowptr[r]; bi < rowptr[r + 1]; ++bi) {
+    for (int bi = it.y; bi < it.z; ++bi) {
       const int c = blocks[bi].y;
       __syncthreads();
       for (int t = threadIdx.x; t < P * LW; t += blockDim.x) {
@@ -78,26 +77,37 @@ __global__ void __launch_bounds__(256) k_far_coupling_f32(int Ls, int cap,
 #pragma unroll
       for (int k = 0; k < NLT; ++k) {
         const int l = l0 + lane + 32 * k;
-        if (l < Ls) {
-          float2* o = yhat + ((size_t)r * P + mu0 + i) * Ls + l;
-          *o = cadd(*o, acc[i][k]);
-        }
+        if (l < Ls) part[((size_t)blockIdx.x * P + mu0 + i) * Ls + l] = acc[i][k];
       }
+  }
+}
+
+// yhat_r[mu][l] += sum of the partial tiles of row r's items, in item order.
+__global__ void k_far_reduce_f32(int Ls, const int* __restrict__ rows,
+                                 const int* __restrict__ item_ptr, const float2* __restrict__ part,
+                                 float2* __restrict__ yhat) {
+  const int k = blockIdx.x;  // index into the list of far rows
+  const int r = rows[k];
+  for (int e = threadIdx.x; e < 64 * Ls; e += blockDim.x) {
+    float2 a = make_float2(0.f, 0.f);
+    for (int it = item_ptr[k]; it < item_ptr[k + 1]; ++it) a = cadd(a, part[(size_t)it * 64 * Ls + e]);
+    float2* o = yhat + (size_t)r * 64 * Ls + e;
+    *o = cadd(*o, a);
   }
 }
 
 // Near field; leaf clusters of at most 32 triangles (8 warps x 4 rows).
 template <int NLT>
 __global__ void __launch_bounds__(256) k_near_apply_f32(
-    int M, int Ls, int cap, const int* __restrict__ leaves, const int* __restrict__ rowptr,
-    const int2* __restrict__ blocks, const int* __restrict__ rank, const int64_t* __restrict__ off,
-    const float2* __restrict__ Cn, const float2* __restrict__ Dn, const int* __restrict__ begin,
-    const int* __restrict__ end, const int* __restrict__ perm, const double2* __restrict__ X,
-    double2* __restrict__ Y) {
+    int M, int Ls, int cap, const int4* __restrict__ items, const int2* __restrict__ blocks,
+    const int* __restrict__ rank, const int64_t* __restrict__ off, const float2* __restrict__ Cn,
+    const float2* __restrict__ Dn, const int* __restrict__ begin, const int* __restrict__ end,
+    const int* __restrict__ perm, const double2* __restrict__ X, float2* __restrict__ part) {
   constexpr int LW = 32 * NLT;
   __shared__ float2 Xs[32 * LW];
   __shared__ float2 Cs[32 * 32];
-  const int r = leaves[blockIdx.x];
+  const int4 it = items[blockIdx.x];  // (leaf row, first block, end block, -)
+  const int r = it.x;
   const int rb = begin[r], nr = end[r] - rb;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int i0 = w * 4;
@@ -107,7 +117,7 @@ __global__ void __launch_bounds__(256) k_near_apply_f32(
     for (int i = 0; i < 4; ++i)
 #pragma unroll
       for (int k = 0; k < NLT; ++k) acc[i][k] = make_float2(0.f, 0.f);
-    for (int bi = rowptr[r]; bi < rowptr[r + 1]; ++bi) {
+    for (int bi = it.y; bi < it.z; ++bi) {
       const int c = blocks[bi].y;
       const int cb = begin[c], nc = end[c] - cb;
       __syncthreads();
@@ -146,9 +156,24 @@ __global__ void __launch_bounds__(256) k_near_apply_f32(
 #pragma unroll
       for (int k = 0; k < NLT; ++k) {
         const int l = l0 + lane + 32 * k;
-        if (i0 + i < nr && l < Ls)
-          Y[(size_t)l * M + perm[rb + i0 + i]] = make_double2(acc[i][k].x, acc[i][k].y);
+        if (i0 + i < nr && l < Ls) part[((size_t)blockIdx.x * 32 + i0 + i) * Ls + l] = acc[i][k];
       }
+  }
+}
+
+// Y[l][perm[rb + i]] = sum of the partial tiles of leaf row k's items, in item order.
+__global__ void k_near_reduce_f32(int M, int Ls, const int* __restrict__ leaves,
+                                  const int* __restrict__ item_ptr, const int* __restrict__ begin,
+                                  const int* __restrict__ end, const int* __restrict__ perm,
+                                  const float2* __restrict__ part, double2* __restrict__ Y) {
+  const int k = blockIdx.x;
+  const int r = leaves[k];
+  const int rb = begin[r], nr = end[r] - rb;
+  for (int e = threadIdx.x; e < nr * Ls; e += blockDim.x) {
+    const int i = e / Ls, l = e - i * Ls;
+    float2 a = make_float2(0.f, 0.f);
+    for (int it = item_ptr[k]; it < item_ptr[k + 1]; ++it) a = cadd(a, part[((size_t)it * 32 + i) * Ls + l]);
+    Y[(size_t)l * M + perm[rb + i]] = make_double2(a.x, a.y);
   }
 }
 
@@ -163,16 +188,23 @@ int setup_f32_kernels(cqm_handle* h) {
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)far_smem<N>()));
   SETUP_NLT(1) SETUP_NLT(2) SETUP_NLT(3) SETUP_NLT(4) SETUP_NLT(5)
 #undef SETUP_NLT
-  return CQM_OK;
+  return setup_tc_kernels(h);
 }
 
 int far_coupling_f32(cqm_handle* h) {
-  const int n = (int)h->h_far_rows.size();
+  const int n = h->n_far_items;
+  if (h->params.tensor_cores && h->p == 64) {
+    CQM_TRY(far_coupling_tc(h));
+    k_far_reduce_f32<<<(unsigned)h->h_far_rows.size(), 256, 0, h->stream>>>(
+        h->Ls, h->d_far_rows.p, h->far_item_ptr.p, h->part_f.p, h->yhat_f.p);
+    CQM_CHECK_LAUNCH();
+    return CQM_OK;
+  }
   ProfScope ps_(h, CQM_K_FAR_COUPLING);
 #define LAUNCH_NLT(N)                                                                              \
   k_far_coupling_f32<N><<<n, 256, far_smem<N>(), h->stream>>>(                                     \
-      h->Ls, h->rank_cap, h->d_far_rows.p, h->far_rowptr.p, h->far_rc.p, h->far_rank.p, h->farC_f.p, \
-      h->farD_f.p, h->xhat_f.p, h->yhat_f.p)
+      h->Ls, h->rank_cap, h->far_items.p, h->far_rc.p, h->far_rank.p, h->farC_f.p, h->farD_f.p,     \
+      h->xhat_f.p, h->part_f.p)
   switch (nlt_for(h->Ls)) {
     case 1: LAUNCH_NLT(1); break;
     case 2: LAUNCH_NLT(2); break;
@@ -181,17 +213,19 @@ int far_coupling_f32(cqm_handle* h) {
     default: LAUNCH_NLT(5); break;
   }
 #undef LAUNCH_NLT
+  k_far_reduce_f32<<<(unsigned)h->h_far_rows.size(), 256, 0, h->stream>>>(
+      h->Ls, h->d_far_rows.p, h->far_item_ptr.p, h->part_f.p, h->yhat_f.p);
   CQM_CHECK_LAUNCH();
   return CQM_OK;
 }
 
 int near_apply_f32(cqm_handle* h, const double2* x, double2* y) {
-  const int n = (int)h->h_leaves.size();
+  const int n = h->n_near_items;
   ProfScope ps_(h, CQM_K_NEAR_APPLY);
 #define LAUNCH_NLT(N)                                                                              \
   k_near_apply_f32<N><<<n, 256, 0, h->stream>>>(                                                   \
-      h->M, h->Ls, h->rank_cap, h->d_leaves.p, h->near_rowptr.p, h->near_rc.p, h->near_rank.p,     \
-      h->near_off.p, h->nearC_f.p, h->nearD_f.p, h->node_begin.p, h->node_end.p, h->perm.p, x, y)
+      h->M, h->Ls, h->rank_cap, h->near_items.p, h->near_rc.p, h->near_rank.p, h->near_off.p,      \
+      h->nearC_f.p, h->nearD_f.p, h->node_begin.p, h->node_end.p, h->perm.p, x, h->part_f.p)
   switch (nlt_for(h->Ls)) {
     case 1: LAUNCH_NLT(1); break;
     case 2: LAUNCH_NLT(2); break;
@@ -200,6 +234,9 @@ int near_apply_f32(cqm_handle* h, const double2* x, double2* y) {
     default: LAUNCH_NLT(5); break;
   }
 #undef LAUNCH_NLT
+  k_near_reduce_f32<<<(unsigned)h->h_leaves.size(), 256, 0, h->stream>>>(
+      h->M, h->Ls, h->d_leaves.p, h->near_item_ptr.p, h->node_begin.p, h->node_end.p, h->perm.p,
+      h->part_f.p, y);
   CQM_CHECK_LAUNCH();
   return CQM_OK;
 }

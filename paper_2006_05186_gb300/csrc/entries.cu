@@ -98,6 +98,16 @@ static void sauter_schwab_rule(int cse, int g, std::vector<double4>& pts, std::v
   }
 }
 
+// Tables of the table-driven exponential: 2^(j/1024) and cis(j pi/512).
+__global__ void k_exp_tables(double* t2, double2* cs) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= 1024) return;
+  t2[j] = exp2((double)j / 1024.0);
+  double sn, co;
+  sincospi((double)j / 512.0, &sn, &co);
+  cs[j] = make_double2(co, sn);
+}
+
 int build_quad_tables(cqm_handle* h) {
   const int gn = h->params.g_near, gs = h->params.g_sing;
   std::vector<double> x, w;
@@ -128,6 +138,12 @@ int build_quad_tables(cqm_handle* h) {
     h->quad.ss_n[t] = (int)pts.size();
   }
   h->quad.near_ratio = h->params.near_ratio;
+  CQM_TRY(h->exp_t2.allocate(h->alloc, 1024));
+  CQM_TRY(h->exp_cs.allocate(h->alloc, 1024));
+  k_exp_tables<<<4, 256, 0, h->stream>>>(h->exp_t2.p, h->exp_cs.p);
+  CQM_CHECK_LAUNCH();
+  h->quad.t2 = h->exp_t2.p;
+  h->quad.cs = h->exp_cs.p;
   CQM_CUDA_TRY(cudaStreamSynchronize(h->stream));  // host vectors go out of scope
   return CQM_OK;
 }

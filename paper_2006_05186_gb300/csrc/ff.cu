@@ -65,22 +65,22 @@ constexpr int PMAX = 64;
 
 // Near field in float-float: one block per leaf row cluster.
 __global__ void __launch_bounds__(256) k_near_apply_ff(
-    int M, int Ls, int cap, const int* __restrict__ leaves, const int* __restrict__ rowptr,
-    const int2* __restrict__ blocks, const int* __restrict__ rank, const int64_t* __restrict__ off,
-    const double2* __restrict__ Cn, const double2* __restrict__ Dn, const int* __restrict__ begin,
-    const int* __restrict__ end, const int* __restrict__ perm, const double2* __restrict__ X,
-    double2* __restrict__ Y) {
+    int M, int Ls, int cap, const int4* __restrict__ items, const int2* __restrict__ blocks,
+    const int* __restrict__ rank, const int64_t* __restrict__ off, const double2* __restrict__ Cn,
+    const double2* __restrict__ Dn, const int* __restrict__ begin, const int* __restrict__ end,
+    const int* __restrict__ perm, const double2* __restrict__ X, double2* __restrict__ part) {
   __shared__ ffc Xs[32][LCF];
   __shared__ ffc Cs[32 * 32];
   __shared__ ffc Ds[LCF];
-  const int r = leaves[blockIdx.x];
+  const int4 itm = items[blockIdx.x];  // (leaf row, first block, end block, -)
+  const int r = itm.x;
   const int rb = begin[r], nr = end[r] - rb;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int l0 = 0; l0 < Ls; l0 += LCF) {
     ffc acc[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) acc[k] = ffc_zero();
-    for (int bi = rowptr[r]; bi < rowptr[r + 1]; ++bi) {
+    for (int bi = itm.y; bi < itm.z; ++bi) {
       const int c = blocks[bi].y;
       const int cb = begin[c], nc = end[c] - cb;
       __syncthreads();
@@ -116,33 +116,61 @@ __global__ void __launch_bounds__(256) k_near_apply_ff(
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const int i = w + 8 * k;
-      if (i < nr && l0 + lane < Ls) Y[(size_t)(l0 + lane) * M + perm[rb + i]] = ffc_to(acc[k]);
+      if (i < nr && l0 + lane < Ls) part[((size_t)blockIdx.x * 32 + i) * Ls + l0 + lane] = ffc_to(acc[k]);
     }
+  }
+}
+
+// Y[l][perm[rb + i]] = sum of leaf row k's item tiles, in item order (FP64).
+__global__ void k_near_reduce_d(int M, int Ls, const int* __restrict__ leaves,
+                                const int* __restrict__ item_ptr, const int* __restrict__ begin,
+                                const int* __restrict__ end, const int* __restrict__ perm,
+                                const double2* __restrict__ part, double2* __restrict__ Y) {
+  const int k = blockIdx.x;
+  const int r = leaves[k];
+  const int rb = begin[r], nr = end[r] - rb;
+  for (int e = threadIdx.x; e < nr * Ls; e += blockDim.x) {
+    const int i = e / Ls, l = e - i * Ls;
+    double2 a = make_double2(0.0, 0.0);
+    for (int it = item_ptr[k]; it < item_ptr[k + 1]; ++it) a = cadd(a, part[((size_t)it * 32 + i) * Ls + l]);
+    Y[(size_t)l * M + perm[rb + i]] = a;
+  }
+}
+
+// yhat_r += sum of row k's item tiles, in item order (FP64).
+__global__ void k_far_reduce_d(int Ls, const int* __restrict__ rows, const int* __restrict__ item_ptr,
+                               const double2* __restrict__ part, double2* __restrict__ yhat) {
+  const int k = blockIdx.x;
+  const int r = rows[k];
+  for (int e = threadIdx.x; e < 64 * Ls; e += blockDim.x) {
+    double2 a = make_double2(0.0, 0.0);
+    for (int it = item_ptr[k]; it < item_ptr[k + 1]; ++it) a = cadd(a, part[(size_t)it * 64 * Ls + e]);
+    double2* o = yhat + (size_t)r * 64 * Ls + e;
+    *o = cadd(*o, a);
   }
 }
 
 // Far coupling in float-float: one block per row cluster owning far blocks;
 // yhat_r (FP64) += sum_b sum_t D_b[t] C_{b,t} xhat_c.
 __global__ void __launch_bounds__(256) k_far_coupling_ff(int Ls, int p, int cap,
-                                                         const int* __restrict__ rows,
-                                                         const int* __restrict__ rowptr,
+                                                         const int4* __restrict__ items,
                                                          const int2* __restrict__ blocks,
                                                          const int* __restrict__ rank,
                                                          const double2* __restrict__ Cf,
                                                          const double2* __restrict__ Df,
                                                          const double2* __restrict__ xhat,
-                                                         double2* __restrict__ yhat) {
+                                                         double2* __restrict__ part) {
   extern __shared__ __align__(16) unsigned char smraw[];
   ffc* Xs = (ffc*)smraw;        // p x LCF
   ffc* Cs = Xs + PMAX * LCF;    // p x p
   __shared__ ffc Ds[LCF];
-  const int r = rows[blockIdx.x];
+  const int4 itm = items[blockIdx.x];  // (row, first block, end block, -)
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int l0 = 0; l0 < Ls; l0 += LCF) {
     ffc acc[PMAX / 8];
 #pragma unroll
     for (int k = 0; k < PMAX / 8; ++k) acc[k] = ffc_zero();
-    for (int bi = rowptr[r]; bi < rowptr[r + 1]; ++bi) {
+    for (int bi = itm.y; bi < itm.z; ++bi) {
       const int c = blocks[bi].y;
       __syncthreads();
       for (int t = threadIdx.x; t < p * LCF; t += blockDim.x) {
@@ -177,10 +205,7 @@ __global__ void __launch_bounds__(256) k_far_coupling_ff(int Ls, int p, int cap,
 #pragma unroll
       for (int k = 0; k < (int)(sizeof(acc) / sizeof(acc[0])); ++k) {
         const int mu = w + 8 * k;
-        if (mu < p) {
-          double2* o = yhat + ((size_t)r * p + mu) * Ls + l0 + lane;
-          *o = cadd(*o, ffc_to(acc[k]));
-        }
+        if (mu < p) part[((size_t)blockIdx.x * p + mu) * Ls + l0 + lane] = ffc_to(acc[k]);
       }
   }
 }
@@ -195,18 +220,23 @@ int setup_ff(cqm_handle* h) {
 
 int near_apply_ff(cqm_handle* h, const double2* x, double2* y) {
   ProfScope ps_(h, CQM_K_NEAR_EXACT);
-  k_near_apply_ff<<<(unsigned)h->h_leaves.size(), 256, 0, h->stream>>>(
-      h->M, h->Ls, h->rank_cap, h->d_leaves.p, h->near_rowptr.p, h->near_rc.p, h->near_rank.p,
-      h->near_off.p, h->nearC.p, h->nearD.p, h->node_begin.p, h->node_end.p, h->perm.p, x, y);
+  k_near_apply_ff<<<(unsigned)h->n_near_items, 256, 0, h->stream>>>(
+      h->M, h->Ls, h->rank_cap, h->near_items.p, h->near_rc.p, h->near_rank.p, h->near_off.p,
+      h->nearC.p, h->nearD.p, h->node_begin.p, h->node_end.p, h->perm.p, x, h->part_d.p);
+  k_near_reduce_d<<<(unsigned)h->h_leaves.size(), 256, 0, h->stream>>>(
+      h->M, h->Ls, h->d_leaves.p, h->near_item_ptr.p, h->node_begin.p, h->node_end.p, h->perm.p,
+      h->part_d.p, y);
   CQM_CHECK_LAUNCH();
   return CQM_OK;
 }
 
 int far_coupling_ff(cqm_handle* h) {
   ProfScope ps_(h, CQM_K_FAR_EXACT);
-  k_far_coupling_ff<<<(unsigned)h->h_far_rows.size(), 256, coupling_smem_ff(h->p), h->stream>>>(
-      h->Ls, h->p, h->rank_cap, h->d_far_rows.p, h->far_rowptr.p, h->far_rc.p, h->far_rank.p,
-      h->farC.p, h->farD.p, h->xhat.p, h->yhat.p);
+  k_far_coupling_ff<<<(unsigned)h->n_far_items, 256, coupling_smem_ff(h->p), h->stream>>>(
+      h->Ls, h->p, h->rank_cap, h->far_items.p, h->far_rc.p, h->far_rank.p, h->farC.p, h->farD.p,
+      h->xhat.p, h->part_d.p);
+  k_far_reduce_d<<<(unsigned)h->h_far_rows.size(), 256, 0, h->stream>>>(
+      h->Ls, h->d_far_rows.p, h->far_item_ptr.p, h->part_d.p, h->yhat.p);
   CQM_CHECK_LAUNCH();
   return CQM_OK;
 }

@@ -22,6 +22,8 @@ struct cqm_handle {
   cqm::DArray<double4> near_pt, ss_pt[3];
   cqm::DArray<double> ss_w[3];
   cqm::Quad quad{};
+  cqm::DArray<double> exp_t2;
+  cqm::DArray<double2> exp_cs;
 
   // CQM frequencies s_l, l = 0..L-1 (eq. cqm_freq)
   cqm::DArray<double2> s;
@@ -57,10 +59,22 @@ struct cqm_handle {
   cqm::DArray<double2> farC, farD;    // C: n_far x cap x p x p ; D: n_far x cap x Ls
   std::vector<int> h_near_rank, h_far_rank;
   std::vector<int64_t> h_near_off;
+  // near-field quadrature points cached for the MACA slices and fibres
+  int64_t n_points = 0;
+  cqm::DArray<int64_t> pt_off;
+  cqm::DArray<int> pt_cnt;
+  cqm::DArray<double> pt_r, pt_c;
 
   // apply plan: leaf clusters and row clusters owning far blocks
   std::vector<int> h_leaves, h_far_rows;
   cqm::DArray<int> d_leaves, d_far_rows;
+  // balanced work items (row, first block, end block) of the contractions,
+  // with per-row item ranges; partial tiles are reduced per row in item order
+  int n_far_items = 0, n_near_items = 0;
+  cqm::DArray<int4> far_items, near_items;
+  cqm::DArray<int> far_item_ptr, near_item_ptr;
+  cqm::DArray<float2> part_f;
+  cqm::DArray<double2> part_d;
 
   // leaf block-diagonal preconditioner: P[leaf][i][j][l]
   bool use_precond = false;
@@ -122,6 +136,10 @@ int setup_f32_kernels(cqm_handle* h);
 int near_apply_f32(cqm_handle* h, const double2* x, double2* y);
 int far_coupling_f32(cqm_handle* h);
 
+// tc.cu (tensor-core far coupling of the inner operator)
+int setup_tc_kernels(cqm_handle* h);
+int far_coupling_tc(cqm_handle* h);
+
 // ff.cu (float-float contractions of the FP64-accurate apply)
 int setup_ff(cqm_handle* h);
 int near_apply_ff(cqm_handle* h, const double2* x, double2* y);
@@ -129,6 +147,7 @@ int far_coupling_ff(cqm_handle* h);
 
 // maca.cu
 int build_maca(cqm_handle* h);
+int build_work_items(cqm_handle* h);
 
 // precond.cu
 int build_precond(cqm_handle* h);

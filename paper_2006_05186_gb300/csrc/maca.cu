@@ -42,6 +42,12 @@ struct MacaBlocks {
   int words;
   int* counters;       // [0] active blocks, [1] capacity overflow
   double eps;
+  // near field: cached quadrature points (r, weight / (4 pi r)) of every pair;
+  // pair k of block b is pair_base[b] + i * #c + j, its points start at pt_off[k]
+  const int64_t* pt_off;
+  const int* pt_cnt;
+  const double* pt_r;
+  const double* pt_c;
 };
 
 __device__ __forceinline__ int rows_of(const MacaBlocks& B, int b) {
@@ -63,11 +69,8 @@ __device__ __forceinline__ void cheb_point(const double* cheb, int r, int m, int
   x[2] = nd[2 * m + mu / (m * m)];
 }
 
-__device__ __forceinline__ double2 kernel_value(double r, double2 s) {
-  const double e = exp(-s.x * r) / (CQM_FOUR_PI * r);
-  double sn, cs;
-  sincos(s.y * r, &sn, &cs);
-  return make_double2(e * cs, -e * sn);
+__device__ __forceinline__ double2 kernel_value(double r, double2 s, const Quad& q) {
+  return cexp_c(r, 1.0 / (CQM_FOUR_PI * r), s, q);
 }
 
 // Slice G[:,:,k] of every active block into slot rank[b].
@@ -87,13 +90,25 @@ __global__ void __launch_bounds__(256) k_maca_slice(MacaBlocks B, Geom g, Quad q
       cheb_point(B.cheb, rc.x, B.m, mu, xr);
       cheb_point(B.cheb, rc.y, B.m, nu, xc);
       const double d0 = xc[0] - xr[0], d1 = xc[1] - xr[1], d2 = xc[2] - xr[2];
-      out[e] = kernel_value(sqrt(d0 * d0 + d1 * d1 + d2 * d2), sk);
+      out[e] = kernel_value(sqrt(d0 * d0 + d1 * d1 + d2 * d2), sk, q);
     }
     return;
   }
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int rb = B.begin[rc.x], cb = B.begin[rc.y];
   double2 sv[1] = {sk};
+  if (B.pt_r) {
+    const int64_t base = B.off[b] / B.cap;
+    for (int e = w; e < nr * nc; e += nw) {
+      const int64_t o = B.pt_off[base + e];
+      const int n = B.pt_cnt[base + e];
+      double2 acc[1] = {make_double2(0.0, 0.0)};
+      for (int k = lane; k < n; k += 32) kernel_accumulate_c<1>(B.pt_r[o + k], B.pt_c[o + k], sv, 1, acc, q);
+      acc[0] = warp_sum2(acc[0]);
+      if (lane == 0) out[e] = acc[0];
+    }
+    return;
+  }
   for (int e = w; e < nr * nc; e += nw) {
     const int i = e / nc, j = e - i * nc;
     const int I = B.perm[rb + i], J = B.perm[cb + j];
@@ -197,13 +212,34 @@ __global__ void __launch_bounds__(256) k_maca_fibre(MacaBlocks B, Geom g, Quad q
     cheb_point(B.cheb, rc.y, B.m, pv.y, xc);
     const double d0 = xc[0] - xr[0], d1 = xc[1] - xr[1], d2 = xc[2] - xr[2];
     const double r = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
-    for (int k = threadIdx.x; k < B.Ls; k += blockDim.x) out[k] = kernel_value(r, s[k]);
+    for (int k = threadIdx.x; k < B.Ls; k += blockDim.x) out[k] = kernel_value(r, s[k], q);
     return;
   }
   const int I = B.perm[B.begin[rc.x] + pv.x], J = B.perm[B.begin[rc.y] + pv.y];
   const int cse = pair_case(g, q, I, J);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   constexpr int NF = 8;
+  if (B.pt_r) {
+    const int nc = B.end[rc.y] - B.begin[rc.y];
+    const int64_t k = B.off[b] / B.cap + (int64_t)pv.x * nc + pv.y;
+    const int64_t o = B.pt_off[k];
+    const int n = B.pt_cnt[k];
+    for (int f0 = w * NF; f0 < B.Ls; f0 += nw * NF) {
+      const int nf = min(NF, B.Ls - f0);
+      double2 sv[NF], acc[NF];
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        sv[f] = f < nf ? s[f0 + f] : make_double2(0.0, 0.0);
+        acc[f] = make_double2(0.0, 0.0);
+      }
+      for (int p = lane; p < n; p += 32) kernel_accumulate_c<NF>(B.pt_r[o + p], B.pt_c[o + p], sv, nf, acc, q);
+#pragma unroll
+      for (int f = 0; f < NF; ++f) acc[f] = warp_sum2(acc[f]);
+      if (lane == 0)
+        for (int f = 0; f < nf; ++f) out[f0 + f] = acc[f];
+    }
+    return;
+  }
   for (int f0 = w * NF; f0 < B.Ls; f0 += nw * NF) {
     const int nf = min(NF, B.Ls - f0);
     double2 sv[NF], acc[NF];
@@ -316,6 +352,158 @@ __global__ void k_maca_init(int n, int words, int* rank, int* active, int* kcur,
   for (int w = 0; w < words; ++w) used[(size_t)b * words + w] = 0u;
 }
 
+// Point counts of every pair of near block b (CTA per block) and their
+// exclusive scan within the block; block totals for the global scan.
+__global__ void __launch_bounds__(1024) k_pair_counts(const int2* __restrict__ rc, const int* __restrict__ begin,
+                                                     const int* __restrict__ end, const int* __restrict__ perm,
+                                                     const int64_t* __restrict__ off, int cap, Geom g, Quad q,
+                                                     int* cnt, int64_t* pt_off, int64_t* block_total) {
+  __shared__ int64_t sh[33];
+  const int b = blockIdx.x;
+  const int2 c2 = rc[b];
+  const int rb = begin[c2.x], nr = end[c2.x] - rb, cb = begin[c2.y], nc = end[c2.y] - cb;
+  const int64_t base = off[b] / cap;
+  const int n = nr * nc;  // <= 1024 (leaves of at most 32)
+  int v = 0;
+  if ((int)threadIdx.x < n) {
+    const int i = threadIdx.x / nc, j = threadIdx.x - i * nc;
+    v = pair_npoints(q, pair_case(g, q, perm[rb + i], perm[cb + j]));
+    cnt[base + threadIdx.x] = v;
+  }
+  // block exclusive scan (int64)
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int64_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) sh[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    const int64_t wv = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0;
+    int64_t z = wv;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t y = __shfl_up_sync(0xffffffffu, z, o);
+      if (lane >= o) z += y;
+    }
+    sh[lane] = z - wv;
+    if (lane == 31) sh[32] = z;
+  }
+  __syncthreads();
+  if ((int)threadIdx.x < n) pt_off[base + threadIdx.x] = sh[warp] + x - v;
+  if (threadIdx.x == 0) block_total[b] = sh[32];
+}
+
+// Exclusive scan of n int64 values in one CTA; out[n] = total.
+__global__ void __launch_bounds__(1024) k_scan_i64(int n, const int64_t* __restrict__ in, int64_t* out) {
+  __shared__ int64_t sh[33];
+  __shared__ int64_t carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int b0 = 0; b0 < n; b0 += blockDim.x) {
+    const int k = b0 + threadIdx.x;
+    const int64_t v = k < n ? in[k] : 0;
+    int64_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) sh[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+      const int64_t wv = sh[lane];
+      int64_t z = wv;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = __shfl_up_sync(0xffffffffu, z, o);
+        if (lane >= o) z += y;
+      }
+      sh[lane] = z - wv;
+      if (lane == 31) sh[32] = z;
+    }
+    __syncthreads();
+    if (k < n) out[k] = carry + sh[warp] + x - v;
+    __syncthreads();
+    if (threadIdx.x == 0) carry += sh[32];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[n] = carry;
+}
+
+// Geometry of every point of every pair of near block b: one warp per pair.
+__global__ void __launch_bounds__(256) k_pair_geometry(const int2* __restrict__ rc, const int* __restrict__ begin,
+                                                      const int* __restrict__ end, const int* __restrict__ perm,
+                                                      const int64_t* __restrict__ off, int cap, Geom g, Quad q,
+                                                      const int64_t* __restrict__ block_base,
+                                                      int64_t* pt_off, double* pt_r, double* pt_c) {
+  const int b = blockIdx.x;
+  const int2 c2 = rc[b];
+  const int rb = begin[c2.x], nr = end[c2.x] - rb, cb = begin[c2.y], nc = end[c2.y] - cb;
+  const int64_t base = off[b] / cap;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int e = w; e < nr * nc; e += nw) {
+    const int i = e / nc, j = e - i * nc;
+    const int I = perm[rb + i], J = perm[cb + j];
+    const int64_t o = pt_off[base + e] + block_base[b];
+    __syncwarp();
+    if (lane == 0) pt_off[base + e] = o;
+    const int cse = pair_case(g, q, I, J);
+    pair_points(g, q, I, J, cse, lane, 32, [&](int k, double r, double c) {
+      pt_r[o + k] = r;
+      pt_c[o + k] = c;
+    });
+  }
+}
+
+static Geom geom_from(const cqm_handle* h);
+
+// Quadrature points of every near-field pair, computed once for all MACA
+// slices and fibres (r and weight / (4 pi r) per point).
+static int build_point_cache(cqm_handle* h, int64_t n_pairs) {
+  const int nb = h->n_near;
+  if (nb == 0 || !h->params.cache_quadrature) return CQM_OK;
+  CQM_TRY(h->pt_cnt.allocate(h->alloc, n_pairs));
+  CQM_TRY(h->pt_off.allocate(h->alloc, n_pairs));
+  DArray<int64_t> tot, bbase;
+  int st = tot.allocate(h->alloc, nb);
+  if (st == CQM_OK) st = bbase.allocate(h->alloc, nb + 1);
+  int64_t npts = 0;
+  if (st == CQM_OK) {
+    const Geom g = geom_from(h);
+    {
+      ProfScope ps_(h, CQM_K_MACA_SLICE);
+      k_pair_counts<<<nb, 1024, 0, h->stream>>>(h->near_rc.p, h->node_begin.p, h->node_end.p, h->perm.p,
+                                               h->near_off.p, h->rank_cap, g, h->quad, h->pt_cnt.p,
+                                               h->pt_off.p, tot.p);
+      k_scan_i64<<<1, 1024, 0, h->stream>>>(nb, tot.p, bbase.p);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&npts, bbase.p + nb, sizeof(int64_t), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+      set_last_error(std::string("point cache: ") + cudaGetErrorString(e));
+      st = CQM_ECUDA;
+    }
+    if (st == CQM_OK) st = h->pt_r.allocate(h->alloc, std::max<int64_t>(npts, 1));
+    if (st == CQM_OK) st = h->pt_c.allocate(h->alloc, std::max<int64_t>(npts, 1));
+    if (st == CQM_OK) {
+      ProfScope ps_(h, CQM_K_MACA_SLICE);
+      k_pair_geometry<<<nb, 256, 0, h->stream>>>(h->near_rc.p, h->node_begin.p, h->node_end.p, h->perm.p,
+                                                h->near_off.p, h->rank_cap, g, h->quad, bbase.p,
+                                                h->pt_off.p, h->pt_r.p, h->pt_c.p);
+      if (cudaGetLastError() != cudaSuccess) st = CQM_ECUDA;
+    }
+  }
+  tot.free(h->alloc);
+  bbase.free(h->alloc);
+  h->n_points = npts;
+  return st;
+}
+
 static Geom geom_from(const cqm_handle* h) {
   Geom g;
   g.M = h->M; g.tri = h->tri.p; g.P = h->P.p; g.area = h->area.p; g.cen = h->cen.p; g.diam = h->diam.p;
@@ -361,6 +549,11 @@ static int run_maca(cqm_handle* h, int kind, int n, const int2* rc, DArray<doubl
   B.active = active.p; B.kcur = kcur.p; B.piv = piv.p; B.pval = pval.p; B.cn2 = cn2.p;
   B.norm2 = norm2.p; B.gramc = gramc.p; B.used = used.p; B.words = words;
   B.counters = counters.p; B.eps = h->params.aca_eps;
+  const bool cached = kind == 0 && h->pt_r.p != nullptr;
+  B.pt_off = cached ? h->pt_off.p : nullptr;
+  B.pt_cnt = cached ? h->pt_cnt.p : nullptr;
+  B.pt_r = cached ? h->pt_r.p : nullptr;
+  B.pt_c = cached ? h->pt_c.p : nullptr;
   cudaStream_t S = h->stream;
   const Geom g = geom_from(h);
   {
@@ -430,8 +623,14 @@ int build_maca(cqm_handle* h) {
   CQM_TRY(h->near_off.allocate(h->alloc, std::max(1, h->n_near)));
   CQM_CUDA_TRY(cudaMemcpyAsync(h->near_off.p, h->h_near_off.data(), sizeof(int64_t) * h->n_near,
                                cudaMemcpyHostToDevice, h->stream));
+  CQM_TRY(build_point_cache(h, total / std::max(1, h->rank_cap)));
   CQM_TRY(run_maca(h, 0, h->n_near, h->near_rc.p, h->nearC, h->nearD, h->near_rank, h->near_off.p,
                    (size_t)std::max<int64_t>(total, 1), h->h_near_rank));
+  // the point cache serves the near-field slices and fibres only
+  h->pt_r.free(h->alloc);
+  h->pt_c.free(h->alloc);
+  h->pt_off.free(h->alloc);
+  h->pt_cnt.free(h->alloc);
   CQM_TRY(run_maca(h, 1, h->n_far, h->far_rc.p, h->farC, h->farD, h->far_rank, nullptr,
                    (size_t)h->n_far * h->rank_cap * h->p * h->p, h->h_far_rank));
   cqm_setup_info& I = h->info;
@@ -452,6 +651,64 @@ int build_maca(cqm_handle* h) {
     I.rank_max = std::max(I.rank_max, h->h_far_rank[b]);
   }
   I.far_coupling = (int64_t)h->n_far * h->p * h->p;
+  return CQM_OK;
+}
+
+// Work items of the apply: every row's blocks split into consecutive runs of
+// about equal work (rank, times #r #c for the near field), so that long rows
+// do not serialise on one SM; about 4 items per SM in total.
+int build_work_items(cqm_handle* h) {
+  const int target = 4 * 152;
+  auto split = [&](const std::vector<int>& rows, const std::vector<int2>& blk,
+                   const std::vector<int>& rank, bool near, std::vector<int4>& items,
+                   std::vector<int>& ptr) {
+    std::vector<int> start(h->n_nodes + 1, 0);
+    for (auto& b : blk) start[b.x + 1]++;
+    for (int r = 0; r < h->n_nodes; ++r) start[r + 1] += start[r];
+    auto weight = [&](int bi) -> double {
+      const int2 rc = blk[bi];
+      const double sz = near ? (double)(h->h_end[rc.x] - h->h_begin[rc.x]) * (h->h_end[rc.y] - h->h_begin[rc.y])
+                             : 1.0;
+      return std::max(1, rank[bi]) * sz;
+    };
+    double total = 0.0;
+    for (size_t bi = 0; bi < blk.size(); ++bi) total += weight((int)bi);
+    const double cap = std::max(1.0, total / target);
+    ptr.assign(1, 0);
+    for (int r : rows) {
+      int b0 = start[r];
+      double acc = 0.0;
+      for (int bi = start[r]; bi < start[r + 1]; ++bi) {
+        acc += weight(bi);
+        if (acc >= cap || bi + 1 == start[r + 1]) {
+          items.push_back(make_int4(r, b0, bi + 1, 0));
+          b0 = bi + 1;
+          acc = 0.0;
+        }
+      }
+      if (start[r + 1] == start[r]) items.push_back(make_int4(r, start[r], start[r], 0));
+      ptr.push_back((int)items.size());
+    }
+  };
+  std::vector<int4> fi, ni;
+  std::vector<int> fp, np;
+  split(h->h_far_rows, h->h_far, h->h_far_rank, false, fi, fp);
+  split(h->h_leaves, h->h_near, h->h_near_rank, true, ni, np);
+  h->n_far_items = (int)fi.size();
+  h->n_near_items = (int)ni.size();
+  CQM_TRY(h->far_items.allocate(h->alloc, std::max<size_t>(1, fi.size())));
+  CQM_TRY(h->near_items.allocate(h->alloc, std::max<size_t>(1, ni.size())));
+  CQM_TRY(h->far_item_ptr.allocate(h->alloc, fp.size()));
+  CQM_TRY(h->near_item_ptr.allocate(h->alloc, np.size()));
+  cudaStream_t S = h->stream;
+  if (!fi.empty()) CQM_CUDA_TRY(cudaMemcpyAsync(h->far_items.p, fi.data(), sizeof(int4) * fi.size(), cudaMemcpyHostToDevice, S));
+  if (!ni.empty()) CQM_CUDA_TRY(cudaMemcpyAsync(h->near_items.p, ni.data(), sizeof(int4) * ni.size(), cudaMemcpyHostToDevice, S));
+  CQM_CUDA_TRY(cudaMemcpyAsync(h->far_item_ptr.p, fp.data(), sizeof(int) * fp.size(), cudaMemcpyHostToDevice, S));
+  CQM_CUDA_TRY(cudaMemcpyAsync(h->near_item_ptr.p, np.data(), sizeof(int) * np.size(), cudaMemcpyHostToDevice, S));
+  const size_t part = std::max((size_t)h->n_far_items * 64, (size_t)h->n_near_items * 32) * h->Ls;
+  CQM_TRY(h->part_d.allocate(h->alloc, std::max<size_t>(1, part)));
+  CQM_TRY(h->part_f.allocate(h->alloc, std::max<size_t>(1, part)));
+  CQM_CUDA_TRY(cudaStreamSynchronize(S));  // host vectors go out of scope
   return CQM_OK;
 }
 

@@ -56,7 +56,49 @@ struct Quad {
   const double* ss_w[3];
   int ss_n[3];
   double near_ratio;
+  const double* t2;   // 2^(j/1024), j = 0..1023
+  const double2* cs;  // (cos, sin)(j pi / 512), j = 0..1023
 };
+
+// c * exp(-s r) in FP64 with table-driven argument reduction (the method of
+// Tang, ACM TOMS 15(2), 1989, for the exponential; the same for the circular
+// functions): x = -Re(s) r = (1024 k + j) ln2/1024 + f with |f| <= ln2/2048,
+// exp(x) = 2^k 2^(j/1024) exp(f); theta = Im(s) r = m pi/512 + g with
+// |g| <= pi/1024, cis(theta) = cis(m pi/512) cis(g).  The reduction constants
+// are split in two (Cody-Waite) so that n * hi is exact; exp(f), sin(g) and
+// cos(g) use their Taylor polynomials, whose omitted terms are below 1e-19
+// relative on these intervals.  About 20 FP64 instructions per value.
+__device__ __forceinline__ double2 cexp_c(double r, double c, double2 s, const Quad& q) {
+  const double x = -s.x * r;
+  if (!(x > -708.0)) return make_double2(0.0, 0.0);
+  if (x > 700.0) {  // growing kernel (R > 1); outside the table's exponent range
+    double sn, co;
+    sincos(s.y * r, &sn, &co);
+    const double e = exp(x) * c;
+    return make_double2(e * co, -e * sn);
+  }
+  const double nx = rint(x * 0x1.71547652b82fep+10);  // 1024 / ln 2
+  double f = fma(-nx, 0x1.62e42ff000000p-11, x);       // ln2/1024, high part
+  f = fma(-nx, -0x1.718432a1b0e26p-45, f);             // ln2/1024, low part
+  const long long n = (long long)nx;
+  const int j = (int)(n & 1023);
+  const long long k = (n - j) >> 10;
+  double e = fma(fma(fma(fma(f, 1.0 / 24.0, 1.0 / 6.0), f, 0.5), f, 1.0), f, 1.0);
+  e *= __ldg(q.t2 + j) * c;
+  e *= __longlong_as_double((k + 1023) << 52);          // 2^k, -1022 <= k <= 1010 here
+  const double th = s.y * r;
+  const double nt = rint(th * 0x1.45f306dc9c883p+7);   // 512 / pi
+  double g = fma(-nt, 0x1.921fb54400000p-8, th);       // pi/512, high part
+  g = fma(-nt, 0x1.0b4611a626331p-42, g);              // pi/512, low part
+  const int m = (int)((long long)nt & 1023);
+  const double g2 = g * g;
+  const double sg = g * fma(fma(g2, 1.0 / 120.0, -1.0 / 6.0), g2, 1.0);
+  const double cg = fma(fma(g2, 1.0 / 24.0, -0.5), g2, 1.0);
+  const double2 T = __ldg(q.cs + m);
+  const double co = T.x * cg - T.y * sg;
+  const double si = T.y * cg + T.x * sg;
+  return make_double2(e * co, -e * si);
+}
 
 enum { CASE_REGULAR = 0, CASE_NEAR = 1, CASE_VERT = 2, CASE_EDGE = 3, CASE_IDENT = 4 };
 
@@ -122,28 +164,12 @@ __device__ __forceinline__ void singular_vertices(const int* tri, int i, int j, 
   }
 }
 
-// w * exp(-s r) / (4 pi r) accumulated for NF frequencies.
-template <int NF>
-__device__ __forceinline__ void kernel_accumulate(double r, double w, const double2* s, int nf,
-                                                  double2* acc) {
-  const double c = w / (CQM_FOUR_PI * r);
-#pragma unroll
-  for (int f = 0; f < NF; ++f) {
-    if (f < nf) {
-      double e = exp(-s[f].x * r) * c;
-      double sn, cs;
-      sincos(s[f].y * r, &sn, &cs);
-      acc[f].x += e * cs;
-      acc[f].y -= e * sn;
-    }
-  }
-}
-
-// Accumulate this lane's share (points lane, lane+nlanes, ...) of the pair
-// integral (i, j) for nf <= NF frequencies into acc.
-template <int NF>
-__device__ void pair_accumulate(const Geom& g, const Quad& q, int i, int j, int cse, int lane,
-                                int nlanes, const double2* s, int nf, double2* acc) {
+// Visit this lane's share (points lane, lane+nlanes, ...) of the quadrature
+// points of pair (i, j): f(k, r, c) with k the point's index within the pair,
+// r = |x - y| and c = weight / (4 pi r) (weights include the area factors).
+template <class F>
+__device__ __forceinline__ void pair_points(const Geom& g, const Quad& q, int i, int j, int cse,
+                                            int lane, int nlanes, F&& f) {
   const double* Pi = g.P + 9 * i;
   const double* Pj = g.P + 9 * j;
   if (cse == CASE_REGULAR || cse == CASE_NEAR) {
@@ -164,7 +190,7 @@ __device__ void pair_accumulate(const Geom& g, const Quad& q, int i, int j, int 
       double d1 = (a0 * Pi[1] + a1 * Pi[4] + a2 * Pi[7]) - (b0 * Pj[1] + b1 * Pj[4] + b2 * Pj[7]);
       double d2 = (a0 * Pi[2] + a1 * Pi[5] + a2 * Pi[8]) - (b0 * Pj[2] + b1 * Pj[5] + b2 * Pj[8]);
       double r = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
-      kernel_accumulate<NF>(r, wa * wb * aa, s, nf, acc);
+      f(p, r, (wa * wb * aa) / (CQM_FOUR_PI * r));
     }
     return;
   }
@@ -193,8 +219,38 @@ __device__ void pair_accumulate(const Geom& g, const Quad& q, int i, int j, int 
     double d1 = (a0 * X[1] + a1 * X[4] + a2 * X[7]) - (b0 * Y[1] + b1 * Y[4] + b2 * Y[7]);
     double d2 = (a0 * X[2] + a1 * X[5] + a2 * X[8]) - (b0 * Y[2] + b1 * Y[5] + b2 * Y[8]);
     double r = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
-    kernel_accumulate<NF>(r, wt[p] * aa, s, nf, acc);
+    f(p, r, (wt[p] * aa) / (CQM_FOUR_PI * r));
   }
+}
+
+// Number of quadrature points of a pair of the given case.
+__device__ __forceinline__ int pair_npoints(const Quad& q, int cse) {
+  if (cse == CASE_REGULAR) return 49;
+  if (cse == CASE_NEAR) return q.n_near * q.n_near;
+  return q.ss_n[cse - CASE_VERT];
+}
+
+// c * exp(-s r) for NF frequencies, accumulated.
+template <int NF>
+__device__ __forceinline__ void kernel_accumulate_c(double r, double c, const double2* s, int nf,
+                                                    double2* acc, const Quad& q) {
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    if (f < nf) {
+      const double2 v = cexp_c(r, c, s[f], q);
+      acc[f].x += v.x;
+      acc[f].y += v.y;
+    }
+  }
+}
+
+// Accumulate this lane's share of the pair integral (i, j) for nf <= NF
+// frequencies into acc.
+template <int NF>
+__device__ void pair_accumulate(const Geom& g, const Quad& q, int i, int j, int cse, int lane,
+                                int nlanes, const double2* s, int nf, double2* acc) {
+  pair_points(g, q, i, j, cse, lane, nlanes,
+              [&](int, double r, double c) { kernel_accumulate_c<NF>(r, c, s, nf, acc, q); });
 }
 
 }  // namespace cqm

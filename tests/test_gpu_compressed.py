@@ -185,3 +185,43 @@ def test_solver_variants_agree(lib, precond, inner_fp32):
     op.close()
     assert info["converged"] == N // 2 + 1 and info["max_rel_residual"] <= 1e-13
     assert dense.rel_err(q, q_ref) <= 1e-10
+
+
+def test_point_cache_matches_direct_quadrature(lib):
+    """Cached near-field quadrature points give the MACA factors of the
+    direct quadrature (same pivots and ranks, entries equal to rounding)."""
+    m = synth.icosphere(3)
+    N, dt = 24, 0.1
+    a = _op(m, dt, N, cache_quadrature=1)
+    b = _op(m, dt, N, cache_quadrature=0)
+    ba, bb = a.blocks(), b.blocks()
+    assert np.array_equal(ba["near_rank"], bb["near_rank"])
+    assert np.array_equal(ba["far_rank"], bb["far_rank"])
+    rng = np.random.default_rng(9)
+    for k in rng.choice(len(ba["near"]), 20, replace=False):
+        Ca, Da = a.block_factors(0, int(k))
+        Cb, Db = b.block_factors(0, int(k))
+        ta = np.einsum("tij,tk->ijk", Ca, Da)
+        tb = np.einsum("tij,tk->ijk", Cb, Db)
+        assert np.linalg.norm(ta - tb) <= 1e-12 * np.linalg.norm(tb)
+    a.close()
+    b.close()
+
+
+@pytest.mark.parametrize("tensor_cores", [0, 1])
+def test_inner_operator_fp32_accuracy(lib, tensor_cores):
+    """The FP32 inner operator (SIMT, or TF32 tensor cores with the three-product
+    split) agrees with the FP64-accurate apply to FP32 accuracy, frequency by
+    frequency."""
+    m = synth.icosphere(4)
+    N, dt = 40, 0.1
+    op = _op(m, dt, N, tensor_cores=tensor_cores)
+    rng = np.random.default_rng(12)
+    x = rng.standard_normal((op.Ls, m.nt)) + 1j * rng.standard_normal((op.Ls, m.nt))
+    y = op.apply(x)
+    yi = op.apply_inner(x)
+    op.close()
+    err = np.linalg.norm(yi - y, axis=1) / np.linalg.norm(y, axis=1)
+    # FP32-class: the three-product TF32 split keeps ~21 bits per operand; a
+    # wrong fragment layout would give errors of order one
+    assert np.max(err) < 1e-5, err
