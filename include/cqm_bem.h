@@ -90,7 +90,7 @@ typedef struct cqm_params {
   double eta;             /* admissibility parameter (eq. qadm)            [1.0] */
   int32_t cheb_m;         /* Chebyshev points per axis, p = m^3 (m <= 4)   [4]   */
   double aca_eps;         /* MACA stopping tolerance (Alg. 2)              [1e-6] */
-  int32_t rank_cap;       /* rank slots reserved per block                 [32]  */
+  int32_t rank_cap;       /* rank slots reserved per block (1..64)         [32]  */
   int32_t gmres_restart;  /* Krylov dimension per cycle                    [50]  */
   int32_t gmres_max_iter; /* total Arnoldi steps cap                       [3000] */
   double gmres_tol;       /* relative residual target ||r_l|| <= tol ||ghat_l|| [1e-13] */
@@ -102,8 +102,9 @@ typedef struct cqm_params {
                              so results keep FP64 accuracy                [1]   */
   double inner_rtol;      /* with inner_fp32: a cycle ends once its residual
                              estimate fell by this factor                 [1e-5] */
-  int32_t tensor_cores;   /* H2MACA with inner_fp32: far coupling of the inner operator
-                             on the tensor cores (TF32, three-product split) [0] */
+  int32_t tensor_cores;   /* H2MACA with inner_fp32, m = 4: far coupling of the inner
+                             operator on the tcgen05 tensor cores (TF32, three-product
+                             split, TMEM accumulator); 0 = FP32 SIMT       [1]   */
   int32_t cache_quadrature; /* H2MACA: keep every near-field quadrature point (r and
                              weight / (4 pi r)) in device memory for the MACA
                              slices and fibres (16 bytes per point)       [1]   */

@@ -12,6 +12,17 @@ namespace cqm {
 static thread_local std::string g_last_error;
 void set_last_error(const std::string& msg) { g_last_error = msg; }
 
+int check_wait_flag(cqm_handle* h) {
+  int w = 0;
+  CQM_CUDA_TRY(cudaMemcpyAsync(&w, h->flag.p + 1, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CQM_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  if (w != 0) {
+    set_last_error("a bounded device wait expired in the tensor-core far coupling");
+    return CQM_ETIMEOUT;
+  }
+  return CQM_OK;
+}
+
 // Device scratch of a call: released when the call returns.
 struct Scratch {
   Allocator* a;
@@ -64,7 +75,7 @@ int cqm_params_default(cqm_params* p) {
   p->inner_rtol = 1e-5;
   p->exact_ff = 1;
   p->cache_quadrature = 1;
-  p->tensor_cores = 0;
+  p->tensor_cores = 1;
   p->allocator = nullptr;
   return CQM_OK;
 }
@@ -142,7 +153,7 @@ int cqm_bem_setup(const cqm_mesh* mesh, double dt, int32_t N, int32_t bdf_order,
   else cqm_params_default(&p);
   if ((p.mode != CQM_MODE_DENSE && p.mode != CQM_MODE_H2MACA) || p.g_sing < 1 || p.g_sing > 12 ||
       p.g_near < 1 || p.g_near > 12 || !(p.near_ratio >= 0.0) || p.n_min < 1 || !(p.eta > 0.0) ||
-      p.cheb_m < 1 || p.cheb_m > 4 || !(p.aca_eps > 0.0) || p.rank_cap < 1 ||
+      p.cheb_m < 1 || p.cheb_m > 4 || !(p.aca_eps > 0.0) || p.rank_cap < 1 || p.rank_cap > 64 ||
       (p.mode == CQM_MODE_H2MACA && p.n_min > 32) ||
       p.gmres_restart < 1 || p.gmres_max_iter < 1 || !(p.gmres_tol > 0.0) ||
       !(p.inner_rtol >= 0.0 && p.inner_rtol < 1.0)) {
@@ -364,7 +375,7 @@ int cqm_bem_apply_inner(cqm_handle* h, const double* x, double* y, int32_t mem) 
   if (mem == CQM_MEM_HOST)
     CQM_CUDA_TRY(cudaMemcpyAsync(y, dy, n * sizeof(double2), cudaMemcpyDeviceToHost, h->stream));
   CQM_CUDA_TRY(cudaStreamSynchronize(h->stream));
-  return CQM_OK;
+  return check_wait_flag(h);
 }
 
 int cqm_bem_solve_frequencies(cqm_handle* h, const double* ghat, double* qhat, int32_t mem,

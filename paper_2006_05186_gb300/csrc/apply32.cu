@@ -86,12 +86,13 @@ __global__ void __launch_bounds__(256) k_far_coupling_f32(int Ls, int cap,
 __global__ void k_far_reduce_f32(int Ls, const int* __restrict__ rows,
                                  const int* __restrict__ item_ptr, const float2* __restrict__ part,
                                  float2* __restrict__ yhat) {
+  constexpr int P = 64;
   const int k = blockIdx.x;  // index into the list of far rows
   const int r = rows[k];
-  for (int e = threadIdx.x; e < 64 * Ls; e += blockDim.x) {
+  for (int e = threadIdx.x; e < P * Ls; e += blockDim.x) {
     float2 a = make_float2(0.f, 0.f);
-    for (int it = item_ptr[k]; it < item_ptr[k + 1]; ++it) a = cadd(a, part[(size_t)it * 64 * Ls + e]);
-    float2* o = yhat + (size_t)r * 64 * Ls + e;
+    for (int it = item_ptr[k]; it < item_ptr[k + 1]; ++it) a = cadd(a, part[(size_t)it * P * Ls + e]);
+    float2* o = yhat + (size_t)r * P * Ls + e;
     *o = cadd(*o, a);
   }
 }
@@ -193,6 +194,7 @@ int setup_f32_kernels(cqm_handle* h) {
 
 int far_coupling_f32(cqm_handle* h) {
   const int n = h->n_far_items;
+  if (h->p != 64) return far_coupling_generic_f32(h);  // the tiled kernels are written for m = 4
   if (h->params.tensor_cores && h->p == 64) {
     CQM_TRY(far_coupling_tc(h));
     k_far_reduce_f32<<<(unsigned)h->h_far_rows.size(), 256, 0, h->stream>>>(

@@ -138,14 +138,15 @@ __global__ void k_near_reduce_d(int M, int Ls, const int* __restrict__ leaves,
 }
 
 // yhat_r += sum of row k's item tiles, in item order (FP64).
-__global__ void k_far_reduce_d(int Ls, const int* __restrict__ rows, const int* __restrict__ item_ptr,
-                               const double2* __restrict__ part, double2* __restrict__ yhat) {
+__global__ void k_far_reduce_d(int Ls, int p, const int* __restrict__ rows,
+                               const int* __restrict__ item_ptr, const double2* __restrict__ part,
+                               double2* __restrict__ yhat) {
   const int k = blockIdx.x;
   const int r = rows[k];
-  for (int e = threadIdx.x; e < 64 * Ls; e += blockDim.x) {
+  for (int e = threadIdx.x; e < p * Ls; e += blockDim.x) {
     double2 a = make_double2(0.0, 0.0);
-    for (int it = item_ptr[k]; it < item_ptr[k + 1]; ++it) a = cadd(a, part[(size_t)it * 64 * Ls + e]);
-    double2* o = yhat + (size_t)r * 64 * Ls + e;
+    for (int it = item_ptr[k]; it < item_ptr[k + 1]; ++it) a = cadd(a, part[(size_t)it * p * Ls + e]);
+    double2* o = yhat + (size_t)r * p * Ls + e;
     *o = cadd(*o, a);
   }
 }
@@ -236,7 +237,7 @@ int far_coupling_ff(cqm_handle* h) {
       h->Ls, h->p, h->rank_cap, h->far_items.p, h->far_rc.p, h->far_rank.p, h->farC.p, h->farD.p,
       h->xhat.p, h->part_d.p);
   k_far_reduce_d<<<(unsigned)h->h_far_rows.size(), 256, 0, h->stream>>>(
-      h->Ls, h->d_far_rows.p, h->far_item_ptr.p, h->part_d.p, h->yhat.p);
+      h->Ls, h->p, h->d_far_rows.p, h->far_item_ptr.p, h->part_d.p, h->yhat.p);
   CQM_CHECK_LAUNCH();
   return CQM_OK;
 }

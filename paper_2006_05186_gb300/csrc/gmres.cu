@@ -328,6 +328,7 @@ int gmres_solve(cqm_handle* h, const double2* d_b, double2* d_x, cqm_solve_info*
   GM_TRY(cu(cudaMemcpyAsync(bn.data(), W.bnorm.p, sizeof(double) * Ls, cudaMemcpyDeviceToHost, S)));
   GM_TRY(cu(cudaMemcpyAsync(conv.data(), W.converged.p, sizeof(int) * Ls, cudaMemcpyDeviceToHost, S)));
   GM_TRY(cu(cudaStreamSynchronize(S)));
+  GM_TRY(check_wait_flag(h));
   for (int l = 0; l < Ls; ++l) rel[l] = bn[l] > 0.0 ? rel[l] / bn[l] : 0.0;
   float ms = 0.f;
   cudaEventElapsedTime(&ms, e0, e1);

@@ -517,6 +517,15 @@ static int apply_t(cqm_handle* h, const OpView<R>& V, const double2* x, double2*
   return CQM_OK;
 }
 
+int far_coupling_generic_f32(cqm_handle* h) {
+  ProfScope ps_(h, CQM_K_FAR_COUPLING);
+  k_far_coupling<float><<<(unsigned)h->h_far_rows.size(), 256, coupling_smem<float>(h->p), h->stream>>>(
+      h->Ls, h->p, h->rank_cap, h->d_far_rows.p, h->far_rowptr.p, h->far_rc.p, h->far_rank.p,
+      h->farC_f.p, h->farD_f.p, h->xhat_f.p, h->yhat_f.p);
+  CQM_CHECK_LAUNCH();
+  return CQM_OK;
+}
+
 int apply_compressed(cqm_handle* h, const double2* x, double2* y) {
   OpView<double> V{h->nearC.p, h->nearD.p, h->farC.p, h->farD.p, h->Uleaf.p, h->Etr.p,
                    h->xhat.p, h->yhat.p};

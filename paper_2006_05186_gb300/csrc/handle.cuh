@@ -135,6 +135,7 @@ int build_f32_copy(cqm_handle* h);
 int setup_f32_kernels(cqm_handle* h);
 int near_apply_f32(cqm_handle* h, const double2* x, double2* y);
 int far_coupling_f32(cqm_handle* h);
+int far_coupling_generic_f32(cqm_handle* h);
 
 // tc.cu (tensor-core far coupling of the inner operator)
 int setup_tc_kernels(cqm_handle* h);
@@ -165,6 +166,10 @@ struct ProfScope {
 };
 void prof_resolve(cqm_handle* h);
 void prof_release(cqm_handle* h);
+
+// flag[1]: a kernel's bounded wait expired (it recorded the error and returned).
+// Reads the word after the stream's work so far; CQM_ETIMEOUT if it is set.
+int check_wait_flag(cqm_handle* h);
 
 // operator dispatch: FP64 operator, and the operator of the inner GMRES
 // iterations (its FP32 copy when mixed precision is on)

@@ -1,166 +1,284 @@
-// Far-field coupling of the inner operator on the tensor cores.
+// Far-field coupling of the inner operator on the fifth-generation tensor
+// cores (tcgen05, accumulator in TMEM).
 //
-// yhat_r[mu][l] += sum_{b=(r,c)} sum_t sum_nu C_{b,t}[mu][nu] (d_t[l] xhat_c[nu][l])
-// (eq. lrfinal at all frequencies) is a dense contraction.  Written in real
-// arithmetic it is, per (b, t), a 128 x 128 by 128 x L product
-//   [Re y; Im y] += [[Re C, -Im C], [Im C, Re C]] [Re x~; Im x~],
-// x~ = d_t (.) xhat_c.  Each warp owns 16 of the 128 output rows and all
-// frequency columns of a chunk; the product runs on mma.sync m16n8k8 TF32 with
-// each operand split as hi + lo (TF32 each) and three products
-// hi*hi + hi*lo + lo*hi accumulated in FP32, which keeps FP32-level accuracy
-// (the inner operator is FP32; FP64-accurate residuals are computed apart).
-// Work items and the per-row reduction of their partial tiles are the same as
-// for the SIMT kernel.
+// yhat_r[mu][l] += sum_{b=(r,c)} sum_t sum_nu C_{b,t}[mu][nu] d_{b,t}[l] xhat_c[nu][l]
+// (eq. lrfinal for all frequencies at once).  In real arithmetic each rank term
+// (b, t) is one GEMM with M = 128, K = 128 and N = the frequency columns:
+//   [Re y; Im y] += [[Re C, -Im C], [Im C, Re C]] [Re x~; Im x~],  x~ = d_t (.) xhat_c,
+// and a work item (a row cluster and a run of its far blocks) sums all of its
+// (b, t) in one TMEM accumulator.  Every operand is split into two tf32 parts
+// and the three products lo*hi + hi*lo + hi*hi are accumulated in fp32, which
+// keeps fp32-level accuracy (the inner operator is fp32; the FP64-accurate
+// residual is computed apart).
+//
+// One CTA per work item: 8 producer warps build each K-slab (16 Chebyshev
+// indices nu, real and imaginary parts: 32 real-form K) in the canonical
+// K-major layout, in a ring of 3 slabs guarded by mbarriers; one thread of
+// warp 0 issues 4 x 3 MMAs per slab and frees the slab with tcgen05.commit;
+// warps 1-4 finally copy the accumulator from TMEM into the item's partial
+// tile, which the per-row reduction adds in item order (as for the SIMT kernel).
+// Every wait is bounded in time; on expiry the kernel records an error in
+// *err, stops issuing work, lets issued MMAs drain, frees TMEM and returns.
 #include <algorithm>
 
 #include "handle.cuh"
+#include "umma.cuh"
 
 namespace cqm {
 
-__device__ __forceinline__ uint32_t to_tf32(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return r;
-}
+namespace {
+constexpr int TP = 64;          // Chebyshev points per cluster (m = 4)
+constexpr int NSTAGE = 3;       // slabs in the ring
+constexpr int NPROD = 256;      // producer threads (warps 1..8)
+constexpr int NTHREADS = 32 + NPROD;
+constexpr uint32_t A_PLANE = 128u * 128u;  // bytes: 128 rows x 32 tf32
+constexpr int ERR_TIMEOUT = 1;
 
-__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
-  hi = to_tf32(x);
-  lo = to_tf32(x - __uint_as_float(hi));
-}
-
-__device__ __forceinline__ void mma_tf32(float* d, const uint32_t* a, const uint32_t* b) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-      "{%8,%9}, {%0,%1,%2,%3};\n"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
-constexpr int TC_P = 64;      // Chebyshev points per cluster (m = 4)
-constexpr int TC_CPAD = 68;   // row stride of the staged C planes (conflict-free A loads)
-
-// Row stride of the staged real x~: = 8 or 24 mod 32 words, so that the four
-// rows a B fragment reads fall into distinct banks.
-__host__ __device__ constexpr int xt_stride(int nc) { return nc + ((40 - (nc % 32)) % 32); }
-
-// NT = 8-column tiles per frequency chunk (chunk = 8 NT columns).
 template <int NT>
-__global__ void __launch_bounds__(256, 1) k_far_coupling_tc(int Ls, int cap,
-                                                            const int4* __restrict__ items,
-                                                            const int2* __restrict__ blocks,
-                                                            const int* __restrict__ rank,
-                                                            const float2* __restrict__ Cf,
-                                                            const float2* __restrict__ Df,
-                                                            const float2* __restrict__ xhat,
-                                                            float2* __restrict__ part) {
-  constexpr int NC = 8 * NT;          // columns per chunk
-  constexpr int XT_STRIDE = xt_stride(NC);
-  extern __shared__ __align__(16) unsigned char smraw[];
-  float2* Xh = (float2*)smraw;                       // TC_P x NC   (xhat chunk, complex)
-  float* Xt = (float*)(Xh + TC_P * NC);              // 128 x NC    (real [Re x~; Im x~])
-  float* Cr = Xt + 128 * XT_STRIDE;                  // TC_P x TC_CPAD
-  float* Ci = Cr + TC_P * TC_CPAD;                   // TC_P x TC_CPAD
-  float2* Ds = (float2*)(Ci + TC_P * TC_CPAD);       // NC
-  const int4 it = items[blockIdx.x];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int g = lane >> 2, tq = lane & 3;
-  const int row0 = 16 * w;  // rows row0 .. row0+15 of the real 128-row output
-  for (int l0 = 0; l0 < Ls; l0 += NC) {
-    float acc[NT][4];
+struct TcCfg {
+  static constexpr int NC = 16 * NT;                       // frequency columns per chunk (MMA N)
+  static constexpr uint32_t B_PLANE = (uint32_t)NC * 128u;  // NC rows x 32 tf32
+  static constexpr uint32_t STAGE = 2 * A_PLANE + 2 * B_PLANE;
+  static constexpr uint32_t TCOLS = NC <= 32 ? 32 : NC <= 64 ? 64 : NC <= 128 ? 128 : 256;
+  static constexpr size_t SMEM = (size_t)NSTAGE * STAGE + 1024;
+};
+
+__device__ __forceinline__ void st_split4(unsigned char* hi, unsigned char* lo, uint32_t off, float a,
+                                          float b, float c, float d) {
+  float4 h, l;
+  umma::split_tf32(a, h.x, l.x);
+  umma::split_tf32(b, h.y, l.y);
+  umma::split_tf32(c, h.z, l.z);
+  umma::split_tf32(d, h.w, l.w);
+  *(float4*)(hi + off) = h;
+  *(float4*)(lo + off) = l;
+}
+}  // namespace
+
+template <int NT>
+__global__ void __launch_bounds__(NTHREADS, 1)
+    k_far_coupling_tc(int Ls, int cap, const int4* __restrict__ items, const int2* __restrict__ blocks,
+                      const int* __restrict__ rank, const float2* __restrict__ Cf,
+                      const float2* __restrict__ Df, const float2* __restrict__ xhat,
+                      float2* __restrict__ part, int* __restrict__ err) {
+  using namespace umma;
+  using K = TcCfg<NT>;
+  constexpr int NC = K::NC;
+  constexpr int NB = (4 * NC + NPROD - 1) / NPROD;  // B items per producer thread and slab
+  extern __shared__ unsigned char smraw[];
+  __shared__ __align__(8) uint64_t full_bar[NSTAGE];
+  __shared__ __align__(8) uint64_t empty_bar[NSTAGE];
+  __shared__ __align__(8) uint64_t done_bar;
+  __shared__ __align__(8) uint64_t fin_bar;
+  __shared__ uint32_t tmem_sh;
+  __shared__ volatile int abort_sh;
+  __shared__ volatile int never_sh;
+  unsigned char* ring = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int4 it = items[blockIdx.x];  // (row, first block, end block, -)
+
+  if (tid == 0) {
+    for (int s = 0; s < NSTAGE; ++s) {
+      mbar_init(&full_bar[s], NPROD);
+      mbar_init(&empty_bar[s], 1);
+    }
+    mbar_init(&done_bar, 1);
+    mbar_init(&fin_bar, 1);
+    abort_sh = 0;
+    never_sh = 0;
+    mbar_init_fence();
+  }
+  if (warp == 0) tmem_alloc(&tmem_sh, K::TCOLS);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_sh;
+
+  int nwork = 0;  // rank terms of the item; none leaves the tile zero
+  for (int bi = it.y; bi < it.z; ++bi) nwork += rank[bi];
+
+  uint32_t use = 0;  // slab uses so far: the same sequence in every role
+  int chunk = 0;
+  for (int l0 = 0; l0 < Ls; l0 += NC, ++chunk) {
+    if (warp == 0) {
+      // ---------------------------------------------------------------- MMA
+      constexpr uint32_t idesc = idesc_tf32(128, NC);
+      uint32_t acc = 0;
+      for (int k = 0; k < 4 * nwork; ++k, ++use) {
+        const int s = (int)(use % NSTAGE);
+        const bool ok = mbar_wait(&full_bar[s], (use / NSTAGE) & 1u, &abort_sh, err, ERR_TIMEOUT);
+        tc_fence_after();
+        if (ok && lane == 0) {
+          const uint32_t a_hi = smem_u32(ring + (size_t)s * K::STAGE), a_lo = a_hi + A_PLANE;
+          const uint32_t b_hi = a_lo + A_PLANE, b_lo = b_hi + K::B_PLANE;
 #pragma unroll
-    for (int n = 0; n < NT; ++n)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) acc[n][q] = 0.f;
-    for (int bi = it.y; bi < it.z; ++bi) {
-      const int c = blocks[bi].y;
-      __syncthreads();
-      for (int e = threadIdx.x; e < TC_P * NC; e += blockDim.x) {
-        const int nu = e / NC, l = e - nu * NC;
-        Xh[e] = (l0 + l < Ls) ? xhat[((size_t)c * TC_P + nu) * Ls + l0 + l] : make_float2(0.f, 0.f);
+          for (int ks = 0; ks < 4; ++ks) {
+            const uint32_t o = 256u * ks;
+            mma_tf32(tmem, sdesc(a_lo + o), sdesc(b_hi + o), idesc, acc);
+            mma_tf32(tmem, sdesc(a_hi + o), sdesc(b_lo + o), idesc, 1u);
+            mma_tf32(tmem, sdesc(a_hi + o), sdesc(b_hi + o), idesc, 1u);
+            acc = 1u;
+          }
+          mma_commit(&empty_bar[s]);
+        }
+        __syncwarp();
       }
-      const int rk = rank[bi];
-      for (int tt = 0; tt < rk; ++tt) {
-        __syncthreads();
-        const float2* Ct = Cf + ((size_t)bi * cap + tt) * TC_P * TC_P;
-        for (int e = threadIdx.x; e < TC_P * TC_P; e += blockDim.x) {
-          const float2 v = Ct[e];
-          const int mu = e >> 6, nu = e & 63;
-          Cr[mu * TC_CPAD + nu] = v.x;
-          Ci[mu * TC_CPAD + nu] = v.y;
+      if (lane == 0 && nwork > 0) mma_commit(&done_bar);
+      __syncwarp();
+    } else {
+      // ---------------------------------------------------------- producers
+      // Slabs in the order (block b, nu slab j, rank term t): the 16 rows of
+      // xhat_c of slab j are loaded once per (b, j) and reused for every t;
+      // the C and d loads of the next slab are issued before the current
+      // slab is built, so their latency overlaps the wait and the build.
+      const int p = tid - 32;
+      const int amu = p & 63, aq = p >> 6;  // A: row mu, nu quad
+      auto load_cd = [&](int bi, int j, int tt, float4& c01, float4& c23, float2 (&dv)[NB]) {
+        const float4* cs = (const float4*)(Cf + ((size_t)bi * cap + tt) * TP * TP + amu * TP + 16 * j + 4 * aq);
+        c01 = cs[0];
+        c23 = cs[1];
+        const float2* Dt = Df + ((size_t)bi * cap + tt) * Ls;
+#pragma unroll
+        for (int i = 0; i < NB; ++i) {
+          const int e = p + NPROD * i;
+          const int lg = l0 + e % NC;
+          dv[i] = (e < 4 * NC && lg < Ls) ? Dt[lg] : make_float2(0.f, 0.f);
         }
-        for (int l = threadIdx.x; l < NC; l += blockDim.x)
-          Ds[l] = (l0 + l < Ls) ? Df[((size_t)bi * cap + tt) * Ls + l0 + l] : make_float2(0.f, 0.f);
-        __syncthreads();
-        for (int e = threadIdx.x; e < TC_P * NC; e += blockDim.x) {
-          const int nu = e / NC, l = e - nu * NC;
-          const float2 x = Xh[e], d = Ds[l];
-          Xt[nu * XT_STRIDE + l] = fmaf(d.x, x.x, -d.y * x.y);
-          Xt[(nu + TC_P) * XT_STRIDE + l] = fmaf(d.x, x.y, d.y * x.x);
+      };
+      auto load_x = [&](int bi, int j, float2 (&xv)[NB][4]) {
+        const float2* xc = xhat + (size_t)blocks[bi].y * TP * Ls;
+#pragma unroll
+        for (int i = 0; i < NB; ++i) {
+          const int e = p + NPROD * i;
+          const int q = e / NC, lg = l0 + e - q * NC;
+          const bool in = e < 4 * NC && lg < Ls;
+#pragma unroll
+          for (int v = 0; v < 4; ++v)
+            xv[i][v] = in ? xc[(size_t)(16 * j + 4 * q + v) * Ls + lg] : make_float2(0.f, 0.f);
         }
-        __syncthreads();
-#pragma unroll 2
-        for (int kk = 0; kk < 128; kk += 8) {
-          // A fragment: rows row0 + g (+8), columns kk + tq (+4)
-          float av[4];
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const int row = row0 + g + ((q & 1) ? 8 : 0);
-            const int k = kk + tq + ((q & 2) ? 4 : 0);
-            const int mu = row & 63, nu = k & 63;
-            const bool im_row = row >= 64, im_col = k >= 64;
-            float v;
-            if (!im_row) v = im_col ? -Ci[mu * TC_CPAD + nu] : Cr[mu * TC_CPAD + nu];
-            else v = im_col ? Cr[mu * TC_CPAD + nu] : Ci[mu * TC_CPAD + nu];
-            av[q] = v;
+      };
+      int bi = it.y, j = 0, tt = 0;
+      while (bi < it.z && rank[bi] == 0) ++bi;
+      float4 c01 = make_float4(0.f, 0.f, 0.f, 0.f), c23 = c01;
+      float2 dv[NB], xv[NB][4];
+      if (bi < it.z) {
+        load_x(bi, 0, xv);
+        load_cd(bi, 0, 0, c01, c23, dv);
+      }
+      for (; bi < it.z; ++use) {
+        int nb = bi, nj = j, nt = tt + 1;
+        if (nt == rank[bi]) {
+          nt = 0;
+          if (++nj == 4) {
+            nj = 0;
+            do ++nb; while (nb < it.z && rank[nb] == 0);
           }
-          uint32_t ah[4], al[4];
+        }
+        const bool has_next = nb < it.z, newx = has_next && nt == 0;
+        float4 c01n = c01, c23n = c23;
+        float2 dvn[NB], xvn[NB][4];
+        if (has_next) {
+          load_cd(nb, nj, nt, c01n, c23n, dvn);
+          if (newx) load_x(nb, nj, xvn);
+        }
+        const int s = (int)(use % NSTAGE);
+        const uint32_t round = use / NSTAGE;
+        if (round > 0) mbar_wait(&empty_bar[s], (round - 1) & 1u, &abort_sh, err, ERR_TIMEOUT);
+        if (!abort_sh) {
+          unsigned char* Ahi = ring + (size_t)s * K::STAGE;
+          unsigned char* Alo = Ahi + A_PLANE;
+          unsigned char* Bhi = Alo + A_PLANE;
+          unsigned char* Blo = Bhi + K::B_PLANE;
+          // A slab: K groups q (Re x~ of nu) and 4 + q (Im x~ of nu), rows mu and 64 + mu
+          st_split4(Ahi, Alo, core_off(amu, 4 * aq), c01.x, c01.z, c23.x, c23.z);
+          st_split4(Ahi, Alo, core_off(amu, 16 + 4 * aq), -c01.y, -c01.w, -c23.y, -c23.w);
+          st_split4(Ahi, Alo, core_off(64 + amu, 4 * aq), c01.y, c01.w, c23.y, c23.w);
+          st_split4(Ahi, Alo, core_off(64 + amu, 16 + 4 * aq), c01.x, c01.z, c23.x, c23.z);
+          // B slab: row l, Re x~ at K group q, Im x~ at K group 4 + q
 #pragma unroll
-          for (int q = 0; q < 4; ++q) split_tf32(av[q], ah[q], al[q]);
+          for (int i = 0; i < NB; ++i) {
+            const int e = p + NPROD * i;
+            if (e < 4 * NC) {
+              const int q = e / NC, l = e - q * NC;
+              float re[4], imv[4];
 #pragma unroll
-          for (int n = 0; n < NT; ++n) {
-            const float b0 = Xt[(kk + tq) * XT_STRIDE + 8 * n + g];
-            const float b1 = Xt[(kk + tq + 4) * XT_STRIDE + 8 * n + g];
-            uint32_t bh[2], bl[2];
-            split_tf32(b0, bh[0], bl[0]);
-            split_tf32(b1, bh[1], bl[1]);
-            mma_tf32(acc[n], al, bh);
-            mma_tf32(acc[n], ah, bl);
-            mma_tf32(acc[n], ah, bh);
+              for (int v = 0; v < 4; ++v) {
+                re[v] = fmaf(dv[i].x, xv[i][v].x, -dv[i].y * xv[i][v].y);
+                imv[v] = fmaf(dv[i].x, xv[i][v].y, dv[i].y * xv[i][v].x);
+              }
+              st_split4(Bhi, Blo, core_off(l, 4 * q), re[0], re[1], re[2], re[3]);
+              st_split4(Bhi, Blo, core_off(l, 16 + 4 * q), imv[0], imv[1], imv[2], imv[3]);
+            }
           }
+          fence_async_shared();
+        }
+        mbar_arrive(&full_bar[s]);
+        bi = nb;
+        j = nj;
+        tt = nt;
+        c01 = c01n;
+        c23 = c23n;
+#pragma unroll
+        for (int i = 0; i < NB; ++i) {
+          dv[i] = dvn[i];
+          if (newx)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) xv[i][v] = xvn[i][v];
         }
       }
     }
-    // D fragment: rows row0 + g (+8), columns 8n + 2 tq (+1)
-    const bool im = row0 >= 64;
+    // ------------------------------------------- epilogue: TMEM -> partial tile
+    if (warp >= 1 && warp <= 4) {
+      const int qd = warp & 3;  // TMEM lanes 32 qd .. 32 qd + 31 belong to this warp
+      const int m = 32 * qd + lane, mu = m & 63, im = m >> 6;
+      bool ok = nwork > 0 && mbar_wait(&done_bar, (uint32_t)chunk & 1u, &abort_sh, err, ERR_TIMEOUT);
+      ok = __all_sync(0xffffffffu, ok);
+      tc_fence_after();
+      float* dst = (float*)(part + ((size_t)blockIdx.x * TP + mu) * Ls) + im;
+      for (int c0 = 0; c0 < NC; c0 += 16) {
+        uint32_t v[16];
+        if (ok) {
+          tmem_ld16(tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)c0, v);
+          tmem_wait_ld();
+        } else {
 #pragma unroll
-    for (int n = 0; n < NT; ++n)
+          for (int i = 0; i < 16; ++i) v[i] = 0u;
+        }
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int row = row0 + g + ((q & 2) ? 8 : 0);
-        const int l = l0 + 8 * n + 2 * tq + (q & 1);
-        if (l < Ls) {
-          float* o = (float*)&part[((size_t)blockIdx.x * TC_P + (row & 63)) * Ls + l];
-          o[im ? 1 : 0] = acc[n][q];
+        for (int i = 0; i < 16; ++i) {
+          const int l = l0 + c0 + i;
+          if (l < Ls) dst[2 * l] = __uint_as_float(v[i]);
         }
       }
+      tc_fence_before();
+    }
+    __syncthreads();
+    tc_fence_after();
+  }
+  // ------------------------------------------------------------------ teardown
+  if (warp == 0) {
+    // every MMA this thread issued has finished before TMEM is released
+    if (lane == 0) mma_commit(&fin_bar);
+    __syncwarp();
+    mbar_wait(&fin_bar, 0u, &never_sh, err, ERR_TIMEOUT);
+    tc_fence_after();
+    __syncwarp();
+    tmem_dealloc(tmem, K::TCOLS);
   }
 }
 
-template <int NT>
-static size_t tc_smem() {
-  constexpr int NC = 8 * NT;
-  return sizeof(float2) * TC_P * NC + sizeof(float) * 128 * xt_stride(NC) +
-         2 * sizeof(float) * TC_P * TC_CPAD + sizeof(float2) * NC;
+static int nt_for(int Ls) {
+  const int nchunk = (Ls + 159) / 160;
+  const int per = (Ls + nchunk - 1) / nchunk;
+  return std::max(1, std::min(10, (per + 15) / 16));
 }
 
-static int nt_for(int Ls) { return std::min(17, std::max(1, (Ls + 7) / 8)); }
-
 int setup_tc_kernels(cqm_handle* h) {
-#define TC_SETUP(N)                                                                             \
+#define TC_SETUP(N)                                                                                \
   CQM_CUDA_TRY(cudaFuncSetAttribute(k_far_coupling_tc<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                    (int)tc_smem<N>()));
-  TC_SETUP(1) TC_SETUP(2) TC_SETUP(3) TC_SETUP(4) TC_SETUP(5) TC_SETUP(6) TC_SETUP(8)
-  TC_SETUP(9) TC_SETUP(12) TC_SETUP(17)
+                                    (int)TcCfg<N>::SMEM));
+  TC_SETUP(1) TC_SETUP(2) TC_SETUP(3) TC_SETUP(4) TC_SETUP(5)
+  TC_SETUP(6) TC_SETUP(7) TC_SETUP(8) TC_SETUP(9) TC_SETUP(10)
 #undef TC_SETUP
   return CQM_OK;
 }
@@ -168,22 +286,18 @@ int setup_tc_kernels(cqm_handle* h) {
 int far_coupling_tc(cqm_handle* h) {
   const int n = h->n_far_items;
   ProfScope ps_(h, CQM_K_FAR_COUPLING);
-#define TC_LAUNCH(N)                                                                            \
-  k_far_coupling_tc<N><<<n, 256, tc_smem<N>(), h->stream>>>(h->Ls, h->rank_cap, h->far_items.p, \
-                                                             h->far_rc.p, h->far_rank.p, h->farC_f.p, \
-                                                             h->farD_f.p, h->xhat_f.p, h->part_f.p)
-  const int nt = nt_for(h->Ls);
-  if (nt <= 1) TC_LAUNCH(1);
-  else if (nt <= 2) TC_LAUNCH(2);
-  else if (nt <= 3) TC_LAUNCH(3);
-  else if (nt <= 4) TC_LAUNCH(4);
-  else if (nt <= 5) TC_LAUNCH(5);
-  else if (nt <= 6) TC_LAUNCH(6);
-  else if (nt <= 8) TC_LAUNCH(8);
-  else if (nt <= 9) TC_LAUNCH(9);
-  else if (nt <= 12) TC_LAUNCH(12);
-  else TC_LAUNCH(17);
-#undef TC_LAUNCH
+#define TC_CASE(N)                                                                                 \
+  case N:                                                                                          \
+    k_far_coupling_tc<N><<<n, NTHREADS, TcCfg<N>::SMEM, h->stream>>>(                              \
+        h->Ls, h->rank_cap, h->far_items.p, h->far_rc.p, h->far_rank.p, h->farC_f.p, h->farD_f.p,  \
+        h->xhat_f.p, h->part_f.p, h->flag.p + 1);                                                      \
+    break;
+  switch (nt_for(h->Ls)) {
+    TC_CASE(1) TC_CASE(2) TC_CASE(3) TC_CASE(4) TC_CASE(5)
+    TC_CASE(6) TC_CASE(7) TC_CASE(8) TC_CASE(9) TC_CASE(10)
+    default: break;
+  }
+#undef TC_CASE
   CQM_CHECK_LAUNCH();
   return CQM_OK;
 }

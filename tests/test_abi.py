@@ -53,6 +53,7 @@ def test_strerror_and_defaults(lib):
     assert b"invalid" in lib.cqm_bem_strerror(1)
     p = _lib.default_params()
     assert p.mode == _lib.MODE_H2MACA and p.n_min == 32 and p.eta == 1.0 and p.cheb_m == 4
+    assert p.tensor_cores == 1 and p.inner_fp32 == 1 and p.rank_cap == 32
     assert p.aca_eps == 1e-6 and p.g_sing == 5 and p.gmres_tol == 1e-13
     assert lib.cqm_params_default(None) == _lib.CQM_EINVAL
 
@@ -74,5 +75,15 @@ def test_setup_rejects_bad_arguments_on_host(lib):
         assert st == _lib.CQM_EINVAL
         assert h.value is None
     assert lib.cqm_bem_setup(None, 0.1, 4, 2, None, None, C.byref(h)) == _lib.CQM_EINVAL
+    tri = np.array([[0, 1, 2]], np.int32)
+    mesh = _lib.cqm_mesh(3, xyz.ctypes.data, 1, tri.ctypes.data)
+    for field, value in [("rank_cap", 65), ("rank_cap", 0), ("cheb_m", 5), ("cheb_m", 0),
+                         ("n_min", 33), ("inner_rtol", 1.0), ("eta", 0.0), ("g_sing", 13)]:
+        prm = _lib.cqm_params()
+        assert lib.cqm_params_default(C.byref(prm)) == 0
+        setattr(prm, field, value)
+        st = lib.cqm_bem_setup(C.byref(mesh), 0.1, 4, 2, C.byref(prm), None, C.byref(h))
+        assert st == _lib.CQM_EINVAL, (field, value)
+        assert h.value is None
     assert lib.cqm_bem_destroy(None) == 0
     assert len(lib.cqm_bem_last_error()) >= 0

@@ -59,26 +59,33 @@ def test_tree_and_partition_bit_exact(lib, name):
     op.close()
 
 
-def _h2_reference(m, N, dt, freqs, tree_ref, near, far):
+def _h2_reference(m, N, dt, freqs, tree_ref, near, far, cheb_m=4):
     s = cqm.frequencies(N, dt, 2)[freqs]
-    return h2.h2_matrices(m.xyz, m.tri, s, tree_ref, near, far, 4)
+    return h2.h2_matrices(m.xyz, m.tri, s, tree_ref, near, far, cheb_m)
 
 
-def test_apply_tight_eps_equals_h2_expanded(lib):
+@pytest.mark.parametrize("cheb_m", [4, 3, 2])
+def test_apply_tight_eps_equals_h2_expanded(lib, cheb_m):
+    """The FP64 apply equals the oracle's H^2-expanded matrices (MACA at a
+    tolerance below rounding) to 1e-10, and the FP32 inner operator to FP32
+    accuracy, for every supported number m of Chebyshev points per axis."""
     m = synth.icosphere(3)
     N, dt = 16, 0.1
-    op = _op(m, dt, N, aca_eps=1e-14, rank_cap=64)
+    op = _op(m, dt, N, aca_eps=1e-14, rank_cap=64, cheb_m=cheb_m)
     t_ref = cluster.build_tree(m.xyz, m.tri, 32)
     near, far = cluster.partition(t_ref, 1.0)
     Ls = op.Ls
-    V = _h2_reference(m, N, dt, np.arange(Ls), t_ref, near, far)
+    V = _h2_reference(m, N, dt, np.arange(Ls), t_ref, near, far, cheb_m)
     rng = np.random.default_rng(4)
     x = rng.standard_normal((Ls, m.nt)) + 1j * rng.standard_normal((Ls, m.nt))
     y = op.apply(x)
+    yi = op.apply_inner(x)
     for l in range(Ls):
         ref = V[l] @ x[l]
         err = np.linalg.norm(y[l] - ref) / np.linalg.norm(ref)
         assert err < 1e-10, (l, err)
+        err_i = np.linalg.norm(yi[l] - ref) / np.linalg.norm(ref)
+        assert err_i < 1e-5, (l, err_i)
     op.close()
 
 
@@ -167,8 +174,9 @@ def test_sphere5120_N256_sampled_frequencies(lib):
     op.close()
 
 
-@pytest.mark.parametrize("precond,inner_fp32", [(0, 0), (1, 0), (0, 1), (1, 1)])
-def test_solver_variants_agree(lib, precond, inner_fp32):
+@pytest.mark.parametrize("precond,inner_fp32,tensor_cores",
+                         [(0, 0, 1), (1, 0, 1), (0, 1, 1), (1, 1, 1), (1, 1, 0)])
+def test_solver_variants_agree(lib, precond, inner_fp32, tensor_cores):
     """Preconditioning and the FP32 inner operator change the iteration, not
     the answer: every variant meets the FP64 residual target and agrees with
     the plain FP64 solve to ~1e-10 in the time domain."""
@@ -179,7 +187,7 @@ def test_solver_variants_agree(lib, precond, inner_fp32):
     b = ref_op.rhs_plane_wave(p.direction, p.width, p.delay)
     q_ref = ref_op.solve(b)
     ref_op.close()
-    op = _op(m, dt, N, precond=precond, inner_fp32=inner_fp32)
+    op = _op(m, dt, N, precond=precond, inner_fp32=inner_fp32, tensor_cores=tensor_cores)
     q = op.solve(b)
     info = op.last_solve_info
     op.close()
