@@ -52,6 +52,17 @@ def _peaks():
 # 69); FP64 at the recipe's nominal 1.25 TFLOP/s (the probe measured 1.19).
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 FP64_PEAK_TFLOPS = 1.25
+FP32_PEAK_SOURCE = "unit counts x max SM clock (152 SMs x 128 FP32 lanes x 2 x 2.07 GHz)"
+# TF32 dense tensor peak: the measured bf16 cuBLAS rate (sustained: the kernel is
+# timed inside a seconds-long step) times the nominal tf32 / bf16 ratio 1.1 / 2.25.
+TF32_OVER_BF16 = 1.1 / 2.25
+
+
+def tf32_peak():
+    pk, src = _peaks()
+    bf16 = pk.get("bf16_tflops_sustained", pk["bf16_tflops"])
+    return bf16 * TF32_OVER_BF16, (f"{src} bf16 cuBLAS {bf16:.1f} TFLOP/s (sustained) x nominal "
+                                   f"tf32/bf16 ratio 1.1/2.25")
 
 
 def dist_init(ngpus):
@@ -138,22 +149,30 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
-def kernel_models(info, Ls, p):
+def kernel_models(info, Ls, p, tensor_cores):
     """Algorithmic work per launch of the contraction kernels and the peak
-    that bounds each: (flop count, peak TFLOP/s, description).
-    Complex multiply-add = 8 flops; coupling: sum_far rank * p^2 * Ls;
-    near field: sum_near rank * #r#c * Ls.  The float-float kernels issue 48
-    FP32 instructions per complex multiply-add (four exact products with
-    TwoSum accumulation); their work is counted in FP32 issue slots, 2 flops
-    each, against the FP32 peak."""
+    that bounds each.  Complex multiply-add = 8 flops; coupling:
+    sum_far rank * p^2 * Ls; near field: sum_near rank * #r#c * Ls.
+    The tensor-core coupling is counted by its useful flops against the TF32
+    tensor peak (its three-product split executes three times as many).  The
+    float-float kernels issue 48 FP32 instructions per complex multiply-add
+    (four exact products with TwoSum accumulation); their work is counted in
+    FP32 issue slots, 2 flops each, against the FP32 peak."""
     cmac_far = info["rank_sum_far"] * p * p * Ls
     cmac_near = info["near_rank_entries"] * Ls
-    return {
-        "far_coupling": (8.0 * cmac_far, FP32_PEAK_TFLOPS, "FP32 complex MAC, inner operator"),
-        "near_apply": (8.0 * cmac_near, FP32_PEAK_TFLOPS, "FP32 complex MAC, inner operator"),
-        "far_exact": (2.0 * 48 * cmac_far, FP32_PEAK_TFLOPS, "float-float complex MAC (FP32 issue)"),
-        "near_exact": (2.0 * 48 * cmac_near, FP32_PEAK_TFLOPS, "float-float complex MAC (FP32 issue)"),
+    fp32 = dict(bound="alu", peak=FP32_PEAK_TFLOPS, peak_source=FP32_PEAK_SOURCE)
+    models = {
+        "far_coupling": dict(fp32, flops=8.0 * cmac_far, what="FP32 complex MAC, inner operator"),
+        "near_apply": dict(fp32, flops=8.0 * cmac_near, what="FP32 complex MAC, inner operator"),
+        "far_exact": dict(fp32, flops=2.0 * 48 * cmac_far, what="float-float complex MAC (FP32 issue)"),
+        "near_exact": dict(fp32, flops=2.0 * 48 * cmac_near, what="float-float complex MAC (FP32 issue)"),
     }
+    if tensor_cores and p == 64:
+        peak, src = tf32_peak()
+        models["far_coupling"] = dict(
+            bound="tensor", peak=peak, peak_source=src, flops=8.0 * cmac_far,
+            what="complex MAC on tcgen05 TF32 (useful flops; the 3-product split executes 3x)")
+    return models
 
 
 def roofline_of(prof, models):
@@ -162,12 +181,14 @@ def roofline_of(prof, models):
     if not timed:
         return None
     name, (n, ms) = max(timed, key=lambda kv: kv[1][1])
-    flops, peak, what = models[name]
-    achieved = flops / (ms / n / 1e3) / 1e12
-    return {"bound": "alu", "kernel": name, "what": what, "achieved": achieved, "peak": peak,
-            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-            "launches": n, "ms_per_launch": ms / n,
-            "peak_source": "unit counts x max SM clock (152 SMs x 128 FP32 lanes x 2 x 2.07 GHz)"}
+    return roofline_entry(name, n, ms, models[name])
+
+
+def roofline_entry(name, n, ms, mdl):
+    achieved = mdl["flops"] / (ms / n / 1e3) / 1e12
+    return {"bound": mdl["bound"], "kernel": name, "what": mdl["what"], "achieved": achieved,
+            "peak": mdl["peak"], "unit": "TFLOP/s", "frac": achieved / mdl["peak"], "traffic": None,
+            "launches": n, "ms_per_launch": ms / n, "peak_source": mdl["peak_source"]}
 
 
 def run_ours(args):
@@ -183,6 +204,8 @@ def run_ours(args):
     M = m.nt
     params = dict(mode="h2maca", eta=W["eta"], cheb_m=W["cheb_m"], n_min=W["n_min"],
                   aca_eps=W["aca_eps"], profile=1)
+    if args.tensor_cores is not None:
+        params["tensor_cores"] = args.tensor_cores
     stream = torch.cuda.current_stream()
     rhs = torch.empty((L, M), dtype=torch.float64, device="cuda")
     q = torch.empty((L, M), dtype=torch.float64, device="cuda")
@@ -214,7 +237,7 @@ def run_ours(args):
                 a = prof.setdefault(k, [0, 0.0])
                 a[0] += n
                 a[1] += ms
-            infos.append(op.info())
+            infos.append(dict(op.info(), tensor_cores=int(op.params.tensor_cores)))
             sinfos.append(op.last_solve_info)
             op.close()
     torch.cuda.synchronize()
@@ -246,7 +269,7 @@ def run_ours(args):
     inf = infos[-1]
     dom = max(prof.items(), key=lambda kv: kv[1][1])
     p = W["cheb_m"] ** 3
-    models = kernel_models(inf, Ls, p)
+    models = kernel_models(inf, Ls, p, inf["tensor_cores"])
     lat = sorted(times)
     clocks = clk.summary()
     line = {
@@ -256,6 +279,7 @@ def run_ours(args):
         "config": {"workload": W["name"], "triangles": M, "N": N, "L": L, "Ls": Ls, "dt": dt,
                    "bdf": 2, "eta": W["eta"], "cheb_m": W["cheb_m"], "leaf": W["n_min"],
                    "aca_eps": W["aca_eps"], "mode": "h2maca", "parallelism": f"replicas{world}",
+                   "far_coupling": "tcgen05 tf32 x3" if inf["tensor_cores"] else "fp32 simt",
                    "l2": "256 MB buffer written between timed steps; working set "
                          f"{inf['device_bytes'] / 2**30:.1f} GiB > L2"},
         "latency_ms": {"p50": 1e3 * lat[len(lat) // 2],
@@ -407,6 +431,8 @@ def main():
     ap.add_argument("--level", type=int, default=None,
                     help="icosphere level override (smaller cases for profiler captures)")
     ap.add_argument("--N", type=int, default=None, help="time-step count override")
+    ap.add_argument("--tensor-cores", type=int, choices=[0, 1], default=None,
+                    help="far-field coupling on the TF32 tensor cores (1) or FP32 SIMT (0)")
     args = ap.parse_args()
     if args.level is not None:
         WORKLOAD["level"] = args.level

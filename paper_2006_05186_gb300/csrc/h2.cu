@@ -249,6 +249,8 @@ __device__ void expand_transfer(const R* __restrict__ Etr, int s, int m, int p, 
 }
 
 // Up-sweep for one level: xhat_r = sum_{s in sons(r)} E_{s,r}^T xhat_s.
+// Both transfer matrices are expanded once per block; each son's tile of
+// p x LC coefficients is staged in shared memory by one coalesced load.
 template <class R>
 __global__ void __launch_bounds__(256) k_upsweep(int node0, int Ls, int m, int p,
                                                  const int* __restrict__ son0,
@@ -256,30 +258,37 @@ __global__ void __launch_bounds__(256) k_upsweep(int node0, int Ls, int m, int p
                                                  const R* __restrict__ Etr,
                                                  typename Cplx<R>::type* __restrict__ xhat) {
   using C = typename Cplx<R>::type;
-  __shared__ R E[MAXP * MAXP];
+  extern __shared__ __align__(16) unsigned char smraw[];
+  R* E = (R*)smraw;                        // 2 x p x p
+  C* Xs = (C*)(E + 2 * MAXP * MAXP);       // p x LC
   const int r = node0 + blockIdx.x;
   if (son0[r] < 0) return;
+  const int sons[2] = {son0[r], son1[r]};
+  expand_transfer<R>(Etr, sons[0], m, p, E);
+  expand_transfer<R>(Etr, sons[1], m, p, E + MAXP * MAXP);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int l0 = 0; l0 < Ls; l0 += LC) {
     C acc[MAXP / 8];
 #pragma unroll
     for (int k = 0; k < MAXP / 8; ++k) acc[k] = cz<C>();
     for (int si = 0; si < 2; ++si) {
-      const int s = si == 0 ? son0[r] : son1[r];
+      const C* xs = xhat + (size_t)sons[si] * p * Ls + l0;
       __syncthreads();
-      expand_transfer<R>(Etr, s, m, p, E);
+      for (int t = threadIdx.x; t < p * LC; t += blockDim.x) {
+        const int lam = t / LC, l = t - lam * LC;
+        Xs[t] = (l0 + l < Ls) ? xs[(size_t)lam * Ls + l] : cz<C>();
+      }
       __syncthreads();
-      if (l0 + lane < Ls) {
-        for (int lam = 0; lam < p; ++lam) {
-          const C xv = xhat[((size_t)s * p + lam) * Ls + l0 + lane];
+      const R* Es = E + si * MAXP * MAXP;
+      for (int lam = 0; lam < p; ++lam) {
+        const C xv = Xs[lam * LC + lane];
 #pragma unroll
-          for (int k = 0; k < (int)(sizeof(acc) / sizeof(acc[0])); ++k) {
-            const int mu = w + 8 * k;
-            if (mu < p) {
-              const R e = E[lam * p + mu];
-              acc[k].x += e * xv.x;
-              acc[k].y += e * xv.y;
-            }
+        for (int k = 0; k < (int)(sizeof(acc) / sizeof(acc[0])); ++k) {
+          const int mu = w + 8 * k;
+          if (mu < p) {
+            const R e = Es[lam * p + mu];
+            acc[k].x += e * xv.x;
+            acc[k].y += e * xv.y;
           }
         }
       }
@@ -355,27 +364,36 @@ __global__ void __launch_bounds__(256) k_far_coupling(int Ls, int p, int cap,
   }
 }
 
-// Down-sweep for one level: yhat_s += E_{s,r} yhat_r for every node s of the level.
+// Down-sweep for one level: yhat_s += E_{s,r} yhat_r for every node s of the
+// level; the parent's tile of p x LC coefficients is staged in shared memory.
 template <class R>
 __global__ void __launch_bounds__(256) k_downsweep(int node0, int Ls, int m, int p,
                                                    const int* __restrict__ parent,
                                                    const R* __restrict__ Etr,
                                                    typename Cplx<R>::type* __restrict__ yhat) {
   using C = typename Cplx<R>::type;
-  __shared__ R E[MAXP * MAXP];
+  extern __shared__ __align__(16) unsigned char smraw[];
+  R* E = (R*)smraw;                  // p x p
+  C* Ys = (C*)(E + MAXP * MAXP);     // p x LC
   const int s = node0 + blockIdx.x;
   const int r = parent[s];
   if (r < 0) return;
   expand_transfer<R>(Etr, s, m, p, E);
-  __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const C* yr = yhat + (size_t)r * p * Ls;
   for (int l0 = 0; l0 < Ls; l0 += LC) {
+    __syncthreads();
+    for (int t = threadIdx.x; t < p * LC; t += blockDim.x) {
+      const int mu = t / LC, l = t - mu * LC;
+      Ys[t] = (l0 + l < Ls) ? yr[(size_t)mu * Ls + l0 + l] : cz<C>();
+    }
+    __syncthreads();
     if (l0 + lane >= Ls) continue;
     for (int lam = w; lam < p; lam += 8) {
       C z = cz<C>();
       for (int mu = 0; mu < p; ++mu) {
         const R e = E[lam * p + mu];
-        const C yv = yhat[((size_t)r * p + mu) * Ls + l0 + lane];
+        const C yv = Ys[mu * LC + lane];
         z.x += e * yv.x;
         z.y += e * yv.y;
       }
@@ -385,7 +403,8 @@ __global__ void __launch_bounds__(256) k_downsweep(int node0, int Ls, int m, int
   }
 }
 
-// y[l][perm[rb + i]] += sum_mu U[rb + i][mu] yhat_r[mu][l] for leaf r.
+// y[l][perm[rb + i]] += sum_mu U[rb + i][mu] yhat_r[mu][l] for leaf r; the
+// leaf's tile of p x LC coefficients is staged in shared memory.
 template <class R>
 __global__ void __launch_bounds__(256) k_leaf_backward(int M, int Ls, int p,
                                                        const int* __restrict__ leaves,
@@ -396,19 +415,27 @@ __global__ void __launch_bounds__(256) k_leaf_backward(int M, int Ls, int p,
                                                        const typename Cplx<R>::type* __restrict__ yhat,
                                                        double2* __restrict__ Y) {
   using C = typename Cplx<R>::type;
-  __shared__ R Us[32 * MAXP];
+  extern __shared__ __align__(16) unsigned char smraw[];
+  R* Us = (R*)smraw;                 // 32 x p
+  C* Ys = (C*)(Us + 32 * MAXP);      // p x LC
   const int r = leaves[blockIdx.x];
   const int rb = begin[r], nr = end[r] - rb;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int t = threadIdx.x; t < nr * p; t += blockDim.x) Us[t] = U[(size_t)rb * p + t];
-  __syncthreads();
+  const C* yr = yhat + (size_t)r * p * Ls;
   for (int l0 = 0; l0 < Ls; l0 += LC) {
+    __syncthreads();
+    for (int t = threadIdx.x; t < p * LC; t += blockDim.x) {
+      const int mu = t / LC, l = t - mu * LC;
+      Ys[t] = (l0 + l < Ls) ? yr[(size_t)mu * Ls + l0 + l] : cz<C>();
+    }
+    __syncthreads();
     if (l0 + lane >= Ls) continue;
     for (int i = w; i < nr; i += 8) {
       C z = cz<C>();
       for (int mu = 0; mu < p; ++mu) {
         const R u = Us[i * p + mu];
-        const C yv = yhat[((size_t)r * p + mu) * Ls + l0 + lane];
+        const C yv = Ys[mu * LC + lane];
         z.x += u * yv.x;
         z.y += u * yv.y;
       }
@@ -416,6 +443,19 @@ __global__ void __launch_bounds__(256) k_leaf_backward(int M, int Ls, int p,
       *o = cadd(*o, to_d(z));
     }
   }
+}
+
+template <class R>
+static size_t upsweep_smem() {
+  return sizeof(R) * 2 * MAXP * MAXP + sizeof(typename Cplx<R>::type) * MAXP * LC;
+}
+template <class R>
+static size_t downsweep_smem() {
+  return sizeof(R) * MAXP * MAXP + sizeof(typename Cplx<R>::type) * MAXP * LC;
+}
+template <class R>
+static size_t leaf_backward_smem() {
+  return sizeof(R) * 32 * MAXP + sizeof(typename Cplx<R>::type) * MAXP * LC;
 }
 
 template <class R>
@@ -443,6 +483,15 @@ int make_apply_plan(cqm_handle* h) {
                                     (int)coupling_smem<double>(h->p)));
   CQM_CUDA_TRY(cudaFuncSetAttribute(k_far_coupling<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)coupling_smem<float>(h->p)));
+#define SWEEP_ATTR(K, F)                                                                          \
+  CQM_CUDA_TRY(cudaFuncSetAttribute(K<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,      \
+                                    (int)F<double>()));                                          \
+  CQM_CUDA_TRY(cudaFuncSetAttribute(K<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,       \
+                                    (int)F<float>()));
+  SWEEP_ATTR(k_upsweep, upsweep_smem)
+  SWEEP_ATTR(k_downsweep, downsweep_smem)
+  SWEEP_ATTR(k_leaf_backward, leaf_backward_smem)
+#undef SWEEP_ATTR
   CQM_TRY(setup_f32_kernels(h));
   return setup_ff(h);
 }
@@ -482,7 +531,7 @@ static int apply_t(cqm_handle* h, const OpView<R>& V, const double2* x, double2*
       const int n0 = h->level_begin[lv], n1 = h->level_begin[lv + 1];
       if (n1 > n0) {
         ProfScope ps_(h, CQM_K_UPSWEEP);
-        k_upsweep<R><<<n1 - n0, 256, 0, S>>>(n0, Ls, m, p, h->node_son0.p, h->node_son1.p, V.Etr, V.xhat);
+        k_upsweep<R><<<n1 - n0, 256, upsweep_smem<R>(), S>>>(n0, Ls, m, p, h->node_son0.p, h->node_son1.p, V.Etr, V.xhat);
       }
     }
     cudaMemsetAsync(V.yhat, 0, sizeof(C) * (size_t)h->n_nodes * p * Ls, S);
@@ -500,12 +549,12 @@ static int apply_t(cqm_handle* h, const OpView<R>& V, const double2* x, double2*
       const int n0 = h->level_begin[lv], n1 = h->level_begin[lv + 1];
       if (n1 > n0) {
         ProfScope ps_(h, CQM_K_DOWNSWEEP);
-        k_downsweep<R><<<n1 - n0, 256, 0, S>>>(n0, Ls, m, p, h->node_parent.p, V.Etr, V.yhat);
+        k_downsweep<R><<<n1 - n0, 256, downsweep_smem<R>(), S>>>(n0, Ls, m, p, h->node_parent.p, V.Etr, V.yhat);
       }
     }
     {
       ProfScope ps_(h, CQM_K_LEAF_BACKWARD);
-      k_leaf_backward<R><<<(unsigned)nleaf, 256, 0, S>>>(M, Ls, p, h->d_leaves.p, h->node_begin.p,
+      k_leaf_backward<R><<<(unsigned)nleaf, 256, leaf_backward_smem<R>(), S>>>(M, Ls, p, h->d_leaves.p, h->node_begin.p,
                                                          h->node_end.p, h->perm.p, V.U, V.yhat, y);
     }
   }
