@@ -110,7 +110,9 @@ typedef struct cqm_params {
                              slices and fibres (16 bytes per point)       [1]   */
   int32_t exact_ff;       /* H2MACA: the FP64-accurate apply (residuals) runs its
                              near-field and coupling contractions in float-float
-                             arithmetic (~48 bits) on the FP32 pipes; 0 = FP64 [1] */
+                             arithmetic (~48 bits) on the FP32 pipes, and the C
+                             factors are held as float-float pairs after setup;
+                             0 = FP64                                     [1]   */
   const cqm_allocator* allocator; /* NULL: stream-ordered CUDA pool        [NULL] */
 } cqm_params;
 
@@ -204,7 +206,9 @@ int cqm_bem_get_blocks(const cqm_handle* h, int32_t* near_rc, int32_t* far_rc,
 /* MACA factors of one block (eq. maca): kind 0 = near, 1 = far; b = index in
  * the sorted list.  C: rank x rows x cols complex (rows/cols in tree order:
  * triangles perm[begin..end) for near blocks, Chebyshev multi-indices for far
- * blocks); D: rank x Ls complex (D[t][l] = d_t[l]).  Either may be NULL. */
+ * blocks); D: rank x Ls complex (D[t][l] = d_t[l]).  Either may be NULL.
+ * With exact_ff the C entries are returned as hi + lo of their float-float
+ * pairs (about 48 significant bits of the FP64 values the MACA computed). */
 int cqm_bem_get_block_factors(const cqm_handle* h, int32_t kind, int32_t b,
                               int32_t* rank, int32_t* rows, int32_t* cols,
                               double* C, double* D);

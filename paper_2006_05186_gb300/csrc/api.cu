@@ -203,6 +203,7 @@ int cqm_bem_setup(const cqm_mesh* mesh, double dt, int32_t N, int32_t bdf_order,
         if ((st = build_f32_copy(h)) != CQM_OK) break;
         h->use_f32 = true;
       }
+      if (p.exact_ff && (st = factors_to_ff(h)) != CQM_OK) break;
     }
     cudaEventRecord(ev[4], h->stream);
     cudaError_t e = cudaStreamSynchronize(h->stream);
@@ -518,16 +519,26 @@ int cqm_bem_get_block_factors(const cqm_handle* h, int32_t kind, int32_t b, int3
   if (cols) *cols = nc;
   cudaStream_t S = h->stream;
   const size_t blk = (size_t)nr * nc;
+  std::vector<float> ffbuf;
   if (Cout && r > 0) {
     const double2* src = kind == 0 ? h->nearC.p + h->h_near_off[b]
                                    : h->farC.p + (size_t)b * h->rank_cap * blk;
-    CQM_CUDA_TRY(cudaMemcpyAsync(Cout, src, sizeof(double2) * blk * r, cudaMemcpyDeviceToHost, S));
+    if (h->factors_ff) {
+      ffbuf.resize(4 * blk * r);
+      CQM_CUDA_TRY(cudaMemcpyAsync(ffbuf.data(), src, sizeof(double2) * blk * r, cudaMemcpyDeviceToHost, S));
+    } else {
+      CQM_CUDA_TRY(cudaMemcpyAsync(Cout, src, sizeof(double2) * blk * r, cudaMemcpyDeviceToHost, S));
+    }
   }
   if (Dout && r > 0) {
     const double2* src = (kind == 0 ? h->nearD.p : h->farD.p) + (size_t)b * h->rank_cap * h->Ls;
     CQM_CUDA_TRY(cudaMemcpyAsync(Dout, src, sizeof(double2) * h->Ls * r, cudaMemcpyDeviceToHost, S));
   }
   CQM_CUDA_TRY(cudaStreamSynchronize(S));
+  for (size_t i = 0; i < ffbuf.size() / 4; ++i) {  // float-float pairs -> hi + lo
+    Cout[2 * i] = (double)ffbuf[4 * i] + (double)ffbuf[4 * i + 2];
+    Cout[2 * i + 1] = (double)ffbuf[4 * i + 1] + (double)ffbuf[4 * i + 3];
+  }
   return CQM_OK;
 }
 

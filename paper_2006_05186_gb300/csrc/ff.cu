@@ -66,7 +66,7 @@ constexpr int PMAX = 64;
 // Near field in float-float: one block per leaf row cluster.
 __global__ void __launch_bounds__(256) k_near_apply_ff(
     int M, int Ls, int cap, const int4* __restrict__ items, const int2* __restrict__ blocks,
-    const int* __restrict__ rank, const int64_t* __restrict__ off, const double2* __restrict__ Cn,
+    const int* __restrict__ rank, const int64_t* __restrict__ off, const ffc* __restrict__ Cn,
     const double2* __restrict__ Dn, const int* __restrict__ begin, const int* __restrict__ end,
     const int* __restrict__ perm, const double2* __restrict__ X, double2* __restrict__ part) {
   __shared__ ffc Xs[32][LCF];
@@ -91,8 +91,8 @@ __global__ void __launch_bounds__(256) k_near_apply_ff(
       const int rk = rank[bi];
       for (int tt = 0; tt < rk; ++tt) {
         __syncthreads();
-        const double2* Ct = Cn + off[bi] + (size_t)tt * nr * nc;
-        for (int t = threadIdx.x; t < nr * nc; t += blockDim.x) Cs[t] = ffc_from(Ct[t]);
+        const ffc* Ct = Cn + off[bi] + (size_t)tt * nr * nc;
+        for (int t = threadIdx.x; t < nr * nc; t += blockDim.x) Cs[t] = Ct[t];
         if (threadIdx.x < LCF)
           Ds[threadIdx.x] = (l0 + threadIdx.x < Ls)
                                 ? ffc_from(Dn[((size_t)bi * cap + tt) * Ls + l0 + threadIdx.x])
@@ -151,23 +151,40 @@ __global__ void k_far_reduce_d(int Ls, int p, const int* __restrict__ rows,
   }
 }
 
-// Far coupling in float-float: one block per row cluster owning far blocks;
-// yhat_r (FP64) += sum_b sum_t D_b[t] C_{b,t} xhat_c.
+// Far coupling in float-float, one block per work item (a row cluster and a
+// run of its far blocks): part = sum_b sum_t d_t (.) (C_{b,t} xhat_c).
+// Full passes of LCF frequency columns give each lane one column and each
+// warp every 8th row; the Ls mod LCF remaining columns are done in one tail
+// pass that gives each thread whole (row, column) outputs instead, so the
+// ragged end costs a fraction of a pass.  Every output is summed in the same
+// order either way.  The staged C has row stride p + 1, which keeps the tail's
+// per-lane rows in distinct banks.
 __global__ void __launch_bounds__(256) k_far_coupling_ff(int Ls, int p, int cap,
                                                          const int4* __restrict__ items,
                                                          const int2* __restrict__ blocks,
                                                          const int* __restrict__ rank,
-                                                         const double2* __restrict__ Cf,
+                                                         const ffc* __restrict__ Cf,
                                                          const double2* __restrict__ Df,
                                                          const double2* __restrict__ xhat,
                                                          double2* __restrict__ part) {
   extern __shared__ __align__(16) unsigned char smraw[];
   ffc* Xs = (ffc*)smraw;        // p x LCF
-  ffc* Cs = Xs + PMAX * LCF;    // p x p
+  ffc* Cs = Xs + PMAX * LCF;    // p x (p + 1)
   __shared__ ffc Ds[LCF];
+  const int cs = p + 1;
   const int4 itm = items[blockIdx.x];  // (row, first block, end block, -)
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  for (int l0 = 0; l0 < Ls; l0 += LCF) {
+  const int nfull = Ls / LCF, rem = Ls - nfull * LCF;
+  auto stage_c = [&](int bi, int tt, int l0, int ncol) {
+    const ffc* Ct = Cf + ((size_t)bi * cap + tt) * p * p;
+    for (int t = threadIdx.x; t < p * p; t += blockDim.x) {
+      const int mu = t / p;
+      Cs[t + mu] = Ct[t];
+    }
+    if (threadIdx.x < ncol) Ds[threadIdx.x] = ffc_from(Df[((size_t)bi * cap + tt) * Ls + l0 + threadIdx.x]);
+  };
+  for (int pass = 0; pass < nfull; ++pass) {
+    const int l0 = pass * LCF;
     ffc acc[PMAX / 8];
 #pragma unroll
     for (int k = 0; k < PMAX / 8; ++k) acc[k] = ffc_zero();
@@ -176,17 +193,12 @@ __global__ void __launch_bounds__(256) k_far_coupling_ff(int Ls, int p, int cap,
       __syncthreads();
       for (int t = threadIdx.x; t < p * LCF; t += blockDim.x) {
         const int nu = t / LCF, l = t - nu * LCF;
-        Xs[t] = (l0 + l < Ls) ? ffc_from(xhat[((size_t)c * p + nu) * Ls + l0 + l]) : ffc_zero();
+        Xs[t] = ffc_from(xhat[((size_t)c * p + nu) * Ls + l0 + l]);
       }
       const int rk = rank[bi];
       for (int tt = 0; tt < rk; ++tt) {
         __syncthreads();
-        const double2* Ct = Cf + ((size_t)bi * cap + tt) * p * p;
-        for (int t = threadIdx.x; t < p * p; t += blockDim.x) Cs[t] = ffc_from(Ct[t]);
-        if (threadIdx.x < LCF)
-          Ds[threadIdx.x] = (l0 + threadIdx.x < Ls)
-                                ? ffc_from(Df[((size_t)bi * cap + tt) * Ls + l0 + threadIdx.x])
-                                : ffc_zero();
+        stage_c(bi, tt, l0, LCF);
         __syncthreads();
         const ffc d = Ds[lane];
 #pragma unroll
@@ -194,7 +206,7 @@ __global__ void __launch_bounds__(256) k_far_coupling_ff(int Ls, int p, int cap,
           const int mu = w + 8 * k;
           if (mu < p) {
             ffc z = ffc_zero();
-            for (int nu = 0; nu < p; ++nu) ffc_mac(z, Cs[mu * p + nu], Xs[nu * LCF + lane]);
+            for (int nu = 0; nu < p; ++nu) ffc_mac(z, Cs[mu * cs + nu], Xs[nu * LCF + lane]);
             ffc_renorm(z);
             ffc_mac(acc[k], d, z);
             ffc_renorm(acc[k]);
@@ -202,16 +214,78 @@ __global__ void __launch_bounds__(256) k_far_coupling_ff(int Ls, int p, int cap,
         }
       }
     }
-    if (l0 + lane < Ls)
 #pragma unroll
-      for (int k = 0; k < (int)(sizeof(acc) / sizeof(acc[0])); ++k) {
-        const int mu = w + 8 * k;
-        if (mu < p) part[((size_t)blockIdx.x * p + mu) * Ls + l0 + lane] = ffc_to(acc[k]);
+    for (int k = 0; k < (int)(sizeof(acc) / sizeof(acc[0])); ++k) {
+      const int mu = w + 8 * k;
+      if (mu < p) part[((size_t)blockIdx.x * p + mu) * Ls + l0 + lane] = ffc_to(acc[k]);
+    }
+  }
+  if (rem > 0) {
+    // tail: output o = mu * rem + j (column l0 + j), outputs tid + 256 k
+    constexpr int KT = PMAX * LCF / 256;
+    const int l0 = nfull * LCF, nout = p * rem;
+    ffc acc[KT];
+#pragma unroll
+    for (int k = 0; k < KT; ++k) acc[k] = ffc_zero();
+    for (int bi = itm.y; bi < itm.z; ++bi) {
+      const int c = blocks[bi].y;
+      __syncthreads();
+      for (int t = threadIdx.x; t < p * rem; t += blockDim.x) {
+        const int nu = t / rem, l = t - nu * rem;
+        Xs[nu * LCF + l] = ffc_from(xhat[((size_t)c * p + nu) * Ls + l0 + l]);
       }
+      const int rk = rank[bi];
+      for (int tt = 0; tt < rk; ++tt) {
+        __syncthreads();
+        stage_c(bi, tt, l0, rem);
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < KT; ++k) {
+          const int o = threadIdx.x + 256 * k;
+          if (o < nout) {
+            const int mu = o / rem, j = o - mu * rem;
+            ffc z = ffc_zero();
+            for (int nu = 0; nu < p; ++nu) ffc_mac(z, Cs[mu * cs + nu], Xs[nu * LCF + j]);
+            ffc_renorm(z);
+            ffc_mac(acc[k], Ds[j], z);
+            ffc_renorm(acc[k]);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < KT; ++k) {
+      const int o = threadIdx.x + 256 * k;
+      if (o < nout) {
+        const int mu = o / rem, j = o - mu * rem;
+        part[((size_t)blockIdx.x * p + mu) * Ls + l0 + j] = ffc_to(acc[k]);
+      }
+    }
   }
 }
 
-static size_t coupling_smem_ff(int p) { return sizeof(ffc) * (PMAX * LCF + (size_t)p * p); }
+// In place: each complex FP64 factor entry becomes its float-float pair
+// (same 16 bytes), the form the contractions above stage.
+__global__ void k_factors_to_ff(int64_t n, double2* __restrict__ a) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    const double2 v = a[i];
+    ((ffc*)a)[i] = ffc_from(v);
+  }
+}
+
+int factors_to_ff(cqm_handle* h) {
+  ProfScope ps_(h, CQM_K_BASES);
+  if (h->nearC.n)
+    k_factors_to_ff<<<grid_for((int64_t)h->nearC.n, 256), 256, 0, h->stream>>>((int64_t)h->nearC.n, h->nearC.p);
+  if (h->farC.n)
+    k_factors_to_ff<<<grid_for((int64_t)h->farC.n, 256), 256, 0, h->stream>>>((int64_t)h->farC.n, h->farC.p);
+  CQM_CHECK_LAUNCH();
+  h->factors_ff = true;
+  return CQM_OK;
+}
+
+static size_t coupling_smem_ff(int p) { return sizeof(ffc) * (PMAX * LCF + (size_t)p * (p + 1)); }
 
 int setup_ff(cqm_handle* h) {
   CQM_CUDA_TRY(cudaFuncSetAttribute(k_far_coupling_ff, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -223,7 +297,7 @@ int near_apply_ff(cqm_handle* h, const double2* x, double2* y) {
   ProfScope ps_(h, CQM_K_NEAR_EXACT);
   k_near_apply_ff<<<(unsigned)h->n_near_items, 256, 0, h->stream>>>(
       h->M, h->Ls, h->rank_cap, h->near_items.p, h->near_rc.p, h->near_rank.p, h->near_off.p,
-      h->nearC.p, h->nearD.p, h->node_begin.p, h->node_end.p, h->perm.p, x, h->part_d.p);
+      (const ffc*)h->nearC.p, h->nearD.p, h->node_begin.p, h->node_end.p, h->perm.p, x, h->part_d.p);
   k_near_reduce_d<<<(unsigned)h->h_leaves.size(), 256, 0, h->stream>>>(
       h->M, h->Ls, h->d_leaves.p, h->near_item_ptr.p, h->node_begin.p, h->node_end.p, h->perm.p,
       h->part_d.p, y);
@@ -234,7 +308,7 @@ int near_apply_ff(cqm_handle* h, const double2* x, double2* y) {
 int far_coupling_ff(cqm_handle* h) {
   ProfScope ps_(h, CQM_K_FAR_EXACT);
   k_far_coupling_ff<<<(unsigned)h->n_far_items, 256, coupling_smem_ff(h->p), h->stream>>>(
-      h->Ls, h->p, h->rank_cap, h->far_items.p, h->far_rc.p, h->far_rank.p, h->farC.p, h->farD.p,
+      h->Ls, h->p, h->rank_cap, h->far_items.p, h->far_rc.p, h->far_rank.p, (const ffc*)h->farC.p, h->farD.p,
       h->xhat.p, h->part_d.p);
   k_far_reduce_d<<<(unsigned)h->h_far_rows.size(), 256, 0, h->stream>>>(
       h->Ls, h->p, h->d_far_rows.p, h->far_item_ptr.p, h->part_d.p, h->yhat.p);

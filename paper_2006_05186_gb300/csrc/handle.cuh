@@ -82,6 +82,7 @@ struct cqm_handle {
 
   // FP32 copy of the operator (inner iterations of mixed precision)
   bool use_f32 = false;
+  bool factors_ff = false;  // nearC / farC hold float-float pairs (hi re, hi im, lo re, lo im)
   cqm::DArray<float2> nearC_f, nearD_f, farC_f, farD_f, xhat_f, yhat_f;
   cqm::DArray<float> Uleaf_f, Etr_f;
 
@@ -145,6 +146,7 @@ int far_coupling_tc(cqm_handle* h);
 int setup_ff(cqm_handle* h);
 int near_apply_ff(cqm_handle* h, const double2* x, double2* y);
 int far_coupling_ff(cqm_handle* h);
+int factors_to_ff(cqm_handle* h);  // after every FP64 reader of the C factors at setup
 
 // maca.cu
 int build_maca(cqm_handle* h);
