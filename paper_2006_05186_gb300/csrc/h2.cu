@@ -596,7 +596,23 @@ __global__ void k_to_f32r(int64_t n, const double* __restrict__ a, float* __rest
   if (i < n) b[i] = (float)a[i];
 }
 
+// FP32 copy of 64 x 64 coupling factors, each stored transposed (nu-major):
+// dst[tile][nu][mu] = src[tile][mu][nu].  One block per tile.
+__global__ void __launch_bounds__(256) k_to_f32c_t64(const double2* __restrict__ src,
+                                                     float2* __restrict__ dst) {
+  __shared__ float2 T[64][65];
+  const size_t base = (size_t)blockIdx.x * 4096;
+  for (int e = threadIdx.x; e < 4096; e += blockDim.x) {
+    const double2 v = src[base + e];
+    T[e & 63][e >> 6] = make_float2((float)v.x, (float)v.y);
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < 4096; e += blockDim.x) dst[base + e] = T[e >> 6][e & 63];
+}
+
 // FP32 copy of the operator factors (the inner operator of mixed precision).
+// With the tensor-core coupling (m = 4) the far C factors are stored
+// transposed, so the coupling kernel reads each row of C coalesced.
 int build_f32_copy(cqm_handle* h) {
   auto cc = [&](DArray<double2>& a, DArray<float2>& b) -> int {
     CQM_TRY(b.allocate(h->alloc, std::max<size_t>(1, a.n)));
@@ -616,7 +632,16 @@ int build_f32_copy(cqm_handle* h) {
   };
   CQM_TRY(cc(h->nearC, h->nearC_f));
   CQM_TRY(cc(h->nearD, h->nearD_f));
-  CQM_TRY(cc(h->farC, h->farC_f));
+  h->farC_f_transposed = h->params.tensor_cores != 0 && h->p == 64;
+  if (h->farC_f_transposed) {
+    CQM_TRY(h->farC_f.allocate(h->alloc, std::max<size_t>(1, h->farC.n)));
+    if (h->farC.n >= 4096) {
+      ProfScope ps_(h, CQM_K_BASES);
+      k_to_f32c_t64<<<(unsigned)(h->farC.n / 4096), 256, 0, h->stream>>>(h->farC.p, h->farC_f.p);
+    }
+  } else {
+    CQM_TRY(cc(h->farC, h->farC_f));
+  }
   CQM_TRY(cc(h->farD, h->farD_f));
   CQM_TRY(cr(h->Uleaf, h->Uleaf_f));
   CQM_TRY(cr(h->Etr, h->Etr_f));

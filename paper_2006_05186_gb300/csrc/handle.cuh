@@ -82,7 +82,8 @@ struct cqm_handle {
 
   // FP32 copy of the operator (inner iterations of mixed precision)
   bool use_f32 = false;
-  bool factors_ff = false;  // nearC / farC hold float-float pairs (hi re, hi im, lo re, lo im)
+  bool factors_ff = false;
+  bool farC_f_transposed = false;  // farC_f tiles stored nu-major (tensor-core coupling)  // nearC / farC hold float-float pairs (hi re, hi im, lo re, lo im)
   cqm::DArray<float2> nearC_f, nearD_f, farC_f, farD_f, xhat_f, yhat_f;
   cqm::DArray<float> Uleaf_f, Etr_f;
 

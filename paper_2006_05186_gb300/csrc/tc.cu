@@ -11,14 +11,17 @@
 // keeps fp32-level accuracy (the inner operator is fp32; the FP64-accurate
 // residual is computed apart).
 //
-// One CTA per work item: 8 producer warps build each K-slab (16 Chebyshev
-// indices nu, real and imaginary parts: 32 real-form K) in the canonical
-// K-major layout, in a ring of 3 slabs guarded by mbarriers; one thread of
-// warp 0 issues 4 x 3 MMAs per slab and frees the slab with tcgen05.commit;
-// warps 1-4 finally copy the accumulator from TMEM into the item's partial
-// tile, which the per-row reduction adds in item order (as for the SIMT kernel).
-// Every wait is bounded in time; on expiry the kernel records an error in
-// *err, stops issuing work, lets issued MMAs drain, frees TMEM and returns.
+// One CTA per work item.  Each K-slab covers 16 Chebyshev indices nu (their
+// real and imaginary parts: 32 real-form K).  Warps 1-4 build the slab's A
+// (the real form of C) row by row straight into tensor memory, one TMEM lane
+// per row; warps 5-8 build B = x~ in shared memory in the canonical K-major
+// layout.  A ring of 4 slabs is guarded by mbarriers; one thread of warp 0
+// issues 4 x 3 MMAs per slab (A from TMEM, B from shared memory) and frees the
+// slab with tcgen05.commit; warps 1-4 finally copy the accumulator from TMEM
+// into the item's partial tile, which the per-row reduction adds in item order
+// (as for the SIMT kernel).  Every wait is bounded in time; on expiry the
+// kernel records an error in *err, stops issuing work, lets issued MMAs drain,
+// frees TMEM and returns.
 #include <algorithm>
 
 #include "handle.cuh"
@@ -28,19 +31,22 @@ namespace cqm {
 
 namespace {
 constexpr int TP = 64;          // Chebyshev points per cluster (m = 4)
-constexpr int NSTAGE = 3;       // slabs in the ring
-constexpr int NPROD = 256;      // producer threads (warps 1..8)
-constexpr int NTHREADS = 32 + NPROD;
-constexpr uint32_t A_PLANE = 128u * 128u;  // bytes: 128 rows x 32 tf32
+constexpr int NSTAGE = 4;       // slabs in the ring
+constexpr int NA = 128;         // A producer threads (warps 1..4): one TMEM lane (row) each
+constexpr int NBP = 128;        // B producer threads (warps 5..8)
+constexpr int NTHREADS = 32 + NA + NBP;
+constexpr uint32_t TCOLS = 512;       // TMEM columns: accumulator [0, 256), A ring [256, 512)
+constexpr uint32_t ACOL = 256;        // first column of the A ring; 64 per slab (hi 32, lo 32)
 constexpr int ERR_TIMEOUT = 1;
 
 template <int NT>
 struct TcCfg {
   static constexpr int NC = 16 * NT;                       // frequency columns per chunk (MMA N)
   static constexpr uint32_t B_PLANE = (uint32_t)NC * 128u;  // NC rows x 32 tf32
-  static constexpr uint32_t STAGE = 2 * A_PLANE + 2 * B_PLANE;
-  static constexpr uint32_t TCOLS = NC <= 32 ? 32 : NC <= 64 ? 64 : NC <= 128 ? 128 : 256;
-  static constexpr size_t SMEM = (size_t)NSTAGE * STAGE + 1024;
+  static constexpr uint32_t STAGE = 2 * B_PLANE;
+  // at least 116 KB: one CTA per SM, which owns all 512 TMEM columns
+  static constexpr size_t SMEM_RING = (size_t)NSTAGE * STAGE + 1024;
+  static constexpr size_t SMEM = SMEM_RING > 118784 ? SMEM_RING : 118784;
 };
 
 __device__ __forceinline__ void st_split4(unsigned char* hi, unsigned char* lo, uint32_t off, float a,
@@ -64,7 +70,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   using namespace umma;
   using K = TcCfg<NT>;
   constexpr int NC = K::NC;
-  constexpr int NB = (4 * NC + NPROD - 1) / NPROD;  // B items per producer thread and slab
+  constexpr int NB = (4 * NC + NBP - 1) / NBP;  // B items per producer thread and slab
   extern __shared__ unsigned char smraw[];
   __shared__ __align__(8) uint64_t full_bar[NSTAGE];
   __shared__ __align__(8) uint64_t empty_bar[NSTAGE];
@@ -79,7 +85,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
   if (tid == 0) {
     for (int s = 0; s < NSTAGE; ++s) {
-      mbar_init(&full_bar[s], NPROD);
+      mbar_init(&full_bar[s], NA + NBP);
       mbar_init(&empty_bar[s], 1);
     }
     mbar_init(&done_bar, 1);
@@ -88,7 +94,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     never_sh = 0;
     mbar_init_fence();
   }
-  if (warp == 0) tmem_alloc(&tmem_sh, K::TCOLS);
+  if (warp == 0) tmem_alloc(&tmem_sh, TCOLS);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -97,7 +103,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   int nwork = 0;  // rank terms of the item; none leaves the tile zero
   for (int bi = it.y; bi < it.z; ++bi) nwork += rank[bi];
 
-  uint32_t use = 0;  // slab uses so far: the same sequence in every role
+  // Slabs in the order (block b, nu slab j, rank term t) in every role.
+  uint32_t use = 0;
   int chunk = 0;
   for (int l0 = 0; l0 < Ls; l0 += NC, ++chunk) {
     if (warp == 0) {
@@ -109,14 +116,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const bool ok = mbar_wait(&full_bar[s], (use / NSTAGE) & 1u, &abort_sh, err, ERR_TIMEOUT);
         tc_fence_after();
         if (ok && lane == 0) {
-          const uint32_t a_hi = smem_u32(ring + (size_t)s * K::STAGE), a_lo = a_hi + A_PLANE;
-          const uint32_t b_hi = a_lo + A_PLANE, b_lo = b_hi + K::B_PLANE;
+          const uint32_t a_hi = tmem + ACOL + 64u * s, a_lo = a_hi + 32u;
+          const uint32_t b_hi = smem_u32(ring + (size_t)s * K::STAGE), b_lo = b_hi + K::B_PLANE;
 #pragma unroll
           for (int ks = 0; ks < 4; ++ks) {
-            const uint32_t o = 256u * ks;
-            mma_tf32(tmem, sdesc(a_lo + o), sdesc(b_hi + o), idesc, acc);
-            mma_tf32(tmem, sdesc(a_hi + o), sdesc(b_lo + o), idesc, 1u);
-            mma_tf32(tmem, sdesc(a_hi + o), sdesc(b_hi + o), idesc, 1u);
+            mma_tf32_ts(tmem, a_lo + 8u * ks, sdesc(b_hi + 256u * ks), idesc, acc);
+            mma_tf32_ts(tmem, a_hi + 8u * ks, sdesc(b_lo + 256u * ks), idesc, 1u);
+            mma_tf32_ts(tmem, a_hi + 8u * ks, sdesc(b_hi + 256u * ks), idesc, 1u);
             acc = 1u;
           }
           mma_commit(&empty_bar[s]);
@@ -125,22 +131,84 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       }
       if (lane == 0 && nwork > 0) mma_commit(&done_bar);
       __syncwarp();
+    } else if (warp <= 4) {
+      // -------------------------------------------------------- A producers
+      // Row m = 32 (warp % 4) + lane of the real form: m < 64 gives Re y_mu,
+      // [Re C | -Im C]; m >= 64 gives Im y_mu, [Im C | Re C] (mu = m mod 64).
+      const int q = warp & 3, m = 32 * q + lane, mu = m & 63;
+      const bool im = m >= 64;
+      const uint32_t trow = tmem + ((uint32_t)(32 * q) << 16) + ACOL;
+      // C_{b,t} is stored transposed (nu-major): a warp reads 32 consecutive mu
+      // of one nu per load
+      auto load_c = [&](int bi, int j, int tt, float4 (&c)[8]) {
+        const float2* cs = Cf + ((size_t)bi * cap + tt) * TP * TP + (16 * j) * TP + mu;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const float2 a = cs[(2 * i) * TP], b = cs[(2 * i + 1) * TP];
+          c[i] = make_float4(a.x, a.y, b.x, b.y);
+        }
+      };
+      int bi = it.y, j = 0, tt = 0;
+      while (bi < it.z && rank[bi] == 0) ++bi;
+      float4 c[8];
+      if (bi < it.z) load_c(bi, 0, 0, c);
+      for (; bi < it.z; ++use) {
+        const int s = (int)(use % NSTAGE);
+        const uint32_t round = use / NSTAGE;
+        if (round > 0) mbar_wait(&empty_bar[s], (round - 1) & 1u, &abort_sh, err, ERR_TIMEOUT);
+        if (!__any_sync(0xffffffffu, abort_sh != 0)) {
+          tc_fence_after();
+          uint32_t hi[16], lo[16];
+          // K 0..15: Re C (Re rows) or Im C (Im rows) of nu = 16 j + k
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            float h, l;
+            split_tf32(im ? c[i].y : c[i].x, h, l);
+            hi[2 * i] = __float_as_uint(h);
+            lo[2 * i] = __float_as_uint(l);
+            split_tf32(im ? c[i].w : c[i].z, h, l);
+            hi[2 * i + 1] = __float_as_uint(h);
+            lo[2 * i + 1] = __float_as_uint(l);
+          }
+          tmem_st16(trow + 64u * s, hi);
+          tmem_st16(trow + 64u * s + 32u, lo);
+          // K 16..31: -Im C (Re rows) or Re C (Im rows)
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            float h, l;
+            split_tf32(im ? c[i].x : -c[i].y, h, l);
+            hi[2 * i] = __float_as_uint(h);
+            lo[2 * i] = __float_as_uint(l);
+            split_tf32(im ? c[i].z : -c[i].w, h, l);
+            hi[2 * i + 1] = __float_as_uint(h);
+            lo[2 * i + 1] = __float_as_uint(l);
+          }
+          tmem_st16(trow + 64u * s + 16u, hi);
+          tmem_st16(trow + 64u * s + 48u, lo);
+          tmem_wait_st();
+          tc_fence_before();
+        }
+        mbar_arrive(&full_bar[s]);
+        // next slab; its loads overlap the wait for the next ring slot
+        if (++tt == rank[bi]) {
+          tt = 0;
+          if (++j == 4) {
+            j = 0;
+            do ++bi; while (bi < it.z && rank[bi] == 0);
+          }
+        }
+        if (bi < it.z) load_c(bi, j, tt, c);
+      }
     } else {
-      // ---------------------------------------------------------- producers
-      // Slabs in the order (block b, nu slab j, rank term t): the 16 rows of
-      // xhat_c of slab j are loaded once per (b, j) and reused for every t;
-      // the C and d loads of the next slab are issued before the current
-      // slab is built, so their latency overlaps the wait and the build.
-      const int p = tid - 32;
-      const int amu = p & 63, aq = p >> 6;  // A: row mu, nu quad
-      auto load_cd = [&](int bi, int j, int tt, float4& c01, float4& c23, float2 (&dv)[NB]) {
-        const float4* cs = (const float4*)(Cf + ((size_t)bi * cap + tt) * TP * TP + amu * TP + 16 * j + 4 * aq);
-        c01 = cs[0];
-        c23 = cs[1];
+      // -------------------------------------------------------- B producers
+      // The 16 rows of xhat_c of slab j are loaded once per (b, j) and reused
+      // for every t.
+      const int pb = tid - 32 - NA;
+      auto load_d = [&](int bi, int tt, float2 (&dv)[NB]) {
         const float2* Dt = Df + ((size_t)bi * cap + tt) * Ls;
 #pragma unroll
         for (int i = 0; i < NB; ++i) {
-          const int e = p + NPROD * i;
+          const int e = pb + NBP * i;
           const int lg = l0 + e % NC;
           dv[i] = (e < 4 * NC && lg < Ls) ? Dt[lg] : make_float2(0.f, 0.f);
         }
@@ -149,82 +217,57 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const float2* xc = xhat + (size_t)blocks[bi].y * TP * Ls;
 #pragma unroll
         for (int i = 0; i < NB; ++i) {
-          const int e = p + NPROD * i;
-          const int q = e / NC, lg = l0 + e - q * NC;
+          const int e = pb + NBP * i;
+          const int qq = e / NC, lg = l0 + e - qq * NC;
           const bool in = e < 4 * NC && lg < Ls;
 #pragma unroll
           for (int v = 0; v < 4; ++v)
-            xv[i][v] = in ? xc[(size_t)(16 * j + 4 * q + v) * Ls + lg] : make_float2(0.f, 0.f);
+            xv[i][v] = in ? xc[(size_t)(16 * j + 4 * qq + v) * Ls + lg] : make_float2(0.f, 0.f);
         }
       };
       int bi = it.y, j = 0, tt = 0;
       while (bi < it.z && rank[bi] == 0) ++bi;
-      float4 c01 = make_float4(0.f, 0.f, 0.f, 0.f), c23 = c01;
       float2 dv[NB], xv[NB][4];
       if (bi < it.z) {
         load_x(bi, 0, xv);
-        load_cd(bi, 0, 0, c01, c23, dv);
+        load_d(bi, 0, dv);
       }
       for (; bi < it.z; ++use) {
-        int nb = bi, nj = j, nt = tt + 1;
-        if (nt == rank[bi]) {
-          nt = 0;
-          if (++nj == 4) {
-            nj = 0;
-            do ++nb; while (nb < it.z && rank[nb] == 0);
-          }
-        }
-        const bool has_next = nb < it.z, newx = has_next && nt == 0;
-        float4 c01n = c01, c23n = c23;
-        float2 dvn[NB], xvn[NB][4];
-        if (has_next) {
-          load_cd(nb, nj, nt, c01n, c23n, dvn);
-          if (newx) load_x(nb, nj, xvn);
-        }
         const int s = (int)(use % NSTAGE);
         const uint32_t round = use / NSTAGE;
         if (round > 0) mbar_wait(&empty_bar[s], (round - 1) & 1u, &abort_sh, err, ERR_TIMEOUT);
         if (!abort_sh) {
-          unsigned char* Ahi = ring + (size_t)s * K::STAGE;
-          unsigned char* Alo = Ahi + A_PLANE;
-          unsigned char* Bhi = Alo + A_PLANE;
+          unsigned char* Bhi = ring + (size_t)s * K::STAGE;
           unsigned char* Blo = Bhi + K::B_PLANE;
-          // A slab: K groups q (Re x~ of nu) and 4 + q (Im x~ of nu), rows mu and 64 + mu
-          st_split4(Ahi, Alo, core_off(amu, 4 * aq), c01.x, c01.z, c23.x, c23.z);
-          st_split4(Ahi, Alo, core_off(amu, 16 + 4 * aq), -c01.y, -c01.w, -c23.y, -c23.w);
-          st_split4(Ahi, Alo, core_off(64 + amu, 4 * aq), c01.y, c01.w, c23.y, c23.w);
-          st_split4(Ahi, Alo, core_off(64 + amu, 16 + 4 * aq), c01.x, c01.z, c23.x, c23.z);
-          // B slab: row l, Re x~ at K group q, Im x~ at K group 4 + q
+          // row l, Re x~ at K group qq, Im x~ at K group 4 + qq
 #pragma unroll
           for (int i = 0; i < NB; ++i) {
-            const int e = p + NPROD * i;
+            const int e = pb + NBP * i;
             if (e < 4 * NC) {
-              const int q = e / NC, l = e - q * NC;
+              const int qq = e / NC, l = e - qq * NC;
               float re[4], imv[4];
 #pragma unroll
               for (int v = 0; v < 4; ++v) {
                 re[v] = fmaf(dv[i].x, xv[i][v].x, -dv[i].y * xv[i][v].y);
                 imv[v] = fmaf(dv[i].x, xv[i][v].y, dv[i].y * xv[i][v].x);
               }
-              st_split4(Bhi, Blo, core_off(l, 4 * q), re[0], re[1], re[2], re[3]);
-              st_split4(Bhi, Blo, core_off(l, 16 + 4 * q), imv[0], imv[1], imv[2], imv[3]);
+              st_split4(Bhi, Blo, core_off(l, 4 * qq), re[0], re[1], re[2], re[3]);
+              st_split4(Bhi, Blo, core_off(l, 16 + 4 * qq), imv[0], imv[1], imv[2], imv[3]);
             }
           }
           fence_async_shared();
         }
         mbar_arrive(&full_bar[s]);
-        bi = nb;
-        j = nj;
-        tt = nt;
-        c01 = c01n;
-        c23 = c23n;
-#pragma unroll
-        for (int i = 0; i < NB; ++i) {
-          dv[i] = dvn[i];
-          if (newx)
-#pragma unroll
-            for (int v = 0; v < 4; ++v) xv[i][v] = xvn[i][v];
+        // next slab; its loads overlap the wait for the next ring slot
+        if (++tt == rank[bi]) {
+          tt = 0;
+          if (++j == 4) {
+            j = 0;
+            do ++bi; while (bi < it.z && rank[bi] == 0);
+          }
+          if (bi < it.z) load_x(bi, j, xv);
         }
+        if (bi < it.z) load_d(bi, tt, dv);
       }
     }
     // ------------------------------------------- epilogue: TMEM -> partial tile
@@ -263,7 +306,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     mbar_wait(&fin_bar, 0u, &never_sh, err, ERR_TIMEOUT);
     tc_fence_after();
     __syncwarp();
-    tmem_dealloc(tmem, K::TCOLS);
+    tmem_dealloc(tmem, TCOLS);
   }
 }
 
