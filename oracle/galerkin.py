@@ -14,7 +14,13 @@ specified for the CUDA path):
   ((P0 + P1) + P2) / 3, lengths as sqrt((x^2 + y^2) + z^2), so that the
   decision is reproducible bit for bit);
 * otherwise regular: Radon's 7-point rule on each triangle (49 points).
-Vertex order used by the singular rules (pair i = test, j = trial):
+Every pair is evaluated in canonical order, the lower triangle index first:
+V[i, j] for i > j is the rule applied to (j, i).  The kernel is symmetric and
+test and trial spaces coincide, so the Galerkin matrix is symmetric (Sec. 3.2);
+the common-edge rule is not symmetric under exchanging the two triangles (its
+two orders differ by the quadrature error, ~4e-7 relative at g_sing = 5), and
+the canonical order makes the discrete matrix exactly symmetric.
+Vertex order used by the singular rules (pair i = test, j = trial, i <= j):
 * identical: the stored order (v0, v1, v2) on both sides;
 * common edge: (u, w, third) on both sides, where (u, w) are the shared
   vertices in the order they appear in triangle i;
@@ -113,6 +119,7 @@ def pair_entries(xyz, tri, I, J, s, qp: QuadParams = QuadParams(), chunk: int = 
     tri = np.asarray(tri)
     I = np.asarray(I, dtype=np.int64)
     J = np.asarray(J, dtype=np.int64)
+    I, J = np.minimum(I, J), np.maximum(I, J)  # canonical order (module docstring)
     s = np.atleast_1d(np.asarray(s, dtype=np.complex128))
     P, area, cen, diam = element_geometry(xyz, tri)
     case = classify(tri, I, J, cen, diam, qp)

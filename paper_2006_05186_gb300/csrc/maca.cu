@@ -11,7 +11,12 @@
 // blocks from the kernel at the Chebyshev points (Alg. 3 FAR).
 // All blocks advance one rank step per round of four launches:
 //   slice -> residual update + pivot + Gram(C) -> fibre -> finalize.
+// The Galerkin matrix and the far-field kernel are symmetric and the
+// partition is symmetric (one cluster tree for rows and columns), so only the
+// blocks r <= c run the MACA; block (c, r) then takes the factors of (r, c)
+// with every C_t transposed.
 #include <algorithm>
+#include <unordered_map>
 #include <vector>
 
 #include "handle.cuh"
@@ -341,15 +346,38 @@ __global__ void __launch_bounds__(256) k_maca_finalize(MacaBlocks B) {
   }
 }
 
-__global__ void k_maca_init(int n, int words, int* rank, int* active, int* kcur, double* norm2,
-                            unsigned* used) {
+__global__ void k_maca_init(int n, int words, const int2* __restrict__ rc, int* rank, int* active,
+                            int* kcur, double* norm2, unsigned* used) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= n) return;
   rank[b] = 0;
-  active[b] = 1;
+  active[b] = rc[b].x <= rc[b].y ? 1 : 0;  // the lower blocks mirror the upper ones
   kcur[b] = 0;
   norm2[b] = 0.0;
   for (int w = 0; w < words; ++w) used[(size_t)b * words + w] = 0u;
+}
+
+// Block (c, r) of a lower-triangle block b takes the factors of its mirror
+// (r, c): the same rank and d_t, every C_t transposed.
+__global__ void __launch_bounds__(256) k_maca_mirror(MacaBlocks B, const int* __restrict__ mirror) {
+  const int b = blockIdx.x;
+  const int2 rc = B.rc[b];
+  if (rc.x <= rc.y) return;
+  const int m = mirror[b];
+  const int rk = B.rank[m];
+  const int nr = rows_of(B, b), nc = cols_of(B, b);  // the mirror is nc x nr
+  if (threadIdx.x == 0) B.rank[b] = rk;
+  for (int t = 0; t < rk; ++t) {
+    const double2* src = slot(B, m, t, nc, nr);
+    double2* dst = slot(B, b, t, nr, nc);
+    for (int e = threadIdx.x; e < nr * nc; e += blockDim.x) {
+      const int i = e / nc, j = e - i * nc;
+      dst[e] = src[(size_t)j * nr + i];
+    }
+    const double2* ds = B.D + ((size_t)m * B.cap + t) * B.Ls;
+    double2* dd = B.D + ((size_t)b * B.cap + t) * B.Ls;
+    for (int l = threadIdx.x; l < B.Ls; l += blockDim.x) dd[l] = ds[l];
+  }
 }
 
 // Point counts of every pair of near block b (CTA per block) and their
@@ -364,10 +392,11 @@ __global__ void __launch_bounds__(1024) k_pair_counts(const int2* __restrict__ r
   const int rb = begin[c2.x], nr = end[c2.x] - rb, cb = begin[c2.y], nc = end[c2.y] - cb;
   const int64_t base = off[b] / cap;
   const int n = nr * nc;  // <= 1024 (leaves of at most 32)
+  const bool upper = c2.x <= c2.y;  // lower blocks are mirrored, not evaluated
   int v = 0;
   if ((int)threadIdx.x < n) {
     const int i = threadIdx.x / nc, j = threadIdx.x - i * nc;
-    v = pair_npoints(q, pair_case(g, q, perm[rb + i], perm[cb + j]));
+    v = upper ? pair_npoints(q, pair_case(g, q, perm[rb + i], perm[cb + j])) : 0;
     cnt[base + threadIdx.x] = v;
   }
   // block exclusive scan (int64)
@@ -442,6 +471,7 @@ __global__ void __launch_bounds__(256) k_pair_geometry(const int2* __restrict__ 
                                                       int64_t* pt_off, double* pt_r, double* pt_c) {
   const int b = blockIdx.x;
   const int2 c2 = rc[b];
+  if (c2.x > c2.y) return;  // mirrored block: no points
   const int rb = begin[c2.x], nr = end[c2.x] - rb, cb = begin[c2.y], nc = end[c2.y] - cb;
   const int64_t base = off[b] / cap;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -513,14 +543,14 @@ static Geom geom_from(const cqm_handle* h) {
 // Runs MACA on one list of blocks; fills rank (device and host).
 static int run_maca(cqm_handle* h, int kind, int n, const int2* rc, DArray<double2>& C,
                     DArray<double2>& D, DArray<int>& rank, const int64_t* d_off, size_t c_entries,
-                    std::vector<int>& h_rank) {
+                    const std::vector<int2>& h_rc, std::vector<int>& h_rank) {
   h_rank.assign(n, 0);
   if (n == 0) return CQM_OK;
   const int Ls = h->Ls, cap = h->rank_cap;
   CQM_TRY(C.allocate(h->alloc, c_entries));
   CQM_TRY(D.allocate(h->alloc, (size_t)n * cap * Ls));
   CQM_TRY(rank.allocate(h->alloc, n));
-  DArray<int> active, kcur, counters;
+  DArray<int> active, kcur, counters, mirror;
   DArray<int2> piv;
   DArray<double2> pval, gramc;
   DArray<double> cn2, norm2;
@@ -529,7 +559,7 @@ static int run_maca(cqm_handle* h, int kind, int n, const int2* rc, DArray<doubl
   auto release = [&]() {
     active.free(h->alloc); kcur.free(h->alloc); counters.free(h->alloc); piv.free(h->alloc);
     pval.free(h->alloc); gramc.free(h->alloc); cn2.free(h->alloc); norm2.free(h->alloc);
-    used.free(h->alloc);
+    used.free(h->alloc); mirror.free(h->alloc);
   };
   int st = CQM_OK;
 #define MT(e) do { if ((st = (e)) != CQM_OK) { release(); return st; } } while (0)
@@ -542,6 +572,30 @@ static int run_maca(cqm_handle* h, int kind, int n, const int2* rc, DArray<doubl
   MT(cn2.allocate(h->alloc, n));
   MT(norm2.allocate(h->alloc, n));
   MT(used.allocate(h->alloc, (size_t)n * words));
+  // mirror[b]: index of block (c, r) for b = (r, c)
+  std::vector<int> h_mirror(n, -1);
+  int n_upper = 0;
+  {
+    std::unordered_map<uint64_t, int> at;
+    at.reserve(2 * (size_t)n);
+    for (int b = 0; b < n; ++b) at[((uint64_t)(uint32_t)h_rc[b].x << 32) | (uint32_t)h_rc[b].y] = b;
+    for (int b = 0; b < n; ++b) {
+      const auto f = at.find(((uint64_t)(uint32_t)h_rc[b].y << 32) | (uint32_t)h_rc[b].x);
+      if (f == at.end()) {
+        release();
+        set_last_error("block partition is not symmetric");
+        return CQM_EINVAL;
+      }
+      h_mirror[b] = f->second;
+      if (h_rc[b].x <= h_rc[b].y) ++n_upper;
+    }
+  }
+  MT(mirror.allocate(h->alloc, n));
+  if (cudaMemcpyAsync(mirror.p, h_mirror.data(), sizeof(int) * n, cudaMemcpyHostToDevice, h->stream) !=
+      cudaSuccess) {
+    release();
+    return CQM_ECUDA;
+  }
   MacaBlocks B;
   B.n = n; B.kind = kind; B.Ls = Ls; B.cap = cap; B.p = h->p; B.m = h->m;
   B.rc = rc; B.begin = h->node_begin.p; B.end = h->node_end.p; B.perm = h->perm.p;
@@ -558,9 +612,9 @@ static int run_maca(cqm_handle* h, int kind, int n, const int2* rc, DArray<doubl
   const Geom g = geom_from(h);
   {
     ProfScope ps_(h, CQM_K_MACA_FINALIZE);
-    k_maca_init<<<grid_for(n, 256), 256, 0, S>>>(n, words, rank.p, active.p, kcur.p, norm2.p, used.p);
+    k_maca_init<<<grid_for(n, 256), 256, 0, S>>>(n, words, rc, rank.p, active.p, kcur.p, norm2.p, used.p);
   }
-  int hc[2] = {n, 0};
+  int hc[2] = {n_upper, 0};
   cudaMemcpyAsync(counters.p, hc, 2 * sizeof(int), cudaMemcpyHostToDevice, S);
   for (int step = 0; step < cap; ++step) {
     {
@@ -594,6 +648,10 @@ static int run_maca(cqm_handle* h, int kind, int n, const int2* rc, DArray<doubl
       if (hc[0] == 0) break;
     }
   }
+  {
+    ProfScope ps_(h, CQM_K_MACA_FINALIZE);
+    k_maca_mirror<<<n, 256, 0, S>>>(B, mirror.p);
+  }
   cudaMemcpyAsync(hc, counters.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, S);
   cudaMemcpyAsync(h_rank.data(), rank.p, sizeof(int) * n, cudaMemcpyDeviceToHost, S);
   cudaError_t e = cudaStreamSynchronize(S);
@@ -625,14 +683,14 @@ int build_maca(cqm_handle* h) {
                                cudaMemcpyHostToDevice, h->stream));
   CQM_TRY(build_point_cache(h, total / std::max(1, h->rank_cap)));
   CQM_TRY(run_maca(h, 0, h->n_near, h->near_rc.p, h->nearC, h->nearD, h->near_rank, h->near_off.p,
-                   (size_t)std::max<int64_t>(total, 1), h->h_near_rank));
+                   (size_t)std::max<int64_t>(total, 1), h->h_near, h->h_near_rank));
   // the point cache serves the near-field slices and fibres only
   h->pt_r.free(h->alloc);
   h->pt_c.free(h->alloc);
   h->pt_off.free(h->alloc);
   h->pt_cnt.free(h->alloc);
   CQM_TRY(run_maca(h, 1, h->n_far, h->far_rc.p, h->farC, h->farD, h->far_rank, nullptr,
-                   (size_t)h->n_far * h->rank_cap * h->p * h->p, h->h_far_rank));
+                   (size_t)h->n_far * h->rank_cap * h->p * h->p, h->h_far, h->h_far_rank));
   cqm_setup_info& I = h->info;
   I.near_entries = 0;
   I.near_rank_entries = 0;

@@ -167,9 +167,18 @@ __device__ __forceinline__ void singular_vertices(const int* tri, int i, int j, 
 // Visit this lane's share (points lane, lane+nlanes, ...) of the quadrature
 // points of pair (i, j): f(k, r, c) with k the point's index within the pair,
 // r = |x - y| and c = weight / (4 pi r) (weights include the area factors).
+// The pair is evaluated in canonical order, lower triangle index first: the
+// single-layer Galerkin matrix is symmetric (symmetric kernel, same test and
+// trial space), and the common-edge rule alone is not symmetric under
+// exchanging the triangles, so this keeps V_l[i][j] == V_l[j][i] bit for bit.
 template <class F>
 __device__ __forceinline__ void pair_points(const Geom& g, const Quad& q, int i, int j, int cse,
                                             int lane, int nlanes, F&& f) {
+  if (i > j) {
+    const int t = i;
+    i = j;
+    j = t;
+  }
   const double* Pi = g.P + 9 * i;
   const double* Pj = g.P + 9 * j;
   if (cse == CASE_REGULAR || cse == CASE_NEAR) {

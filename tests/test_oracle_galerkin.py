@@ -7,6 +7,7 @@ import numpy as np
 import pytest
 
 from oracle import galerkin as G
+from oracle import quadrature as Q
 from paper_2006_05186_gb300 import synth
 
 
@@ -68,12 +69,42 @@ def test_T5_laplace_limit():
 
 
 def test_matrix_symmetric_and_conjugate():
-    """V(s) is complex symmetric up to quadrature asymmetry; V(conj s) = conj V(s)."""
+    """V(s) is complex symmetric (symmetric kernel, same test and trial space;
+    every pair is evaluated in canonical order, so exactly); V(conj s) = conj V(s)."""
     m = synth.icosphere(1)
     s = 1.7 + 2.9j
     V = G.dense_matrices(m.xyz, m.tri, np.array([s, np.conj(s)]))
     assert np.max(np.abs(V[1] - np.conj(V[0]))) < 1e-15 * np.max(np.abs(V[0])) * 10
-    assert np.max(np.abs(V[0] - V[0].T)) < 1e-6 * np.max(np.abs(V[0]))
+    assert np.array_equal(V[0], V[0].T)
+
+
+def test_common_edge_rule_orders_agree_to_quadrature_accuracy():
+    """The common-edge Sauter-Schwab rule applied with the two triangles
+    exchanged gives the same entry up to the quadrature error: the canonical
+    order chooses between two valid approximations, it does not hide a wrong
+    rule.  Both orders also converge to each other as g grows."""
+    m = synth.icosphere(1)
+    tri = np.asarray(m.tri)
+    pairs = [(i, j) for i in range(len(tri)) for j in range(len(tri))
+             if i < j and len(set(tri[i]) & set(tri[j])) == 2][:12]
+    s = np.array([0.8, 2.0 + 3.0j])
+    P, _, _, _ = G.element_geometry(m.xyz, m.tri)
+
+    def edge_entry(i, j, g):
+        vx, vy = G._ordered_vertices(tri, i, j, 3)
+        xh, yh, wr = Q.sauter_schwab("edge", g)
+        X = Q.ref_to_bary(xh) @ np.asarray(m.xyz)[vx]
+        Y = Q.ref_to_bary(yh) @ np.asarray(m.xyz)[vy]
+        r = np.sqrt(np.sum((X - Y) ** 2, axis=1))
+        area_i = 0.5 * np.linalg.norm(np.cross(P[i, 1] - P[i, 0], P[i, 2] - P[i, 0]))
+        area_j = 0.5 * np.linalg.norm(np.cross(P[j, 1] - P[j, 0], P[j, 2] - P[j, 0]))
+        w = wr * (2 * area_i) * (2 * area_j)
+        return np.array([np.sum(w * np.exp(-sk * r) / (4 * np.pi * r)) for sk in s])
+
+    for i, j in pairs:
+        e5 = np.abs(edge_entry(i, j, 5) - edge_entry(j, i, 5)) / np.abs(edge_entry(i, j, 5))
+        e9 = np.abs(edge_entry(i, j, 9) - edge_entry(j, i, 9)) / np.abs(edge_entry(i, j, 9))
+        assert np.all(e5 < 1e-5) and np.all(e9 < e5 + 1e-13)
 
 
 def test_T6_disjoint_pairs_brute_force():
