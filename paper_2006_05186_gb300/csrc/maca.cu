@@ -103,14 +103,35 @@ __global__ void __launch_bounds__(256) k_maca_slice(MacaBlocks B, Geom g, Quad q
   const int rb = B.begin[rc.x], cb = B.begin[rc.y];
   double2 sv[1] = {sk};
   if (B.pt_r) {
+    // a diagonal block evaluates its pairs i <= j (the pair order is
+    // canonical, so V[i][j] and V[j][i] are the same sum) and writes both
     const int64_t base = B.off[b] / B.cap;
-    for (int e = w; e < nr * nc; e += nw) {
+    const bool diag = rc.x == rc.y;
+    const int npair = diag ? nr * (nr + 1) / 2 : nr * nc;
+    for (int e2 = w; e2 < npair; e2 += nw) {
+      int i, j;
+      if (diag) {  // e2 -> (i, j), i <= j, row-major over the upper triangle
+        i = 0;
+        int rem = e2;
+        while (rem >= nr - i) {
+          rem -= nr - i;
+          ++i;
+        }
+        j = i + rem;
+      } else {
+        i = e2 / nc;
+        j = e2 - i * nc;
+      }
+      const int e = i * nc + j;
       const int64_t o = B.pt_off[base + e];
       const int n = B.pt_cnt[base + e];
       double2 acc[1] = {make_double2(0.0, 0.0)};
       for (int k = lane; k < n; k += 32) kernel_accumulate_c<1>(B.pt_r[o + k], B.pt_c[o + k], sv, 1, acc, q);
       acc[0] = warp_sum2(acc[0]);
-      if (lane == 0) out[e] = acc[0];
+      if (lane == 0) {
+        out[e] = acc[0];
+        if (diag) out[j * nc + i] = acc[0];
+      }
     }
     return;
   }
@@ -226,7 +247,9 @@ __global__ void __launch_bounds__(256) k_maca_fibre(MacaBlocks B, Geom g, Quad q
   constexpr int NF = 8;
   if (B.pt_r) {
     const int nc = B.end[rc.y] - B.begin[rc.y];
-    const int64_t k = B.off[b] / B.cap + (int64_t)pv.x * nc + pv.y;
+    // a diagonal block caches its pairs i <= j only; (i, j) and (j, i) are one pair
+    const bool swap = rc.x == rc.y && pv.x > pv.y;
+    const int64_t k = B.off[b] / B.cap + (swap ? (int64_t)pv.y * nc + pv.x : (int64_t)pv.x * nc + pv.y);
     const int64_t o = B.pt_off[k];
     const int n = B.pt_cnt[k];
     for (int f0 = w * NF; f0 < B.Ls; f0 += nw * NF) {
@@ -396,7 +419,8 @@ __global__ void __launch_bounds__(1024) k_pair_counts(const int2* __restrict__ r
   int v = 0;
   if ((int)threadIdx.x < n) {
     const int i = threadIdx.x / nc, j = threadIdx.x - i * nc;
-    v = upper ? pair_npoints(q, pair_case(g, q, perm[rb + i], perm[cb + j])) : 0;
+    const bool keep = upper && (c2.x != c2.y || i <= j);  // diagonal blocks: pairs i <= j
+    v = keep ? pair_npoints(q, pair_case(g, q, perm[rb + i], perm[cb + j])) : 0;
     cnt[base + threadIdx.x] = v;
   }
   // block exclusive scan (int64)
@@ -477,6 +501,7 @@ __global__ void __launch_bounds__(256) k_pair_geometry(const int2* __restrict__ 
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int e = w; e < nr * nc; e += nw) {
     const int i = e / nc, j = e - i * nc;
+    if (c2.x == c2.y && i > j) continue;  // diagonal blocks cache their pairs i <= j
     const int I = perm[rb + i], J = perm[cb + j];
     const int64_t o = pt_off[base + e] + block_base[b];
     __syncwarp();
