@@ -6,22 +6,25 @@
 // (b, t) is one GEMM with M = 128, K = 128 and N = the frequency columns:
 //   [Re y; Im y] += [[Re C, -Im C], [Im C, Re C]] [Re x~; Im x~],  x~ = d_t (.) xhat_c,
 // and a work item (a row cluster and a run of its far blocks) sums all of its
-// (b, t) in one TMEM accumulator.  Every operand is split into two tf32 parts
-// and the three products lo*hi + hi*lo + hi*hi are accumulated in fp32, which
-// keeps fp32-level accuracy (the inner operator is fp32; the FP64-accurate
-// residual is computed apart).
+// (b, t) in one TMEM accumulator.  Every operand is split as hi (rounded to
+// tf32) + lo, and the three products lo*hi + hi*lo + hi*hi are accumulated in
+// fp32, which carries each operand to 2^-21 (the inner operator is fp32-class;
+// the FP64-accurate residual is computed apart).
 //
 // One CTA per work item.  Each K-slab covers 16 Chebyshev indices nu (their
-// real and imaginary parts: 32 real-form K).  Warps 1-4 build the slab's A
-// (the real form of C) row by row straight into tensor memory, one TMEM lane
-// per row; warps 5-8 build B = x~ in shared memory in the canonical K-major
-// layout.  A ring of 4 slabs is guarded by mbarriers; one thread of warp 0
-// issues 4 x 3 MMAs per slab (A from TMEM, B from shared memory) and frees the
-// slab with tcgen05.commit; warps 1-4 finally copy the accumulator from TMEM
-// into the item's partial tile, which the per-row reduction adds in item order
-// (as for the SIMT kernel).  Every wait is bounded in time; on expiry the
-// kernel records an error in *err, stops issuing work, lets issued MMAs drain,
-// frees TMEM and returns.
+// real and imaginary parts: 32 real-form K).  Warp 9 runs ahead and copies
+// each slab's 16 x 64 block of C (stored nu-major, 8 KB contiguous) into a
+// ring of 8 staging buffers with bulk asynchronous copies; warps 1-4 build the
+// slab's A (the real form of C) from there row by row straight into tensor
+// memory, one TMEM lane per row; warps 5-8 build B = x~ in shared memory in
+// the canonical K-major layout, with the d_t values loaded three slabs ahead.
+// A ring of 4 slabs is guarded by mbarriers; one thread of warp 0 issues
+// 4 x 3 MMAs per slab (A from TMEM, B from shared memory) and frees the slab
+// with tcgen05.commit; warps 1-4 finally copy the accumulator from TMEM into
+// the item's partial tile, which the per-row reduction adds in item order (as
+// for the SIMT kernel).  Every wait is bounded in time; on expiry the kernel
+// records an error in *err, stops issuing work, lets issued copies and MMAs
+// drain, frees TMEM and returns.
 #include <algorithm>
 
 #include "handle.cuh"
@@ -31,10 +34,13 @@ namespace cqm {
 
 namespace {
 constexpr int TP = 64;          // Chebyshev points per cluster (m = 4)
-constexpr int NSTAGE = 4;       // slabs in the ring
+constexpr int NSTAGE = 4;       // slabs in the MMA ring
+constexpr int NCS = 8;          // C staging buffers (8 KB each)
+constexpr uint32_t CSLAB = 16u * TP * 8u;  // bytes of one slab of C: 16 nu x 64 mu complex fp32
 constexpr int NA = 128;         // A producer threads (warps 1..4): one TMEM lane (row) each
 constexpr int NBP = 128;        // B producer threads (warps 5..8)
-constexpr int NTHREADS = 32 + NA + NBP;
+constexpr int LOADER = 9;       // warp that issues the C copies
+constexpr int NTHREADS = 32 * (LOADER + 1);
 constexpr uint32_t TCOLS = 512;       // TMEM columns: accumulator [0, 256), A ring [256, 512)
 constexpr uint32_t ACOL = 256;        // first column of the A ring; 64 per slab (hi 32, lo 32)
 constexpr int ERR_TIMEOUT = 1;
@@ -44,9 +50,29 @@ struct TcCfg {
   static constexpr int NC = 16 * NT;                       // frequency columns per chunk (MMA N)
   static constexpr uint32_t B_PLANE = (uint32_t)NC * 128u;  // NC rows x 32 tf32
   static constexpr uint32_t STAGE = 2 * B_PLANE;
+  static constexpr size_t SMEM_RING = (size_t)NSTAGE * STAGE + (size_t)NCS * CSLAB + 1024;
   // at least 116 KB: one CTA per SM, which owns all 512 TMEM columns
-  static constexpr size_t SMEM_RING = (size_t)NSTAGE * STAGE + 1024;
   static constexpr size_t SMEM = SMEM_RING > 118784 ? SMEM_RING : 118784;
+};
+
+// Position in the slab sequence (block b, nu slab j, rank term t), blocks of
+// rank 0 skipped; bi == end once the sequence is exhausted.
+struct SlabPos {
+  int bi, j, tt;
+  __device__ void start(int b0, int end, const int* rank) {
+    bi = b0;
+    j = tt = 0;
+    while (bi < end && rank[bi] == 0) ++bi;
+  }
+  __device__ void next(int end, const int* rank) {
+    if (++tt == rank[bi]) {
+      tt = 0;
+      if (++j == 4) {
+        j = 0;
+        do ++bi; while (bi < end && rank[bi] == 0);
+      }
+    }
+  }
 };
 
 __device__ __forceinline__ void st_split4(unsigned char* hi, unsigned char* lo, uint32_t off, float a,
@@ -74,19 +100,26 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   extern __shared__ unsigned char smraw[];
   __shared__ __align__(8) uint64_t full_bar[NSTAGE];
   __shared__ __align__(8) uint64_t empty_bar[NSTAGE];
+  __shared__ __align__(8) uint64_t cfull_bar[NCS];
+  __shared__ __align__(8) uint64_t cempty_bar[NCS];
   __shared__ __align__(8) uint64_t done_bar;
   __shared__ __align__(8) uint64_t fin_bar;
   __shared__ uint32_t tmem_sh;
   __shared__ volatile int abort_sh;
   __shared__ volatile int never_sh;
   unsigned char* ring = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
+  unsigned char* cstage = ring + (size_t)NSTAGE * K::STAGE;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int4 it = items[blockIdx.x];  // (row, first block, end block, -)
 
   if (tid == 0) {
     for (int s = 0; s < NSTAGE; ++s) {
-      mbar_init(&full_bar[s], NA + NBP);
+      mbar_init(&full_bar[s], (NA + NBP) / 32);  // one arrival per producer warp
       mbar_init(&empty_bar[s], 1);
+    }
+    for (int s = 0; s < NCS; ++s) {
+      mbar_init(&cfull_bar[s], 1);
+      mbar_init(&cempty_bar[s], NA / 32);
     }
     mbar_init(&done_bar, 1);
     mbar_init(&fin_bar, 1);
@@ -106,6 +139,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   // Slabs in the order (block b, nu slab j, rank term t) in every role.
   uint32_t use = 0;
   int chunk = 0;
+  uint32_t c_issued = 0;  // loader: C copies issued so far
   for (int l0 = 0; l0 < Ls; l0 += NC, ++chunk) {
     if (warp == 0) {
       // ---------------------------------------------------------------- MMA
@@ -131,6 +165,23 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       }
       if (lane == 0 && nwork > 0) mma_commit(&done_bar);
       __syncwarp();
+    } else if (warp == LOADER) {
+      // ------------------------------------------------------------- loader
+      if (lane == 0) {
+        SlabPos sp;
+        sp.start(it.y, it.z, rank);
+        for (; sp.bi < it.z; sp.next(it.z, rank), ++c_issued) {
+          const int sc = (int)(c_issued % NCS);
+          if (c_issued >= NCS &&
+              !mbar_wait(&cempty_bar[sc], (c_issued / NCS - 1) & 1u, &abort_sh, err, ERR_TIMEOUT))
+            break;
+          mbar_arrive_expect_tx(&cfull_bar[sc], CSLAB);
+          bulk_g2s(cstage + (size_t)sc * CSLAB,
+                   Cf + ((size_t)sp.bi * cap + sp.tt) * TP * TP + (size_t)(16 * sp.j) * TP, CSLAB,
+                   &cfull_bar[sc]);
+        }
+      }
+      __syncwarp();
     } else if (warp <= 4) {
       // -------------------------------------------------------- A producers
       // Row m = 32 (warp % 4) + lane of the real form: m < 64 gives Re y_mu,
@@ -138,21 +189,17 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const int q = warp & 3, m = 32 * q + lane, mu = m & 63;
       const bool im = m >= 64;
       const uint32_t trow = tmem + ((uint32_t)(32 * q) << 16) + ACOL;
-      // C_{b,t} is stored transposed (nu-major): a warp reads 32 consecutive mu
-      // of one nu per load
-      auto load_c = [&](int bi, int j, int tt, float4 (&c)[8]) {
-        const float2* cs = Cf + ((size_t)bi * cap + tt) * TP * TP + (16 * j) * TP + mu;
+      for (int k = 0; k < 4 * nwork; ++k, ++use) {
+        const int sc = (int)(use % NCS);
+        float2 c[16];
+        const bool cok = mbar_wait(&cfull_bar[sc], (use / NCS) & 1u, &abort_sh, err, ERR_TIMEOUT);
+        if (cok) {
+          const float2* cs = (const float2*)(cstage + (size_t)sc * CSLAB) + mu;
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const float2 a = cs[(2 * i) * TP], b = cs[(2 * i + 1) * TP];
-          c[i] = make_float4(a.x, a.y, b.x, b.y);
+          for (int v = 0; v < 16; ++v) c[v] = cs[v * TP];
         }
-      };
-      int bi = it.y, j = 0, tt = 0;
-      while (bi < it.z && rank[bi] == 0) ++bi;
-      float4 c[8];
-      if (bi < it.z) load_c(bi, 0, 0, c);
-      for (; bi < it.z; ++use) {
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&cempty_bar[sc]);
         const int s = (int)(use % NSTAGE);
         const uint32_t round = use / NSTAGE;
         if (round > 0) mbar_wait(&empty_bar[s], (round - 1) & 1u, &abort_sh, err, ERR_TIMEOUT);
@@ -161,51 +208,38 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           uint32_t hi[16], lo[16];
           // K 0..15: Re C (Re rows) or Im C (Im rows) of nu = 16 j + k
 #pragma unroll
-          for (int i = 0; i < 8; ++i) {
+          for (int v = 0; v < 16; ++v) {
             float h, l;
-            split_tf32(im ? c[i].y : c[i].x, h, l);
-            hi[2 * i] = __float_as_uint(h);
-            lo[2 * i] = __float_as_uint(l);
-            split_tf32(im ? c[i].w : c[i].z, h, l);
-            hi[2 * i + 1] = __float_as_uint(h);
-            lo[2 * i + 1] = __float_as_uint(l);
+            split_tf32(im ? c[v].y : c[v].x, h, l);
+            hi[v] = __float_as_uint(h);
+            lo[v] = __float_as_uint(l);
           }
           tmem_st16(trow + 64u * s, hi);
           tmem_st16(trow + 64u * s + 32u, lo);
           // K 16..31: -Im C (Re rows) or Re C (Im rows)
 #pragma unroll
-          for (int i = 0; i < 8; ++i) {
+          for (int v = 0; v < 16; ++v) {
             float h, l;
-            split_tf32(im ? c[i].x : -c[i].y, h, l);
-            hi[2 * i] = __float_as_uint(h);
-            lo[2 * i] = __float_as_uint(l);
-            split_tf32(im ? c[i].z : -c[i].w, h, l);
-            hi[2 * i + 1] = __float_as_uint(h);
-            lo[2 * i + 1] = __float_as_uint(l);
+            split_tf32(im ? c[v].x : -c[v].y, h, l);
+            hi[v] = __float_as_uint(h);
+            lo[v] = __float_as_uint(l);
           }
           tmem_st16(trow + 64u * s + 16u, hi);
           tmem_st16(trow + 64u * s + 48u, lo);
           tmem_wait_st();
           tc_fence_before();
         }
-        mbar_arrive(&full_bar[s]);
-        // next slab; its loads overlap the wait for the next ring slot
-        if (++tt == rank[bi]) {
-          tt = 0;
-          if (++j == 4) {
-            j = 0;
-            do ++bi; while (bi < it.z && rank[bi] == 0);
-          }
-        }
-        if (bi < it.z) load_c(bi, j, tt, c);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&full_bar[s]);
       }
     } else {
       // -------------------------------------------------------- B producers
       // The 16 rows of xhat_c of slab j are loaded once per (b, j) and reused
-      // for every t.
+      // for every t; d_t is loaded three slabs ahead (register chain).
       const int pb = tid - 32 - NA;
-      auto load_d = [&](int bi, int tt, float2 (&dv)[NB]) {
-        const float2* Dt = Df + ((size_t)bi * cap + tt) * Ls;
+      auto load_d = [&](const SlabPos& sp, float2 (&dv)[NB]) {
+        if (sp.bi >= it.z) return;
+        const float2* Dt = Df + ((size_t)sp.bi * cap + sp.tt) * Ls;
 #pragma unroll
         for (int i = 0; i < NB; ++i) {
           const int e = pb + NBP * i;
@@ -213,8 +247,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           dv[i] = (e < 4 * NC && lg < Ls) ? Dt[lg] : make_float2(0.f, 0.f);
         }
       };
-      auto load_x = [&](int bi, int j, float2 (&xv)[NB][4]) {
-        const float2* xc = xhat + (size_t)blocks[bi].y * TP * Ls;
+      auto load_x = [&](const SlabPos& sp, float2 (&xv)[NB][4]) {
+        const float2* xc = xhat + (size_t)blocks[sp.bi].y * TP * Ls;
 #pragma unroll
         for (int i = 0; i < NB; ++i) {
           const int e = pb + NBP * i;
@@ -222,17 +256,21 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           const bool in = e < 4 * NC && lg < Ls;
 #pragma unroll
           for (int v = 0; v < 4; ++v)
-            xv[i][v] = in ? xc[(size_t)(16 * j + 4 * qq + v) * Ls + lg] : make_float2(0.f, 0.f);
+            xv[i][v] = in ? xc[(size_t)(16 * sp.j + 4 * qq + v) * Ls + lg] : make_float2(0.f, 0.f);
         }
       };
-      int bi = it.y, j = 0, tt = 0;
-      while (bi < it.z && rank[bi] == 0) ++bi;
-      float2 dv[NB], xv[NB][4];
-      if (bi < it.z) {
-        load_x(bi, 0, xv);
-        load_d(bi, 0, dv);
-      }
-      for (; bi < it.z; ++use) {
+      SlabPos cur, ahead;
+      cur.start(it.y, it.z, rank);
+      ahead = cur;
+      float2 d0[NB], d1[NB], d2[NB], xv[NB][4];
+      if (cur.bi < it.z) load_x(cur, xv);
+      load_d(ahead, d0);
+      if (ahead.bi < it.z) ahead.next(it.z, rank);
+      load_d(ahead, d1);
+      if (ahead.bi < it.z) ahead.next(it.z, rank);
+      load_d(ahead, d2);
+      if (ahead.bi < it.z) ahead.next(it.z, rank);
+      for (; cur.bi < it.z; ++use) {
         const int s = (int)(use % NSTAGE);
         const uint32_t round = use / NSTAGE;
         if (round > 0) mbar_wait(&empty_bar[s], (round - 1) & 1u, &abort_sh, err, ERR_TIMEOUT);
@@ -248,8 +286,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
               float re[4], imv[4];
 #pragma unroll
               for (int v = 0; v < 4; ++v) {
-                re[v] = fmaf(dv[i].x, xv[i][v].x, -dv[i].y * xv[i][v].y);
-                imv[v] = fmaf(dv[i].x, xv[i][v].y, dv[i].y * xv[i][v].x);
+                re[v] = fmaf(d0[i].x, xv[i][v].x, -d0[i].y * xv[i][v].y);
+                imv[v] = fmaf(d0[i].x, xv[i][v].y, d0[i].y * xv[i][v].x);
               }
               st_split4(Bhi, Blo, core_off(l, 4 * qq), re[0], re[1], re[2], re[3]);
               st_split4(Bhi, Blo, core_off(l, 16 + 4 * qq), imv[0], imv[1], imv[2], imv[3]);
@@ -257,17 +295,17 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           }
           fence_async_shared();
         }
-        mbar_arrive(&full_bar[s]);
-        // next slab; its loads overlap the wait for the next ring slot
-        if (++tt == rank[bi]) {
-          tt = 0;
-          if (++j == 4) {
-            j = 0;
-            do ++bi; while (bi < it.z && rank[bi] == 0);
-          }
-          if (bi < it.z) load_x(bi, j, xv);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&full_bar[s]);
+        cur.next(it.z, rank);
+#pragma unroll
+        for (int i = 0; i < NB; ++i) {
+          d0[i] = d1[i];
+          d1[i] = d2[i];
         }
-        if (bi < it.z) load_d(bi, tt, dv);
+        load_d(ahead, d2);
+        if (ahead.bi < it.z) ahead.next(it.z, rank);
+        if (cur.bi < it.z && cur.tt == 0) load_x(cur, xv);
       }
     }
     // ------------------------------------------- epilogue: TMEM -> partial tile
@@ -299,6 +337,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     tc_fence_after();
   }
   // ------------------------------------------------------------------ teardown
+  if (warp == LOADER && lane == 0) {
+    // every copy issued has landed before the CTA's shared memory is released
+    const uint32_t first = c_issued > NCS ? c_issued - NCS : 0;
+    for (uint32_t u = first; u < c_issued; ++u)
+      mbar_wait(&cfull_bar[u % NCS], (u / NCS) & 1u, &never_sh, err, ERR_TIMEOUT);
+  }
   if (warp == 0) {
     // every MMA this thread issued has finished before TMEM is released
     if (lane == 0) mma_commit(&fin_bar);

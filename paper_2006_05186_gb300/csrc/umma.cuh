@@ -46,10 +46,12 @@ __device__ __forceinline__ uint32_t to_tf32(float x) {
   return r;
 }
 
-// x = hi + lo + O(2^-22 |x|), hi and lo both exact in tf32.
+// x = hi + lo exactly, hi rounded to tf32 (|lo| <= 2^-11 |x|).  lo is left
+// in fp32: the tensor core reads its tf32 part (truncation), so the pair
+// carries x to 2^-21 |x|.
 __device__ __forceinline__ void split_tf32(float x, float& hi, float& lo) {
   hi = __uint_as_float(to_tf32(x));
-  lo = __uint_as_float(to_tf32(x - hi));
+  lo = x - hi;
 }
 
 // ---- mbarriers -------------------------------------------------------------
@@ -99,6 +101,24 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile
       }
     }
   }
+}
+
+// One arrival on *b that also expects `bytes` of asynchronous copies.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(
+                   smem_u32(b)),
+               "r"(bytes)
+               : "memory");
+}
+
+// Bulk copy of `bytes` (multiple of 16, both addresses 16-byte aligned) from
+// global to this CTA's shared memory; completes as transaction bytes on *b.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* b) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(b))
+      : "memory");
 }
 
 // ---- proxy and tcgen05 ordering fences --------------------------------------
