@@ -249,8 +249,10 @@ __device__ void expand_transfer(const R* __restrict__ Etr, int s, int m, int p, 
 }
 
 // Up-sweep for one level: xhat_r = sum_{s in sons(r)} E_{s,r}^T xhat_s.
-// Both transfer matrices are expanded once per block; each son's tile of
-// p x LC coefficients is staged in shared memory by one coalesced load.
+// One block per (node, chunk of LC frequencies), so that the top levels with
+// few nodes still fill the GPU; both transfer matrices are expanded per
+// block and each son's p x LC tile is staged in shared memory by one
+// coalesced load.
 template <class R>
 __global__ void __launch_bounds__(256) k_upsweep(int node0, int Ls, int m, int p,
                                                  const int* __restrict__ son0,
@@ -267,7 +269,8 @@ __global__ void __launch_bounds__(256) k_upsweep(int node0, int Ls, int m, int p
   expand_transfer<R>(Etr, sons[0], m, p, E);
   expand_transfer<R>(Etr, sons[1], m, p, E + MAXP * MAXP);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  for (int l0 = 0; l0 < Ls; l0 += LC) {
+  {
+    const int l0 = blockIdx.y * LC;
     C acc[MAXP / 8];
 #pragma unroll
     for (int k = 0; k < MAXP / 8; ++k) acc[k] = cz<C>();
@@ -365,7 +368,8 @@ __global__ void __launch_bounds__(256) k_far_coupling(int Ls, int p, int cap,
 }
 
 // Down-sweep for one level: yhat_s += E_{s,r} yhat_r for every node s of the
-// level; the parent's tile of p x LC coefficients is staged in shared memory.
+// level; one block per (node, chunk of LC frequencies), the parent's p x LC
+// tile staged in shared memory.
 template <class R>
 __global__ void __launch_bounds__(256) k_downsweep(int node0, int Ls, int m, int p,
                                                    const int* __restrict__ parent,
@@ -381,14 +385,15 @@ __global__ void __launch_bounds__(256) k_downsweep(int node0, int Ls, int m, int
   expand_transfer<R>(Etr, s, m, p, E);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const C* yr = yhat + (size_t)r * p * Ls;
-  for (int l0 = 0; l0 < Ls; l0 += LC) {
+  {
+    const int l0 = blockIdx.y * LC;
     __syncthreads();
     for (int t = threadIdx.x; t < p * LC; t += blockDim.x) {
       const int mu = t / LC, l = t - mu * LC;
       Ys[t] = (l0 + l < Ls) ? yr[(size_t)mu * Ls + l0 + l] : cz<C>();
     }
     __syncthreads();
-    if (l0 + lane >= Ls) continue;
+    if (l0 + lane >= Ls) return;
     for (int lam = w; lam < p; lam += 8) {
       C z = cz<C>();
       for (int mu = 0; mu < p; ++mu) {
@@ -531,7 +536,7 @@ static int apply_t(cqm_handle* h, const OpView<R>& V, const double2* x, double2*
       const int n0 = h->level_begin[lv], n1 = h->level_begin[lv + 1];
       if (n1 > n0) {
         ProfScope ps_(h, CQM_K_UPSWEEP);
-        k_upsweep<R><<<n1 - n0, 256, upsweep_smem<R>(), S>>>(n0, Ls, m, p, h->node_son0.p, h->node_son1.p, V.Etr, V.xhat);
+        k_upsweep<R><<<dim3((unsigned)(n1 - n0), (unsigned)((Ls + LC - 1) / LC)), 256, upsweep_smem<R>(), S>>>(n0, Ls, m, p, h->node_son0.p, h->node_son1.p, V.Etr, V.xhat);
       }
     }
     cudaMemsetAsync(V.yhat, 0, sizeof(C) * (size_t)h->n_nodes * p * Ls, S);
@@ -549,7 +554,7 @@ static int apply_t(cqm_handle* h, const OpView<R>& V, const double2* x, double2*
       const int n0 = h->level_begin[lv], n1 = h->level_begin[lv + 1];
       if (n1 > n0) {
         ProfScope ps_(h, CQM_K_DOWNSWEEP);
-        k_downsweep<R><<<n1 - n0, 256, downsweep_smem<R>(), S>>>(n0, Ls, m, p, h->node_parent.p, V.Etr, V.yhat);
+        k_downsweep<R><<<dim3((unsigned)(n1 - n0), (unsigned)((Ls + LC - 1) / LC)), 256, downsweep_smem<R>(), S>>>(n0, Ls, m, p, h->node_parent.p, V.Etr, V.yhat);
       }
     }
     {
