@@ -113,6 +113,10 @@ typedef struct cqm_params {
                              arithmetic (~48 bits) on the FP32 pipes, and the C
                              factors are held as float-float pairs after setup;
                              0 = FP64                                     [1]   */
+  int32_t expand_near;    /* H2MACA: after the MACA, expand every near block per
+                             frequency (sum_t C_t d_t, FP64 with an FP32 copy,
+                             Ls x #near entries x 24 bytes) and apply the near
+                             field from it; 0 = apply it from the factors  [1]   */
   const cqm_allocator* allocator; /* NULL: stream-ordered CUDA pool        [NULL] */
 } cqm_params;
 

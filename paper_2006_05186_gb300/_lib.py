@@ -56,6 +56,7 @@ class cqm_params(C.Structure):
         ("profile", C.c_int32), ("precond", C.c_int32), ("inner_fp32", C.c_int32),
         ("inner_rtol", C.c_double), ("tensor_cores", C.c_int32), ("cache_quadrature", C.c_int32),
         ("exact_ff", C.c_int32),
+        ("expand_near", C.c_int32),
         ("allocator", C.POINTER(cqm_allocator)),
     ]
 

@@ -74,6 +74,7 @@ int cqm_params_default(cqm_params* p) {
   p->inner_fp32 = 1;
   p->inner_rtol = 1e-5;
   p->exact_ff = 1;
+  p->expand_near = 1;
   p->cache_quadrature = 1;
   p->tensor_cores = 1;
   p->allocator = nullptr;
@@ -115,6 +116,7 @@ int cqm_bem_destroy(cqm_handle* h) {
   h->part_f.free(A); h->part_d.free(A);
   h->pt_off.free(A); h->pt_cnt.free(A); h->pt_r.free(A); h->pt_c.free(A);
   h->nearC_f.free(A); h->nearD_f.free(A); h->farC_f.free(A); h->farD_f.free(A);
+  h->nearV.free(A); h->nearV_f.free(A); h->nearV_off.free(A);
   h->xhat_f.free(A); h->yhat_f.free(A); h->Uleaf_f.free(A); h->Etr_f.free(A);
   cudaStreamSynchronize(h->stream);
   prof_release(h);
@@ -199,6 +201,7 @@ int cqm_bem_setup(const cqm_mesh* mesh, double dt, int32_t N, int32_t bdf_order,
       if ((st = build_maca(h)) != CQM_OK) break;
       if ((st = build_work_items(h)) != CQM_OK) break;
       if (p.precond && (st = build_precond(h)) != CQM_OK) break;
+      if (p.expand_near && (st = build_near_expanded(h)) != CQM_OK) break;
       if (p.inner_fp32) {
         if ((st = build_f32_copy(h)) != CQM_OK) break;
         h->use_f32 = true;

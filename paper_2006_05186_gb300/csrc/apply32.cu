@@ -97,7 +97,9 @@ __global__ void k_far_reduce_f32(int Ls, const int* __restrict__ rows,
   }
 }
 
-// Near field; leaf clusters of at most 32 triangles (8 warps x 4 rows).
+// Near field; leaf clusters of at most 32 triangles: warp w owns rows
+// w, w + 8, w + 16, w + 24, so a leaf of #r rows keeps every warp at
+// ceil(#r / 8) rows or one fewer.
 template <int NLT>
 __global__ void __launch_bounds__(256) k_near_apply_f32(
     int M, int Ls, int cap, const int4* __restrict__ items, const int2* __restrict__ blocks,
@@ -111,7 +113,7 @@ __global__ void __launch_bounds__(256) k_near_apply_f32(
   const int r = it.x;
   const int rb = begin[r], nr = end[r] - rb;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int i0 = w * 4;
+  const int nrw = (nr - w + 7) >> 3;  // rows of this warp: w + 8 i for i < nrw
   for (int l0 = 0; l0 < Ls; l0 += LW) {
     float2 acc[4][NLT];
 #pragma unroll
@@ -145,9 +147,11 @@ __global__ void __launch_bounds__(256) k_near_apply_f32(
           for (int k = 0; k < NLT; ++k) xd[k] = f2mul(d[k], Xs[j * LW + lane + 32 * k]);
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
-            const float2 cv = (i0 + i < nr) ? Cs[(i0 + i) * nc + j] : make_float2(0.f, 0.f);
+            if (i < nrw) {
+              const float2 cv = Cs[(w + 8 * i) * nc + j];
 #pragma unroll
-            for (int k = 0; k < NLT; ++k) cfma(acc[i][k], cv, xd[k]);
+              for (int k = 0; k < NLT; ++k) cfma(acc[i][k], cv, xd[k]);
+            }
           }
         }
       }
@@ -157,7 +161,7 @@ __global__ void __launch_bounds__(256) k_near_apply_f32(
 #pragma unroll
       for (int k = 0; k < NLT; ++k) {
         const int l = l0 + lane + 32 * k;
-        if (i0 + i < nr && l < Ls) part[((size_t)blockIdx.x * 32 + i0 + i) * Ls + l] = acc[i][k];
+        if (i < nrw && l < Ls) part[((size_t)blockIdx.x * 32 + w + 8 * i) * Ls + l] = acc[i][k];
       }
   }
 }
@@ -224,6 +228,7 @@ int far_coupling_f32(cqm_handle* h) {
 int near_apply_f32(cqm_handle* h, const double2* x, double2* y) {
   const int n = h->n_near_items;
   ProfScope ps_(h, CQM_K_NEAR_APPLY);
+  if (h->near_expanded) return near_apply_expanded(h, x, y, false);
 #define LAUNCH_NLT(N)                                                                              \
   k_near_apply_f32<N><<<n, 256, 0, h->stream>>>(                                                   \
       h->M, h->Ls, h->rank_cap, h->near_items.p, h->near_rc.p, h->near_rank.p, h->near_off.p,      \

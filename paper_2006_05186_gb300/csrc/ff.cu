@@ -295,6 +295,7 @@ int setup_ff(cqm_handle* h) {
 
 int near_apply_ff(cqm_handle* h, const double2* x, double2* y) {
   ProfScope ps_(h, CQM_K_NEAR_EXACT);
+  if (h->near_expanded) return near_apply_expanded(h, x, y, true);
   k_near_apply_ff<<<(unsigned)h->n_near_items, 256, 0, h->stream>>>(
       h->M, h->Ls, h->rank_cap, h->near_items.p, h->near_rc.p, h->near_rank.p, h->near_off.p,
       (const ffc*)h->nearC.p, h->nearD.p, h->node_begin.p, h->node_end.p, h->perm.p, x, h->part_d.p);

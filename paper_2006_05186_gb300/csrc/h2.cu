@@ -635,8 +635,10 @@ int build_f32_copy(cqm_handle* h) {
     }
     return CQM_OK;
   };
-  CQM_TRY(cc(h->nearC, h->nearC_f));
-  CQM_TRY(cc(h->nearD, h->nearD_f));
+  if (!h->near_expanded) {  // the expanded near field replaces the factored FP32 near field
+    CQM_TRY(cc(h->nearC, h->nearC_f));
+    CQM_TRY(cc(h->nearD, h->nearD_f));
+  }
   h->farC_f_transposed = h->params.tensor_cores != 0 && h->p == 64;
   if (h->farC_f_transposed) {
     CQM_TRY(h->farC_f.allocate(h->alloc, std::max<size_t>(1, h->farC.n)));

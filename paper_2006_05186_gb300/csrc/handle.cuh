@@ -83,7 +83,14 @@ struct cqm_handle {
   // FP32 copy of the operator (inner iterations of mixed precision)
   bool use_f32 = false;
   bool factors_ff = false;
-  bool farC_f_transposed = false;  // farC_f tiles stored nu-major (tensor-core coupling)  // nearC / farC hold float-float pairs (hi re, hi im, lo re, lo im)
+  bool farC_f_transposed = false;  // farC_f tiles stored nu-major (tensor-core coupling)
+  // expanded near field: block b, frequency l, entry (i, j) at
+  // nearV_off[b] + (l #c + j) #r + i (FP64 and an FP32 copy)
+  bool near_expanded = false;
+  cqm::DArray<double2> nearV;
+  cqm::DArray<float2> nearV_f;
+  cqm::DArray<int64_t> nearV_off;
+  std::vector<int64_t> h_nearV_off;  // nearC / farC hold float-float pairs (hi re, hi im, lo re, lo im)
   cqm::DArray<float2> nearC_f, nearD_f, farC_f, farD_f, xhat_f, yhat_f;
   cqm::DArray<float> Uleaf_f, Etr_f;
 
@@ -148,6 +155,10 @@ int setup_ff(cqm_handle* h);
 int near_apply_ff(cqm_handle* h, const double2* x, double2* y);
 int far_coupling_ff(cqm_handle* h);
 int factors_to_ff(cqm_handle* h);  // after every FP64 reader of the C factors at setup
+
+// near_dense.cu (expanded near field)
+int build_near_expanded(cqm_handle* h);  // after the near MACA, before factors_to_ff
+int near_apply_expanded(cqm_handle* h, const double2* x, double2* y, bool fp64);
 
 // maca.cu
 int build_maca(cqm_handle* h);

@@ -233,3 +233,26 @@ def test_inner_operator_fp32_accuracy(lib, tensor_cores):
     # FP32-class: the three-product TF32 split keeps ~21 bits per operand; a
     # wrong fragment layout would give errors of order one
     assert np.max(err) < 1e-5, err
+
+
+def test_expanded_near_field_equals_factored(lib):
+    """The near field expanded per frequency (sum_t C_t d_t in FP64) is the
+    factored operator up to rounding: the FP64 applies agree to 1e-12, and the
+    FP32 inner operator of the expanded form is at least as close to the FP64
+    operator as the factored FP32 one (its entries are rounded once)."""
+    m = synth.icosphere(3)
+    N, dt = 64, 0.1
+    ops = {e: _op(m, dt, N, expand_near=e) for e in (0, 1)}
+    Ls = ops[0].Ls
+    rng = np.random.default_rng(11)
+    x = rng.standard_normal((Ls, m.nt)) + 1j * rng.standard_normal((Ls, m.nt))
+    y = {e: ops[e].apply(x) for e in (0, 1)}
+    yi = {e: ops[e].apply_inner(x) for e in (0, 1)}
+    for l in range(Ls):
+        nrm = np.linalg.norm(y[0][l])
+        assert np.linalg.norm(y[1][l] - y[0][l]) <= 1e-12 * nrm, l
+        e_fact = np.linalg.norm(yi[0][l] - y[0][l]) / nrm
+        e_exp = np.linalg.norm(yi[1][l] - y[1][l]) / nrm
+        assert e_exp <= 1e-5 and e_exp <= 2.0 * e_fact + 1e-7, (l, e_exp, e_fact)
+    for op in ops.values():
+        op.close()
