@@ -151,27 +151,44 @@ class ClockSampler:
 
 def kernel_models(info, Ls, p, tensor_cores):
     """Algorithmic work per launch of the contraction kernels and the peak
-    that bounds each.  Complex multiply-add = 8 flops; coupling:
-    sum_far rank * p^2 * Ls; near field: sum_near rank * #r#c * Ls.
-    The tensor-core coupling is counted by its useful flops against the TF32
-    tensor peak (its three-product split executes three times as many).  The
-    float-float kernels issue 48 FP32 instructions per complex multiply-add
-    (four exact products with TwoSum accumulation); their work is counted in
-    FP32 issue slots, 2 flops each, against the FP32 peak."""
+    that bounds each.  Complex multiply-add = 8 flops.  Factored forms:
+    coupling sum_far rank * p^2 * Ls, near field sum_near rank * #r#c * Ls
+    complex multiply-adds.  The tensor-core coupling is counted by its useful
+    flops against the TF32 tensor peak (its three-product split executes three
+    times as many).  The float-float kernels issue 48 FP32 instructions per
+    complex multiply-add (four exact products with TwoSum accumulation); their
+    work is counted in FP32 issue slots, 2 flops each, against the FP32 peak.
+    Expanded forms stream their tables once per launch: the FP32 near field
+    8 bytes and the float-float far couplings 16 bytes per entry and
+    frequency, against the measured HBM bandwidth; the FP64 near field does
+    4 FP64 FMAs per entry and frequency against the FP64 peak."""
     cmac_far = info["rank_sum_far"] * p * p * Ls
     cmac_near = info["near_rank_entries"] * Ls
-    fp32 = dict(bound="alu", peak=FP32_PEAK_TFLOPS, peak_source=FP32_PEAK_SOURCE)
+    fp32 = dict(bound="alu", peak=FP32_PEAK_TFLOPS, peak_source=FP32_PEAK_SOURCE, unit="TFLOP/s")
     models = {
-        "far_coupling": dict(fp32, flops=8.0 * cmac_far, what="FP32 complex MAC, inner operator"),
-        "near_apply": dict(fp32, flops=8.0 * cmac_near, what="FP32 complex MAC, inner operator"),
-        "far_exact": dict(fp32, flops=2.0 * 48 * cmac_far, what="float-float complex MAC (FP32 issue)"),
-        "near_exact": dict(fp32, flops=2.0 * 48 * cmac_near, what="float-float complex MAC (FP32 issue)"),
+        "far_coupling": dict(fp32, work=8.0 * cmac_far, what="FP32 complex MAC, inner operator"),
+        "near_apply": dict(fp32, work=8.0 * cmac_near, what="FP32 complex MAC, inner operator"),
+        "far_exact": dict(fp32, work=2.0 * 48 * cmac_far, what="float-float complex MAC (FP32 issue)"),
+        "near_exact": dict(fp32, work=2.0 * 48 * cmac_near, what="float-float complex MAC (FP32 issue)"),
     }
     if tensor_cores and p == 64:
         peak, src = tf32_peak()
         models["far_coupling"] = dict(
-            bound="tensor", peak=peak, peak_source=src, flops=8.0 * cmac_far,
+            bound="tensor", peak=peak, peak_source=src, unit="TFLOP/s", work=8.0 * cmac_far,
             what="complex MAC on tcgen05 TF32 (useful flops; the 3-product split executes 3x)")
+    pk, src = _peaks()
+    hbm = dict(bound="hbm", peak=pk["hbm_gbs"], unit="GB/s",
+               peak_source=f"{src} STREAM-style copy, MEASURED_PEAKS.json hbm_gbs")
+    entries = info["near_entries"] * Ls
+    if info.get("near_expanded"):
+        models["near_apply"] = dict(hbm, work=8.0 * entries,
+                                    what="expanded FP32 near field streamed (8 B per entry and frequency)")
+        models["near_exact"] = dict(bound="alu", peak=FP64_PEAK_TFLOPS, unit="TFLOP/s",
+                                    peak_source="recipe nominal FP64 (a probe measured 1.19)",
+                                    work=8.0 * entries, what="expanded FP64 near field, FP64 complex MAC")
+    if info.get("far_expanded"):
+        models["far_exact"] = dict(hbm, work=16.0 * info["far_coupling"] * Ls,
+                                   what="expanded float-float far couplings streamed (16 B per entry and frequency)")
     return models
 
 
@@ -185,9 +202,10 @@ def roofline_of(prof, models):
 
 
 def roofline_entry(name, n, ms, mdl):
-    achieved = mdl["flops"] / (ms / n / 1e3) / 1e12
+    scale = 1e9 if mdl["unit"] == "GB/s" else 1e12
+    achieved = mdl["work"] / (ms / n / 1e3) / scale
     return {"bound": mdl["bound"], "kernel": name, "what": mdl["what"], "achieved": achieved,
-            "peak": mdl["peak"], "unit": "TFLOP/s", "frac": achieved / mdl["peak"], "traffic": None,
+            "peak": mdl["peak"], "unit": mdl["unit"], "frac": achieved / mdl["peak"], "traffic": None,
             "launches": n, "ms_per_launch": ms / n, "peak_source": mdl["peak_source"]}
 
 

@@ -117,6 +117,11 @@ typedef struct cqm_params {
                              frequency (sum_t C_t d_t, FP64 with an FP32 copy,
                              Ls x #near entries x 24 bytes) and apply the near
                              field from it; 0 = apply it from the factors  [1]   */
+  int32_t expand_far;     /* H2MACA with exact_ff: expand every far coupling per
+                             frequency (sum_t C_t d_t, float-float, Ls x p^2 x 16
+                             bytes per far block) for the FP64-accurate apply,
+                             if that takes at most 40% of the device memory and
+                             the allocation succeeds; 0 = keep it factored [1]   */
   const cqm_allocator* allocator; /* NULL: stream-ordered CUDA pool        [NULL] */
 } cqm_params;
 
@@ -134,6 +139,8 @@ typedef struct cqm_setup_info {
   int64_t device_bytes;         /* device memory held by the handle */
   double t_geometry_ms, t_tree_ms, t_bases_ms, t_assembly_ms; /* stage times (CUDA events) */
   int64_t near_rank_entries;    /* sum over near blocks of rank * #r * #c */
+  int32_t near_expanded;        /* 1 if the near field is held expanded per frequency */
+  int32_t far_expanded;         /* 1 if the far couplings of the FP64-accurate apply are */
 } cqm_setup_info;
 
 /* Per-solve summary. */

@@ -57,6 +57,7 @@ class cqm_params(C.Structure):
         ("inner_rtol", C.c_double), ("tensor_cores", C.c_int32), ("cache_quadrature", C.c_int32),
         ("exact_ff", C.c_int32),
         ("expand_near", C.c_int32),
+        ("expand_far", C.c_int32),
         ("allocator", C.POINTER(cqm_allocator)),
     ]
 
@@ -70,6 +71,7 @@ class cqm_setup_info(C.Structure):
         ("rank_max", C.c_int32), ("R", C.c_double), ("device_bytes", C.c_int64),
         ("t_geometry_ms", C.c_double), ("t_tree_ms", C.c_double), ("t_bases_ms", C.c_double),
         ("t_assembly_ms", C.c_double), ("near_rank_entries", C.c_int64),
+        ("near_expanded", C.c_int32), ("far_expanded", C.c_int32),
     ]
 
 

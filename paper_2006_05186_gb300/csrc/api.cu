@@ -75,6 +75,7 @@ int cqm_params_default(cqm_params* p) {
   p->inner_rtol = 1e-5;
   p->exact_ff = 1;
   p->expand_near = 1;
+  p->expand_far = 1;
   p->cache_quadrature = 1;
   p->tensor_cores = 1;
   p->allocator = nullptr;
@@ -116,7 +117,7 @@ int cqm_bem_destroy(cqm_handle* h) {
   h->part_f.free(A); h->part_d.free(A);
   h->pt_off.free(A); h->pt_cnt.free(A); h->pt_r.free(A); h->pt_c.free(A);
   h->nearC_f.free(A); h->nearD_f.free(A); h->farC_f.free(A); h->farD_f.free(A);
-  h->nearV.free(A); h->nearV_f.free(A); h->nearV_off.free(A);
+  h->nearV.free(A); h->nearV_f.free(A); h->nearV_off.free(A); h->farS.free(A);
   h->xhat_f.free(A); h->yhat_f.free(A); h->Uleaf_f.free(A); h->Etr_f.free(A);
   cudaStreamSynchronize(h->stream);
   prof_release(h);
@@ -207,6 +208,7 @@ int cqm_bem_setup(const cqm_mesh* mesh, double dt, int32_t N, int32_t bdf_order,
         h->use_f32 = true;
       }
       if (p.exact_ff && (st = factors_to_ff(h)) != CQM_OK) break;
+      if (p.exact_ff && p.expand_far && (st = build_far_expanded(h)) != CQM_OK) break;
     }
     cudaEventRecord(ev[4], h->stream);
     cudaError_t e = cudaStreamSynchronize(h->stream);
@@ -221,6 +223,8 @@ int cqm_bem_setup(const cqm_mesh* mesh, double dt, int32_t N, int32_t bdf_order,
     I.n_nodes = h->n_nodes; I.n_leaves = h->n_leaves; I.n_near = h->n_near; I.n_far = h->n_far;
     I.R = h->R;
     I.device_bytes = h->alloc.bytes_held;
+    I.near_expanded = h->near_expanded ? 1 : 0;
+    I.far_expanded = h->far_expanded ? 1 : 0;
     I.t_geometry_ms = elapsed(ev[0], ev[1]);
     I.t_tree_ms = elapsed(ev[1], ev[2]);
     I.t_bases_ms = elapsed(ev[2], ev[3]);

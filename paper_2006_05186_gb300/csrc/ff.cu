@@ -308,11 +308,130 @@ int near_apply_ff(cqm_handle* h, const double2* x, double2* y) {
 
 int far_coupling_ff(cqm_handle* h) {
   ProfScope ps_(h, CQM_K_FAR_EXACT);
+  if (h->far_expanded) return far_apply_expanded_ff(h);
   k_far_coupling_ff<<<(unsigned)h->n_far_items, 256, coupling_smem_ff(h->p), h->stream>>>(
       h->Ls, h->p, h->rank_cap, h->far_items.p, h->far_rc.p, h->far_rank.p, (const ffc*)h->farC.p, h->farD.p,
       h->xhat.p, h->part_d.p);
   k_far_reduce_d<<<(unsigned)h->h_far_rows.size(), 256, 0, h->stream>>>(
       h->Ls, h->p, h->d_far_rows.p, h->far_item_ptr.p, h->part_d.p, h->yhat.p);
+  CQM_CHECK_LAUNCH();
+  return CQM_OK;
+}
+
+}  // namespace cqm
+
+namespace cqm {
+
+// Expanded far couplings for the FP64-accurate apply: S_b(l) = sum_t C_t d_t(l)
+// (eq. lrfinal) per far block and solved frequency, as float-float pairs,
+// stored column-major per frequency: entry (l, mu, nu) of block b at
+// (b Ls + l) p^2 + nu p + mu.  One block per (far block, chunk of FAR_NF
+// frequencies), a thread per entry.
+namespace {
+constexpr int FAR_NF = 8;
+}
+
+__global__ void __launch_bounds__(256) k_far_expand_ff(int Ls, int p, int cap, const int* __restrict__ rank,
+                                                       const ffc* __restrict__ Cf, const double2* __restrict__ Df,
+                                                       ffc* __restrict__ S) {
+  __shared__ ffc Ds[32][FAR_NF];
+  const int b = blockIdx.y, l0 = blockIdx.x * FAR_NF;
+  const int rk = rank[b], nf = min(FAR_NF, Ls - l0);
+  for (int t = threadIdx.x; t < rk * FAR_NF; t += blockDim.x) {
+    const int tt = t / FAR_NF, f = t - tt * FAR_NF;
+    Ds[tt][f] = f < nf ? ffc_from(Df[((size_t)b * cap + tt) * Ls + l0 + f]) : ffc_zero();
+  }
+  __syncthreads();
+  const int pp = p * p;
+  for (int e = threadIdx.x; e < pp; e += blockDim.x) {
+    const int mu = e / p, nu = e - mu * p;
+    ffc acc[FAR_NF];
+#pragma unroll
+    for (int f = 0; f < FAR_NF; ++f) acc[f] = ffc_zero();
+    for (int tt = 0; tt < rk; ++tt) {
+      const ffc c = Cf[((size_t)b * cap + tt) * pp + e];
+#pragma unroll
+      for (int f = 0; f < FAR_NF; ++f) ffc_mac(acc[f], c, Ds[tt][f]);
+    }
+    for (int f = 0; f < nf; ++f) {
+      ffc_renorm(acc[f]);
+      S[((size_t)b * Ls + l0 + f) * pp + (size_t)nu * p + mu] = acc[f];
+    }
+  }
+}
+
+// yhat_r(l)[mu] = sum over the far blocks (r, c) of row r of
+// sum_nu S_b(l)[mu][nu] xhat_c(l)[nu], in float-float: one warp per (row
+// cluster, frequency), lane k owns rows k and k + 32, blocks in their stored
+// order.  Overwrites yhat on the row.
+__global__ void __launch_bounds__(256) k_far_dense_ff(int Ls, int p, int nrows, const int* __restrict__ rows,
+                                                      const int* __restrict__ rowptr,
+                                                      const int2* __restrict__ rc,
+                                                      const ffc* __restrict__ S,
+                                                      const double2* __restrict__ xhat,
+                                                      double2* __restrict__ yhat) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int l = blockIdx.x * 8 + w;
+  if (l >= Ls) return;
+  const int r = rows[blockIdx.y];
+  const int pp = p * p;
+  ffc acc0 = ffc_zero(), acc1 = ffc_zero();
+  const bool has0 = lane < p, has1 = lane + 32 < p;
+  for (int bi = rowptr[r]; bi < rowptr[r + 1]; ++bi) {
+    const int c = rc[bi].y;
+    const double2* xc = xhat + (size_t)c * p * Ls + l;
+    const ffc x0 = has0 ? ffc_from(xc[(size_t)lane * Ls]) : ffc_zero();
+    const ffc x1 = has1 ? ffc_from(xc[(size_t)(lane + 32) * Ls]) : ffc_zero();
+    const ffc* Sb = S + ((size_t)bi * Ls + l) * pp;
+    for (int nu = 0; nu < p; ++nu) {
+      const ffc src = nu < 32 ? x0 : x1;
+      ffc xv;
+      xv.rh = __shfl_sync(0xffffffffu, src.rh, nu & 31);
+      xv.ih = __shfl_sync(0xffffffffu, src.ih, nu & 31);
+      xv.rl = __shfl_sync(0xffffffffu, src.rl, nu & 31);
+      xv.il = __shfl_sync(0xffffffffu, src.il, nu & 31);
+      if (has0) ffc_mac(acc0, Sb[(size_t)nu * p + lane], xv);
+      if (has1) ffc_mac(acc1, Sb[(size_t)nu * p + lane + 32], xv);
+      if ((nu & 15) == 15) {
+        ffc_renorm(acc0);
+        ffc_renorm(acc1);
+      }
+    }
+    ffc_renorm(acc0);
+    ffc_renorm(acc1);
+  }
+  double2* yr = yhat + (size_t)r * p * Ls + l;
+  if (has0) yr[(size_t)lane * Ls] = ffc_to(acc0);
+  if (has1) yr[(size_t)(lane + 32) * Ls] = ffc_to(acc1);
+}
+
+int build_far_expanded(cqm_handle* h) {
+  if (h->n_far == 0 || !h->factors_ff) return CQM_OK;
+  const size_t n = (size_t)h->n_far * h->Ls * h->p * h->p;
+  size_t free_b = 0, total_b = 0;
+  CQM_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+  if (n * sizeof(ffc) > total_b / 10 * 4) return CQM_OK;  // over 40% of the device: stay factored
+  if (h->farS.allocate(h->alloc, n) != CQM_OK) {
+    set_last_error("");
+    return CQM_OK;  // the allocation did not fit: stay factored
+  }
+  {
+    ProfScope ps_(h, CQM_K_BASES);
+    dim3 g((unsigned)((h->Ls + FAR_NF - 1) / FAR_NF), (unsigned)h->n_far);
+    k_far_expand_ff<<<g, 256, 0, h->stream>>>(h->Ls, h->p, h->rank_cap, h->far_rank.p,
+                                               (const ffc*)h->farC.p, h->farD.p, (ffc*)h->farS.p);
+  }
+  CQM_CHECK_LAUNCH();
+  h->far_expanded = true;
+  return CQM_OK;
+}
+
+int far_apply_expanded_ff(cqm_handle* h) {
+  const int nfr = (int)h->h_far_rows.size();
+  if (nfr == 0) return CQM_OK;
+  dim3 g((unsigned)((h->Ls + 7) / 8), (unsigned)nfr);
+  k_far_dense_ff<<<g, 256, 0, h->stream>>>(h->Ls, h->p, nfr, h->d_far_rows.p, h->far_rowptr.p,
+                                            h->far_rc.p, (const ffc*)h->farS.p, h->xhat.p, h->yhat.p);
   CQM_CHECK_LAUNCH();
   return CQM_OK;
 }

@@ -90,7 +90,11 @@ struct cqm_handle {
   cqm::DArray<double2> nearV;
   cqm::DArray<float2> nearV_f;
   cqm::DArray<int64_t> nearV_off;
-  std::vector<int64_t> h_nearV_off;  // nearC / farC hold float-float pairs (hi re, hi im, lo re, lo im)
+  std::vector<int64_t> h_nearV_off;
+  // expanded far couplings (float-float pairs) for the FP64-accurate apply:
+  // block b, frequency l, entry (mu, nu) at (b Ls + l) p^2 + nu p + mu
+  bool far_expanded = false;
+  cqm::DArray<double2> farS;  // nearC / farC hold float-float pairs (hi re, hi im, lo re, lo im)
   cqm::DArray<float2> nearC_f, nearD_f, farC_f, farD_f, xhat_f, yhat_f;
   cqm::DArray<float> Uleaf_f, Etr_f;
 
@@ -159,6 +163,9 @@ int factors_to_ff(cqm_handle* h);  // after every FP64 reader of the C factors a
 // near_dense.cu (expanded near field)
 int build_near_expanded(cqm_handle* h);  // after the near MACA, before factors_to_ff
 int near_apply_expanded(cqm_handle* h, const double2* x, double2* y, bool fp64);
+// ff.cu (expanded far couplings of the FP64-accurate apply)
+int build_far_expanded(cqm_handle* h);  // after factors_to_ff; stays factored if it does not fit
+int far_apply_expanded_ff(cqm_handle* h);
 
 // maca.cu
 int build_maca(cqm_handle* h);

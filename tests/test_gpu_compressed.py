@@ -236,13 +236,16 @@ def test_inner_operator_fp32_accuracy(lib, tensor_cores):
 
 
 def test_expanded_near_field_equals_factored(lib):
-    """The near field expanded per frequency (sum_t C_t d_t in FP64) is the
-    factored operator up to rounding: the FP64 applies agree to 1e-12, and the
-    FP32 inner operator of the expanded form is at least as close to the FP64
-    operator as the factored FP32 one (its entries are rounded once)."""
+    """The near field and the far couplings expanded per frequency
+    (sum_t C_t d_t, near in FP64, far in float-float) are the factored
+    operator up to rounding: the FP64-accurate applies agree to 1e-12, and
+    the FP32 inner operator of the expanded near field is at least as close
+    to the FP64 operator as the factored FP32 one (its entries are rounded
+    once)."""
     m = synth.icosphere(3)
     N, dt = 64, 0.1
-    ops = {e: _op(m, dt, N, expand_near=e) for e in (0, 1)}
+    ops = {e: _op(m, dt, N, expand_near=e, expand_far=e) for e in (0, 1)}
+    assert ops[1].info()["device_bytes"] > ops[0].info()["device_bytes"]
     Ls = ops[0].Ls
     rng = np.random.default_rng(11)
     x = rng.standard_normal((Ls, m.nt)) + 1j * rng.standard_normal((Ls, m.nt))
