@@ -202,12 +202,13 @@ int cqm_bem_setup(const cqm_mesh* mesh, double dt, int32_t N, int32_t bdf_order,
       if ((st = build_maca(h)) != CQM_OK) break;
       if ((st = build_work_items(h)) != CQM_OK) break;
       if (p.precond && (st = build_precond(h)) != CQM_OK) break;
-      if (p.expand_near && (st = build_near_expanded(h)) != CQM_OK) break;
+      if (p.expand_near && !p.exact_ff && (st = build_near_expanded(h)) != CQM_OK) break;
       if (p.inner_fp32) {
         if ((st = build_f32_copy(h)) != CQM_OK) break;
         h->use_f32 = true;
       }
       if (p.exact_ff && (st = factors_to_ff(h)) != CQM_OK) break;
+      if (p.exact_ff && p.expand_near && (st = build_near_expanded_ff(h)) != CQM_OK) break;
       if (p.exact_ff && p.expand_far && (st = build_far_expanded(h)) != CQM_OK) break;
     }
     cudaEventRecord(ev[4], h->stream);

@@ -295,7 +295,7 @@ int setup_ff(cqm_handle* h) {
 
 int near_apply_ff(cqm_handle* h, const double2* x, double2* y) {
   ProfScope ps_(h, CQM_K_NEAR_EXACT);
-  if (h->near_expanded) return near_apply_expanded(h, x, y, true);
+  if (h->near_expanded) return h->nearV_ff ? near_apply_expanded_ff(h, x, y) : near_apply_expanded(h, x, y, true);
   k_near_apply_ff<<<(unsigned)h->n_near_items, 256, 0, h->stream>>>(
       h->M, h->Ls, h->rank_cap, h->near_items.p, h->near_rc.p, h->near_rank.p, h->near_off.p,
       (const ffc*)h->nearC.p, h->nearD.p, h->node_begin.p, h->node_end.p, h->perm.p, x, h->part_d.p);
@@ -432,6 +432,131 @@ int far_apply_expanded_ff(cqm_handle* h) {
   dim3 g((unsigned)((h->Ls + 7) / 8), (unsigned)nfr);
   k_far_dense_ff<<<g, 256, 0, h->stream>>>(h->Ls, h->p, nfr, h->d_far_rows.p, h->far_rowptr.p,
                                             h->far_rc.p, (const ffc*)h->farS.p, h->xhat.p, h->yhat.p);
+  CQM_CHECK_LAUNCH();
+  return CQM_OK;
+}
+
+}  // namespace cqm
+
+namespace cqm {
+
+// Expanded near field in float-float, for the FP64-accurate apply: the same
+// table as the FP64 expansion (block b, frequency l, entry (i, j) at
+// nearV_off[b] + (l #c + j) #r + i) with float-float pairs in nearV and their
+// high parts in nearV_f, formed on the FP32 pipes from the float-float C
+// factors.  One block per (near block, chunk of FAR_NF frequencies).
+__global__ void __launch_bounds__(256) k_near_expand_ff(int Ls, int cap, const int2* __restrict__ rc,
+                                                        const int* __restrict__ begin,
+                                                        const int* __restrict__ end,
+                                                        const int64_t* __restrict__ coff,
+                                                        const int* __restrict__ rank,
+                                                        const ffc* __restrict__ C,
+                                                        const double2* __restrict__ D,
+                                                        const int64_t* __restrict__ voff,
+                                                        ffc* __restrict__ V, float2* __restrict__ Vf) {
+  __shared__ ffc Ds[32][FAR_NF];
+  const int b = blockIdx.y, l0 = blockIdx.x * FAR_NF;
+  const int2 c2 = rc[b];
+  const int nr = end[c2.x] - begin[c2.x], nc = end[c2.y] - begin[c2.y];
+  const int rk = rank[b], nf = min(FAR_NF, Ls - l0);
+  for (int t = threadIdx.x; t < rk * FAR_NF; t += blockDim.x) {
+    const int tt = t / FAR_NF, f = t - tt * FAR_NF;
+    Ds[tt][f] = f < nf ? ffc_from(D[((size_t)b * cap + tt) * Ls + l0 + f]) : ffc_zero();
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < nr * nc; e += blockDim.x) {
+    const int i = e / nc, j = e - i * nc;
+    ffc acc[FAR_NF];
+#pragma unroll
+    for (int f = 0; f < FAR_NF; ++f) acc[f] = ffc_zero();
+    for (int tt = 0; tt < rk; ++tt) {
+      const ffc c = C[coff[b] + (size_t)tt * nr * nc + e];
+#pragma unroll
+      for (int f = 0; f < FAR_NF; ++f) ffc_mac(acc[f], c, Ds[tt][f]);
+    }
+    for (int f = 0; f < nf; ++f) {
+      ffc_renorm(acc[f]);
+      const size_t o = voff[b] + ((size_t)(l0 + f) * nc + j) * nr + i;
+      V[o] = acc[f];
+      Vf[o] = make_float2(acc[f].rh, acc[f].ih);
+    }
+  }
+}
+
+// y_l[perm[rb + i]] = sum over the near blocks (r, c) of leaf row r of
+// sum_j V_l[i][j] x_l[perm[cb + j]] in float-float: one warp per (leaf row,
+// frequency), lanes over the rows, blocks in their stored order.
+__global__ void __launch_bounds__(256) k_near_dense_ff(int M, int Ls, const int* __restrict__ leaves,
+                                                       const int* __restrict__ rowptr,
+                                                       const int2* __restrict__ rc,
+                                                       const int* __restrict__ begin,
+                                                       const int* __restrict__ end,
+                                                       const int* __restrict__ perm,
+                                                       const int64_t* __restrict__ voff,
+                                                       const ffc* __restrict__ V,
+                                                       const double2* __restrict__ x,
+                                                       double2* __restrict__ y) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int l = blockIdx.x * 8 + w;
+  if (l >= Ls) return;
+  const int r = leaves[blockIdx.y];
+  const int rb = begin[r], nr = end[r] - rb;
+  const double2* xl = x + (size_t)l * M;
+  ffc acc = ffc_zero();
+  for (int bi = rowptr[r]; bi < rowptr[r + 1]; ++bi) {
+    const int c = rc[bi].y;
+    const int cb = begin[c], nc = end[c] - cb;
+    const ffc xj = lane < nc ? ffc_from(xl[perm[cb + lane]]) : ffc_zero();
+    const ffc* Vb = V + voff[bi] + (size_t)l * nc * nr;
+    for (int j = 0; j < nc; ++j) {
+      ffc xv;
+      xv.rh = __shfl_sync(0xffffffffu, xj.rh, j);
+      xv.ih = __shfl_sync(0xffffffffu, xj.ih, j);
+      xv.rl = __shfl_sync(0xffffffffu, xj.rl, j);
+      xv.il = __shfl_sync(0xffffffffu, xj.il, j);
+      if (lane < nr) ffc_mac(acc, Vb[(size_t)j * nr + lane], xv);
+      if ((j & 15) == 15) ffc_renorm(acc);
+    }
+    ffc_renorm(acc);
+  }
+  if (lane < nr) y[(size_t)l * M + perm[rb + lane]] = ffc_to(acc);
+}
+
+int build_near_expanded_ff(cqm_handle* h) {
+  const int nb = h->n_near;
+  h->h_nearV_off.assign(nb + 1, 0);
+  for (int b = 0; b < nb; ++b) {
+    const int2 rc = h->h_near[b];
+    h->h_nearV_off[b + 1] = h->h_nearV_off[b] + (int64_t)h->Ls * (h->h_end[rc.x] - h->h_begin[rc.x]) *
+                                                     (h->h_end[rc.y] - h->h_begin[rc.y]);
+  }
+  const size_t n = (size_t)std::max<int64_t>(1, h->h_nearV_off[nb]);
+  CQM_TRY(h->nearV_off.allocate(h->alloc, nb + 1));
+  CQM_TRY(h->nearV.allocate(h->alloc, n));
+  CQM_TRY(h->nearV_f.allocate(h->alloc, n));
+  CQM_CUDA_TRY(cudaMemcpyAsync(h->nearV_off.p, h->h_nearV_off.data(), sizeof(int64_t) * (nb + 1),
+                               cudaMemcpyHostToDevice, h->stream));
+  if (nb > 0) {
+    ProfScope ps_(h, CQM_K_BASES);
+    dim3 g((unsigned)((h->Ls + FAR_NF - 1) / FAR_NF), (unsigned)nb);
+    k_near_expand_ff<<<g, 256, 0, h->stream>>>(h->Ls, h->rank_cap, h->near_rc.p, h->node_begin.p,
+                                               h->node_end.p, h->near_off.p, h->near_rank.p,
+                                               (const ffc*)h->nearC.p, h->nearD.p, h->nearV_off.p,
+                                               (ffc*)h->nearV.p, h->nearV_f.p);
+  }
+  CQM_CHECK_LAUNCH();
+  h->near_expanded = true;
+  h->nearV_ff = true;
+  return CQM_OK;
+}
+
+int near_apply_expanded_ff(cqm_handle* h, const double2* x, double2* y) {
+  const int nleaf = (int)h->h_leaves.size();
+  if (nleaf == 0) return CQM_OK;
+  dim3 g((unsigned)((h->Ls + 7) / 8), (unsigned)nleaf);
+  k_near_dense_ff<<<g, 256, 0, h->stream>>>(h->M, h->Ls, h->d_leaves.p, h->near_rowptr.p, h->near_rc.p,
+                                            h->node_begin.p, h->node_end.p, h->perm.p, h->nearV_off.p,
+                                            (const ffc*)h->nearV.p, x, y);
   CQM_CHECK_LAUNCH();
   return CQM_OK;
 }

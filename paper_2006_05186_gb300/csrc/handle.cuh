@@ -87,6 +87,7 @@ struct cqm_handle {
   // expanded near field: block b, frequency l, entry (i, j) at
   // nearV_off[b] + (l #c + j) #r + i (FP64 and an FP32 copy)
   bool near_expanded = false;
+  bool nearV_ff = false;  // nearV holds float-float pairs (expanded after factors_to_ff)
   cqm::DArray<double2> nearV;
   cqm::DArray<float2> nearV_f;
   cqm::DArray<int64_t> nearV_off;
@@ -166,6 +167,8 @@ int near_apply_expanded(cqm_handle* h, const double2* x, double2* y, bool fp64);
 // ff.cu (expanded far couplings of the FP64-accurate apply)
 int build_far_expanded(cqm_handle* h);  // after factors_to_ff; stays factored if it does not fit
 int far_apply_expanded_ff(cqm_handle* h);
+int build_near_expanded_ff(cqm_handle* h);  // after factors_to_ff
+int near_apply_expanded_ff(cqm_handle* h, const double2* x, double2* y);
 
 // maca.cu
 int build_maca(cqm_handle* h);
