@@ -159,9 +159,8 @@ def kernel_models(info, Ls, p, tensor_cores):
     complex multiply-add (four exact products with TwoSum accumulation); their
     work is counted in FP32 issue slots, 2 flops each, against the FP32 peak.
     Expanded forms stream their tables once per launch: the FP32 near field
-    8 bytes and the float-float far couplings 16 bytes per entry and
-    frequency, against the measured HBM bandwidth; the FP64 near field does
-    4 FP64 FMAs per entry and frequency against the FP64 peak."""
+    8 bytes, the float-float near field and far couplings 16 bytes per entry
+    and frequency, against the measured HBM bandwidth."""
     cmac_far = info["rank_sum_far"] * p * p * Ls
     cmac_near = info["near_rank_entries"] * Ls
     fp32 = dict(bound="alu", peak=FP32_PEAK_TFLOPS, peak_source=FP32_PEAK_SOURCE, unit="TFLOP/s")
@@ -183,9 +182,8 @@ def kernel_models(info, Ls, p, tensor_cores):
     if info.get("near_expanded"):
         models["near_apply"] = dict(hbm, work=8.0 * entries,
                                     what="expanded FP32 near field streamed (8 B per entry and frequency)")
-        models["near_exact"] = dict(bound="alu", peak=FP64_PEAK_TFLOPS, unit="TFLOP/s",
-                                    peak_source="recipe nominal FP64 (a probe measured 1.19)",
-                                    work=8.0 * entries, what="expanded FP64 near field, FP64 complex MAC")
+        models["near_exact"] = dict(hbm, work=16.0 * entries,
+                                    what="expanded float-float near field streamed (16 B per entry and frequency)")
     if info.get("far_expanded"):
         models["far_exact"] = dict(hbm, work=16.0 * info["far_coupling"] * Ls,
                                    what="expanded float-float far couplings streamed (16 B per entry and frequency)")

@@ -51,7 +51,9 @@ __global__ void k_restart(int M, int m, const double2* __restrict__ b, const dou
   const bool done = !(bt > tol * bn) || bn == 0.0;
   if (threadIdx.x == 0) {
     beta[l] = bt;
-    thr[l] = fmax(tol * bn, rtol * bt);  // this cycle stops at thr (FP64 residual decides convergence)
+    // this cycle stops at thr; convergence is decided on the FP64 residual at the
+    // next restart, so the cycle aims below tol to land under it in one go
+    thr[l] = fmax(0.25 * tol * bn, rtol * bt);
     converged[l] = done ? 1 : 0;
     active[l] = done ? 0 : 1;
     if (!done) atomicAdd(&counters[0], 1);

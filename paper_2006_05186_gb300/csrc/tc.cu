@@ -12,11 +12,11 @@
 // the FP64-accurate residual is computed apart).
 //
 // One CTA per work item.  Each K-slab covers 16 Chebyshev indices nu (their
-// real and imaginary parts: 32 real-form K).  Warp 9 runs ahead and copies
+// real and imaginary parts: 32 real-form K).  Warp 13 runs ahead and copies
 // each slab's 16 x 64 block of C (stored nu-major, 8 KB contiguous) into a
 // ring of 8 staging buffers with bulk asynchronous copies; warps 1-4 build the
 // slab's A (the real form of C) from there row by row straight into tensor
-// memory, one TMEM lane per row; warps 5-8 build B = x~ in shared memory in
+// memory, one TMEM lane per row; warps 5-12 build B = x~ in shared memory in
 // the canonical K-major layout, with the d_t values loaded three slabs ahead.
 // A ring of 4 slabs is guarded by mbarriers; one thread of warp 0 issues
 // 4 x 3 MMAs per slab (A from TMEM, B from shared memory) and frees the slab
@@ -38,8 +38,8 @@ constexpr int NSTAGE = 4;       // slabs in the MMA ring
 constexpr int NCS = 8;          // C staging buffers (8 KB each)
 constexpr uint32_t CSLAB = 16u * TP * 8u;  // bytes of one slab of C: 16 nu x 64 mu complex fp32
 constexpr int NA = 128;         // A producer threads (warps 1..4): one TMEM lane (row) each
-constexpr int NBP = 128;        // B producer threads (warps 5..8)
-constexpr int LOADER = 9;       // warp that issues the C copies
+constexpr int NBP = 256;        // B producer threads (warps 5..12)
+constexpr int LOADER = 13;      // warp that issues the C copies
 constexpr int NTHREADS = 32 * (LOADER + 1);
 constexpr uint32_t TCOLS = 512;       // TMEM columns: accumulator [0, 256), A ring [256, 512)
 constexpr uint32_t ACOL = 256;        // first column of the A ring; 64 per slab (hi 32, lo 32)
