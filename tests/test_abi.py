@@ -54,6 +54,7 @@ def test_strerror_and_defaults(lib):
     p = _lib.default_params()
     assert p.mode == _lib.MODE_H2MACA and p.n_min == 32 and p.eta == 1.0 and p.cheb_m == 4
     assert p.tensor_cores == 1 and p.inner_fp32 == 1 and p.rank_cap == 32
+    assert p.exact_ff == 1 and p.expand_near == 1 and p.expand_far == 1
     assert p.aca_eps == 1e-6 and p.g_sing == 5 and p.gmres_tol == 1e-13
     assert lib.cqm_params_default(None) == _lib.CQM_EINVAL
 

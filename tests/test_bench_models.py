@@ -1,0 +1,50 @@
+"""Host logic of the benchmark's roofline reporting: the algorithmic work per
+launch of each modelled kernel and the achieved rate derived from the live
+launch timings (no GPU)."""
+import importlib.util
+import os
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def bench():
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+INFO = dict(rank_sum_far=1000, near_rank_entries=50000, near_entries=8000, far_coupling=20 * 4096)
+
+
+def test_factored_models_count_complex_macs(bench):
+    m = bench.kernel_models(dict(INFO, near_expanded=0, far_expanded=0), Ls=129, p=64, tensor_cores=0)
+    assert m["far_coupling"]["work"] == 8.0 * 1000 * 64 * 64 * 129
+    assert m["near_apply"]["work"] == 8.0 * 50000 * 129
+    # float-float: 48 FP32 instructions per complex multiply-add, 2 flops each
+    assert m["far_exact"]["work"] == 2.0 * 48 * 1000 * 64 * 64 * 129
+    assert all(v["bound"] == "alu" and v["unit"] == "TFLOP/s" for v in m.values())
+
+
+def test_tensor_and_expanded_models(bench):
+    m = bench.kernel_models(dict(INFO, near_expanded=1, far_expanded=1), Ls=129, p=64, tensor_cores=1)
+    assert m["far_coupling"]["bound"] == "tensor"
+    peak, _ = bench.tf32_peak()
+    assert m["far_coupling"]["peak"] == pytest.approx(peak)
+    assert m["near_apply"]["bound"] == "hbm" and m["near_apply"]["work"] == 8.0 * 8000 * 129
+    assert m["near_exact"]["work"] == 16.0 * 8000 * 129
+    assert m["far_exact"]["bound"] == "hbm" and m["far_exact"]["work"] == 16.0 * 20 * 4096 * 129
+
+
+def test_roofline_entry_rates(bench):
+    mdl = dict(bound="hbm", peak=8000.0, unit="GB/s", work=4.0e9, what="", peak_source="")
+    r = bench.roofline_entry("k", 4, 8.0, mdl)  # 4 launches, 8 ms in total: 2 ms each
+    assert r["ms_per_launch"] == pytest.approx(2.0)
+    assert r["achieved"] == pytest.approx(4.0e9 / 2e-3 / 1e9)
+    assert r["frac"] == pytest.approx(r["achieved"] / 8000.0)
+    mdl = dict(bound="alu", peak=80.0, unit="TFLOP/s", work=1.0e12, what="", peak_source="")
+    r = bench.roofline_entry("k", 10, 100.0, mdl)
+    assert r["achieved"] == pytest.approx(1.0e12 / 1e-2 / 1e12)
