@@ -58,6 +58,17 @@ FP32_PEAK_SOURCE = "unit counts x max SM clock (152 SMs x 128 FP32 lanes x 2 x 2
 TF32_OVER_BF16 = 1.1 / 2.25
 
 
+# DRAM bytes (read + write) of one launch of the tensor-core coupling per far
+# rank term, from the ncu capture of that kernel (commit 8b60da1) on the
+# 1280-triangle sphere with N = 64: 351.6 MB read + 8.2 MB written for 10586
+# rank terms.  The traffic is the FP32 coupling factors read once (32 KB per
+# rank term) plus the small d_t, xhat and partial-tile terms, so it grows with
+# the rank terms; the bench scales it to the workload's rank-term count.
+TC_DRAM_BYTES_PER_RANK_TERM = (351.601152e6 + 8.199936e6) / 10586
+TC_DRAM_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of k_far_coupling_tc (commit 8b60da1, "
+                  "1280-triangle sphere, N = 64), scaled by far rank terms")
+
+
 def tf32_peak():
     pk, src = _peaks()
     bf16 = pk.get("bf16_tflops_sustained", pk["bf16_tflops"])
@@ -174,7 +185,9 @@ def kernel_models(info, Ls, p, tensor_cores):
         peak, src = tf32_peak()
         models["far_coupling"] = dict(
             bound="tensor", peak=peak, peak_source=src, unit="TFLOP/s", work=8.0 * cmac_far,
-            what="complex MAC on tcgen05 TF32 (useful flops; the 3-product split executes 3x)")
+            what="complex MAC on tcgen05 TF32 (useful flops; the 3-product split executes 3x)",
+            traffic=TC_DRAM_BYTES_PER_RANK_TERM * info["rank_sum_far"],
+            traffic_source=TC_DRAM_SOURCE)
     pk, src = _peaks()
     hbm = dict(bound="hbm", peak=pk["hbm_gbs"], unit="GB/s",
                peak_source=f"{src} STREAM-style copy, MEASURED_PEAKS.json hbm_gbs")
@@ -202,9 +215,13 @@ def roofline_of(prof, models):
 def roofline_entry(name, n, ms, mdl):
     scale = 1e9 if mdl["unit"] == "GB/s" else 1e12
     achieved = mdl["work"] / (ms / n / 1e3) / scale
-    return {"bound": mdl["bound"], "kernel": name, "what": mdl["what"], "achieved": achieved,
-            "peak": mdl["peak"], "unit": mdl["unit"], "frac": achieved / mdl["peak"], "traffic": None,
-            "launches": n, "ms_per_launch": ms / n, "peak_source": mdl["peak_source"]}
+    out = {"bound": mdl["bound"], "kernel": name, "what": mdl["what"], "achieved": achieved,
+           "peak": mdl["peak"], "unit": mdl["unit"], "frac": achieved / mdl["peak"],
+           "traffic": mdl.get("traffic"), "launches": n, "ms_per_launch": ms / n,
+           "peak_source": mdl["peak_source"]}
+    if mdl.get("traffic_source"):
+        out["traffic_source"] = mdl["traffic_source"]
+    return out
 
 
 def run_ours(args):
