@@ -343,19 +343,21 @@ __global__ void __launch_bounds__(256) k_far_expand_ff(int Ls, int p, int cap, c
   }
   __syncthreads();
   const int pp = p * p;
+  // thread e -> (nu, mu) with mu fastest: consecutive threads write consecutive
+  // entries of the column-major table
   for (int e = threadIdx.x; e < pp; e += blockDim.x) {
-    const int mu = e / p, nu = e - mu * p;
+    const int nu = e / p, mu = e - nu * p;
     ffc acc[FAR_NF];
 #pragma unroll
     for (int f = 0; f < FAR_NF; ++f) acc[f] = ffc_zero();
     for (int tt = 0; tt < rk; ++tt) {
-      const ffc c = Cf[((size_t)b * cap + tt) * pp + e];
+      const ffc c = Cf[((size_t)b * cap + tt) * pp + (size_t)mu * p + nu];
 #pragma unroll
       for (int f = 0; f < FAR_NF; ++f) ffc_mac(acc[f], c, Ds[tt][f]);
     }
     for (int f = 0; f < nf; ++f) {
       ffc_renorm(acc[f]);
-      S[((size_t)b * Ls + l0 + f) * pp + (size_t)nu * p + mu] = acc[f];
+      S[((size_t)b * Ls + l0 + f) * pp + e] = acc[f];
     }
   }
 }
@@ -464,13 +466,15 @@ __global__ void __launch_bounds__(256) k_near_expand_ff(int Ls, int cap, const i
     Ds[tt][f] = f < nf ? ffc_from(D[((size_t)b * cap + tt) * Ls + l0 + f]) : ffc_zero();
   }
   __syncthreads();
+  // thread e -> (j, i) with i fastest: consecutive threads write consecutive
+  // entries of the column-major table
   for (int e = threadIdx.x; e < nr * nc; e += blockDim.x) {
-    const int i = e / nc, j = e - i * nc;
+    const int j = e / nr, i = e - j * nr;
     ffc acc[FAR_NF];
 #pragma unroll
     for (int f = 0; f < FAR_NF; ++f) acc[f] = ffc_zero();
     for (int tt = 0; tt < rk; ++tt) {
-      const ffc c = C[coff[b] + (size_t)tt * nr * nc + e];
+      const ffc c = C[coff[b] + (size_t)tt * nr * nc + (size_t)i * nc + j];
 #pragma unroll
       for (int f = 0; f < FAR_NF; ++f) ffc_mac(acc[f], c, Ds[tt][f]);
     }
