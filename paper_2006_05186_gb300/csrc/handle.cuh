@@ -82,10 +82,11 @@ struct cqm_handle {
 
   // FP32 copy of the operator (inner iterations of mixed precision)
   bool use_f32 = false;
-  bool factors_ff = false;
+  bool factors_ff = false;  // nearC / farC hold float-float pairs (hi re, hi im, lo re, lo im)
   bool farC_f_transposed = false;  // farC_f tiles stored nu-major (tensor-core coupling)
   // expanded near field: block b, frequency l, entry (i, j) at
-  // nearV_off[b] + (l #c + j) #r + i (FP64 and an FP32 copy)
+  // nearV_off[b] + (l #c + j) #r + i; nearV holds FP64 values, or float-float
+  // pairs when nearV_ff, and nearV_f their FP32 values
   bool near_expanded = false;
   bool nearV_ff = false;  // nearV holds float-float pairs (expanded after factors_to_ff)
   cqm::DArray<double2> nearV;
@@ -95,7 +96,7 @@ struct cqm_handle {
   // expanded far couplings (float-float pairs) for the FP64-accurate apply:
   // block b, frequency l, entry (mu, nu) at (b Ls + l) p^2 + nu p + mu
   bool far_expanded = false;
-  cqm::DArray<double2> farS;  // nearC / farC hold float-float pairs (hi re, hi im, lo re, lo im)
+  cqm::DArray<double2> farS;
   cqm::DArray<float2> nearC_f, nearD_f, farC_f, farD_f, xhat_f, yhat_f;
   cqm::DArray<float> Uleaf_f, Etr_f;
 
