@@ -1,6 +1,9 @@
-// FP32 contractions of the inner operator (mixed-precision GMRES), register
-// tiled: one block covers a row cluster and up to 32 * NLT frequencies, so a
-// stored factor C_{b,t} is read once per apply; every thread keeps a tile of
+// FP32 SIMT contractions of the inner operator (mixed-precision GMRES) from
+// the factors: the far coupling with tensor_cores = 0 (or m < 4, through the
+// generic kernel) and the near field with expand_near = 0.  Register tiled:
+// one block covers a work item (a row cluster and a run of its blocks) and up
+// to 32 * NLT frequencies, so a stored factor C_{b,t} is read once per apply;
+// the items' partial tiles are summed per row in item order.  Every thread keeps a tile of
 // rows x NLT frequencies of complex accumulators, and d_t[l] is folded into
 // the staged x_c (yhat[mu][l] += sum_nu C_t[mu][nu] (d_t[l] xhat[nu][l])),
 // which is eq. lrfinal applied to all frequencies at once.

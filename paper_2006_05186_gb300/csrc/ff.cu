@@ -5,8 +5,11 @@
 // sums Knuth's error-free TwoSum, which together keep about 48 significant
 // bits.  The near-field and far-field coupling contractions (the bulk of the
 // flops of eq. lrfinal) run this way; the H^2 transforms, which are cheap,
-// stay in FP64.  Inputs and outputs are FP64; the factors are read from their
-// FP64 storage and split while they are staged in shared memory.
+// stay in FP64.  Inputs and outputs are FP64.  The C factors are converted to
+// float-float pairs once at setup (factors_to_ff).  This file also forms the
+// expanded near field and far couplings in float-float (V_l = sum_t C_t d_t(l)
+// per block and frequency) and streams them in the FP64-accurate apply; the
+// factored contractions remain for tables that are not expanded.
 #include <algorithm>
 #include <vector>
 

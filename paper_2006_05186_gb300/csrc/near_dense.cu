@@ -1,6 +1,8 @@
 // Expanded near field: after the MACA of the near blocks (Alg. 3, NEAR), every
 // near block is expanded per solved frequency, V_l[i][j] = sum_t C_t[i][j] d_t[l]
-// (eq. lrfinal), in FP64, and kept with an FP32 copy.  This is the same
+// (eq. lrfinal), with an FP32 copy.  This file holds the FP64 expansion and
+// apply (used without exact_ff) and the FP32 apply of the inner operator; with
+// exact_ff the table is formed and applied in float-float (ff.cu).  This is the same
 // operator as the factored form (up to rounding); the applies then stream it
 // once per product instead of recontracting every rank term, which on this
 // GPU turns a compute-bound contraction into an HBM-bound one with Ls / rank
