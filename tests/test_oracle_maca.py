@@ -67,3 +67,32 @@ def test_T7_coupling_tensor_geometric_decay_and_tolerance():
         assert e < 30 * eps, (eps, e)
     ranks = [x[0] for x in errs]
     assert ranks == sorted(ranks) and ranks[-1] < Gt.shape[2]
+
+
+def test_maca_of_transposed_block_is_a_transposed_approximation():
+    """Reading of the symmetric MACA: a block (c, r) of the symmetric single
+    layer is the transpose of (r, c) at every frequency, and Alg. 2 run on the
+    transposed tensor meets the same tolerance with the same rank (up to
+    one); the transposed approximation of (r, c) is therefore as good an
+    approximation of (c, r) as the one Alg. 2 computes for it."""
+    from oracle import galerkin as G
+    from paper_2006_05186_gb300 import synth
+    m = synth.icosphere(2)
+    t = cluster.build_tree(m.xyz, m.tri, 16)
+    near, _ = cluster.partition(t, 1.0)
+    r, c = next((r, c) for r, c in near if r != c)
+    N, eps = 32, 1e-8
+    s = cqm.frequencies(N, 0.1, 2)[: cqm.n_solved(N + 1)]
+    ir, ic = t.indices(r), t.indices(c)
+    I, J = np.meshgrid(ir, ic, indexing="ij")
+    Gt = G.pair_entries(m.xyz, m.tri, I.ravel(), J.ravel(), s).reshape(len(ir), len(ic), -1)
+    Gtt = np.transpose(Gt, (1, 0, 2))
+    I2, J2 = np.meshgrid(ic, ir, indexing="ij")
+    assert np.array_equal(G.pair_entries(m.xyz, m.tri, I2.ravel(), J2.ravel(), s).reshape(Gtt.shape), Gtt)
+    C, D, info = maca.maca(lambda k: Gt[:, :, k], lambda i, j: Gt[i, j, :], len(s), eps)
+    Ct, Dt, info_t = maca.maca(lambda k: Gtt[:, :, k], lambda i, j: Gtt[i, j, :], len(s), eps)
+    assert abs(info["rank"] - info_t["rank"]) <= 1
+    mirrored = np.transpose(maca.reconstruct(C, D), (1, 0, 2))
+    nrm = np.linalg.norm(Gtt)
+    assert np.linalg.norm(mirrored - Gtt) <= 20 * eps * nrm
+    assert np.linalg.norm(maca.reconstruct(Ct, Dt) - Gtt) <= 20 * eps * nrm
