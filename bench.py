@@ -337,7 +337,7 @@ def run_ours(args):
     }
     if args.dense_baseline:
         line["dense_fp64_gpu"] = dense_baseline(m, pulse, W, q)
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and world == 1:  # rank 0 at N = 1 only
         line["cpu_baseline"] = cpu_baseline(max_seconds=args.cpu_seconds)
     print(json.dumps(line), flush=True)
 
