@@ -256,7 +256,7 @@ int cqm_bem_inverse_transform(cqm_handle* h, const double* qhat, double* q, int3
 #define CQM_K_GEOMETRY       0
 #define CQM_K_TREE           1
 #define CQM_K_PARTITION      2
-#define CQM_K_BASES          3
+#define CQM_K_BASES          3    /* cluster bases, FP32 and float-float factor copies, expanded tables */
 #define CQM_K_DENSE_ASSEMBLE 4
 #define CQM_K_ENTRIES        5
 #define CQM_K_MACA_SLICE     6
