@@ -212,6 +212,18 @@ def roofline_of(prof, models):
     return roofline_entry(name, n, ms, models[name])
 
 
+def time_weighted_frac(prof, models):
+    """Fraction of peak of the modelled contraction kernels, each weighted by
+    its share of their summed device time (live CUDA-event timings)."""
+    parts = [(prof[k][1], roofline_entry(k, prof[k][0], prof[k][1], models[k])["frac"])
+             for k in models if k in prof and prof[k][0]]
+    total = sum(ms for ms, _ in parts)
+    if total <= 0:
+        return None
+    return {"frac": sum(ms * f for ms, f in parts) / total, "kernels": [k for k in models if k in prof and prof[k][0]],
+            "ms": total}
+
+
 def roofline_entry(name, n, ms, mdl):
     scale = 1e9 if mdl["unit"] == "GB/s" else 1e12
     achieved = mdl["work"] / (ms / n / 1e3) / scale
@@ -321,6 +333,7 @@ def run_ours(args):
                      "converged_frequencies": min(s["converged"] for s in sinfos), "Ls": Ls},
         "roofline": roofline_of(prof, models),
         "roofline_all": {k: roofline_of({k: prof[k]}, models) for k in models if k in prof and prof[k][0]},
+        "roofline_time_weighted": time_weighted_frac(prof, models),
         "dominant_kernel": {"name": dom[0], "launches": dom[1][0], "ms": dom[1][1]},
         "kernel_ms": {k: round(v[1], 3) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1]) if v[0]},
         "gpu_launches": int(sum(v[0] for v in prof.values())),

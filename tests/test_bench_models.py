@@ -48,3 +48,14 @@ def test_roofline_entry_rates(bench):
     mdl = dict(bound="alu", peak=80.0, unit="TFLOP/s", work=1.0e12, what="", peak_source="")
     r = bench.roofline_entry("k", 10, 100.0, mdl)
     assert r["achieved"] == pytest.approx(1.0e12 / 1e-2 / 1e12)
+
+
+def test_time_weighted_fraction(bench):
+    models = {"a": dict(bound="hbm", peak=100.0, unit="GB/s", work=1.0e9, what="", peak_source=""),
+              "b": dict(bound="alu", peak=10.0, unit="TFLOP/s", work=1.0e12, what="", peak_source="")}
+    prof = {"a": (10, 100.0), "b": (1, 300.0), "c": (5, 1.0)}
+    fa = bench.roofline_entry("a", 10, 100.0, models["a"])["frac"]
+    fb = bench.roofline_entry("b", 1, 300.0, models["b"])["frac"]
+    tw = bench.time_weighted_frac(prof, models)
+    assert tw["frac"] == pytest.approx((100.0 * fa + 300.0 * fb) / 400.0)
+    assert tw["ms"] == pytest.approx(400.0) and tw["kernels"] == ["a", "b"]
