@@ -25,6 +25,8 @@ based on Hierarchical Matrices and Adaptive Cross Approximation") step by step:
 * ``h2``         -- Chebyshev interpolation bases (eqs. degexp, uniformlr; Def. 5)
                     and the H^2-expanded matrices V_l.
 * ``maca``       -- multivariate adaptive cross approximation (Sec. 5.1, Alg. 2).
+* ``mot``        -- marching on in time with the CQM weights (Sec. 3.2, eq. dft),
+                    the paper's own time stepping (not on the GPU path yet).
 
 Parity pins: every module is checked in ``tests/test_oracle_*.py`` against
 closed forms, invariants or brute force.  The conventions the paper leaves
