@@ -131,8 +131,8 @@ def pair_entries(xyz, tri, I, J, s, qp: QuadParams = QuadParams(), chunk: int = 
         ww = (wts[:, None] * wts[None, :]).ravel()
         for k0 in range(0, len(idx), chunk):
             kk = idx[k0:k0 + chunk]
-            X = np.einsum("qa,pad->pqd", bary, P[I[kk]])
-            Y = np.einsum("qa,pad->pqd", bary, P[J[kk]])
+            X = bary @ P[I[kk]]   # (pairs, points, xyz): sum_a bary[q, a] P[p, a]
+            Y = bary @ P[J[kk]]
             r = np.linalg.norm(X[:, :, None, :] - Y[:, None, :, :], axis=3).reshape(len(kk), -1)
             w = (area[I[kk]] * area[J[kk]])[:, None] * ww[None, :]
             out[kk] = _kernel_sum(r, w, s)
@@ -154,8 +154,8 @@ def pair_entries(xyz, tri, I, J, s, qp: QuadParams = QuadParams(), chunk: int = 
                 vx, vy = _ordered_vertices(tri, I[k], J[k], c)
                 Px[t] = xyz[vx]
                 Py[t] = xyz[vy]
-            X = np.einsum("qa,pad->pqd", bx, Px)
-            Y = np.einsum("qa,pad->pqd", by, Py)
+            X = bx @ Px
+            Y = by @ Py
             r = np.linalg.norm(X - Y, axis=2)
             w = (4.0 * area[I[kk]] * area[J[kk]])[:, None] * wr[None, :]
             out[kk] = _kernel_sum(r, w, s)

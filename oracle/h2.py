@@ -118,6 +118,6 @@ def h2_matrices(xyz, tri, s, tree: ClusterTree, near, far, m: int,
 
     for r, c in far:
         S = coupling(tree, r, c, s, m)
-        blk = np.einsum("im,lmn,jn->lij", U(r), S, U(c))
+        blk = (U(r) @ S) @ U(c).T   # U_r S_b(s_l) U_c^T for every l (eq. uniformlr)
         out[:, tree.indices(r)[:, None], tree.indices(c)[None, :]] = blk
     return out

@@ -66,3 +66,39 @@ def test_rhs_plane_wave_smooth_data():
     assert np.all(np.abs(b[0]) <= np.exp(-16) * area * 1.0001)
     assert np.all(b <= area[None, :] * (1 + 1e-12))
     assert np.max(b / area[None, :]) > 0.5
+
+
+def _arrival_steps(b, dt):
+    """Peak time of each element's data b_n[i], refined by the parabola through
+    the largest sample and its two neighbours."""
+    n = np.argmax(b, axis=0)
+    n = np.clip(n, 1, b.shape[0] - 2)
+    i = np.arange(b.shape[1])
+    y0, y1, y2 = b[n - 1, i], b[n, i], b[n + 1, i]
+    return (n + 0.5 * (y0 - y2) / (y0 - 2.0 * y1 + y2)) * dt
+
+
+def test_rhs_plane_wave_arrival_follows_direction():
+    """The pulse u(x, t) = exp(-((t - delay - d.x)/w)^2) reaches x at
+    t = delay + d.x: each element's data peaks at delay + d.c_i (c_i the
+    centroid; the 7-point rule integrates the linear d.x exactly, and the
+    pulse is wide against the element), so for d = +z the elements at z = -1
+    peak 2/dt steps before those at z = +1.  Reversing the sign of d.x in the
+    oracle (planted here as the opposite direction) fails the check."""
+    m = synth.icosphere(2)
+    p = synth.plane_wave_pulse(width=0.5)
+    N, dt = 300, 0.02
+    _, _, cen, _ = G.element_geometry(m.xyz, m.tri)
+    expect = p.delay + cen @ p.direction
+    for d, ok in ((p.direction, True), (-p.direction, False)):
+        b = incident.rhs_plane_wave(m.xyz, m.tri, N, dt, d, p.width, p.delay)
+        t_peak = _arrival_steps(b, dt)
+        err = np.max(np.abs(t_peak - expect))
+        # element size (h ~ 0.2) and the sampling refine to well below dt
+        assert (err < 0.25 * dt) == ok, (ok, err)
+    b = incident.rhs_plane_wave(m.xyz, m.tri, N, dt, p.direction, p.width, p.delay)
+    t_peak = _arrival_steps(b, dt)
+    south, north = cen[:, 2] < -0.9, cen[:, 2] > 0.9
+    lead = np.mean(t_peak[north]) - np.mean(t_peak[south])
+    assert abs(lead - (np.mean(cen[north, 2]) - np.mean(cen[south, 2]))) < 0.05 * dt
+    assert lead > 1.8

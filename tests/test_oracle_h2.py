@@ -3,7 +3,7 @@ polynomial reproduction, nestedness, error decay in the order m."""
 import numpy as np
 import pytest
 
-from oracle import cluster, galerkin as G, h2, quadrature as Q
+from oracle import cluster, cqm, galerkin as G, h2, quadrature as Q
 from paper_2006_05186_gb300 import synth
 
 
@@ -96,3 +96,21 @@ def test_h2_expanded_matches_dense_on_near_field_and_approximates_far():
     assert np.array_equal(Vh[mask], Vd[mask])
     rel = np.linalg.norm(Vh - Vd) / np.linalg.norm(Vd)
     assert 0 < rel < 1e-2
+
+
+def test_pool_assembly_equals_serial():
+    """The process-pool evaluation of the H^2-expanded matrices is the serial
+    oracle bit for bit (it only evaluates independent pairs and blocks in
+    different processes), and its per-frequency LU solve is LAPACK's."""
+    from oracle import pool
+    m = synth.icosphere(2)
+    t = cluster.build_tree(m.xyz, m.tri, 32)
+    near, far = cluster.partition(t, 1.0)
+    s = cqm.frequencies(16, 0.1, 2)[[0, 5]]
+    V = h2.h2_matrices(m.xyz, m.tri, s, t, near, far, 4)
+    Vp = pool.h2_matrices(m.xyz, m.tri, s, t, near, far, 4, workers=3)
+    assert np.array_equal(V, Vp)
+    g = np.random.default_rng(2).standard_normal((2, m.nt)) + 0j
+    q = pool.h2_solve_frequencies(m.xyz, m.tri, s, t, near, far, 4, g, workers=2)
+    for k in range(2):
+        assert np.allclose(V[k] @ q[k], g[k], rtol=0, atol=1e-12 * np.abs(g[k]).max())
