@@ -6,14 +6,17 @@ of one full pass of the hot path -- geometry, cluster tree, partition,
 Chebyshev bases, MACA of every block, plane-wave data, forward R-scaled DFT,
 batched GMRES over the solved frequencies, inverse DFT -- on the 5120-triangle
 unit sphere, BDF2, N = 256, dt = 0.1, eta = 1, m = 4, leaf 32, MACA tolerance
-1e-6, FP64.  Synthetic input: seeded icosphere and Gaussian plane-wave pulse.
+1e-7.  Arithmetic: tf32x3 tensor-core far coupling and fp32 near field in the
+inner GMRES iterations, float-float residual applies, fp64 MACA, transforms and
+Krylov basis; the result meets the FP64 residual target.  Synthetic input:
+seeded icosphere and Gaussian plane-wave pulse.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 N > 1 runs one independent replica per GPU (the method does not shard across
 GPUs here); value = all ranks' units / max over ranks of the timed region.
 --impl reference times the FP64 CPU oracle on a bounded sample of the same
-workload on the host cores (rank 0 only).
+workload (3 of its solved frequencies) on all host cores (rank 0 only).
 """
 from __future__ import annotations
 
@@ -74,6 +77,33 @@ def tf32_peak():
     bf16 = pk.get("bf16_tflops_sustained", pk["bf16_tflops"])
     return bf16 * TF32_OVER_BF16, (f"{src} bf16 cuBLAS {bf16:.1f} TFLOP/s (sustained) x nominal "
                                    f"tf32/bf16 ratio 1.1/2.25")
+
+
+def measure_tf32_peak():
+    """Dense TF32 tensor rate of this GPU: cuBLAS fp32 GEMM with TF32 math,
+    8192^3 (2 n^3 flops), best of 10 after warm-up, CUDA events."""
+    import torch
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = True
+    try:
+        n = 8192
+        a = torch.randn(n, n, device="cuda")
+        b = torch.randn(n, n, device="cuda")
+        for _ in range(3):
+            torch.matmul(a, b)
+        best = float("inf")
+        for _ in range(10):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, b)
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1) / 1e3)
+        del a, b
+        torch.cuda.empty_cache()
+        return 2.0 * n ** 3 / best / 1e12
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
 
 
 def dist_init(ngpus):
@@ -160,7 +190,7 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
-def kernel_models(info, Ls, p, tensor_cores):
+def kernel_models(info, Ls, p, tensor_cores, tf32=None):
     """Algorithmic work per launch of the contraction kernels and the peak
     that bounds each.  Complex multiply-add = 8 flops.  Factored forms:
     coupling sum_far rank * p^2 * Ls, near field sum_near rank * #r#c * Ls
@@ -182,7 +212,8 @@ def kernel_models(info, Ls, p, tensor_cores):
         "near_exact": dict(fp32, work=2.0 * 48 * cmac_near, what="float-float complex MAC (FP32 issue)"),
     }
     if tensor_cores and p == 64:
-        peak, src = tf32_peak()
+        peak, src = tf32_peak() if tf32 is None else (
+            tf32, "measured here: cuBLAS TF32 GEMM 8192^3 (torch.matmul, allow_tf32), best of 10")
         models["far_coupling"] = dict(
             bound="tensor", peak=peak, peak_source=src, unit="TFLOP/s", work=8.0 * cmac_far,
             what="complex MAC on tcgen05 TF32 (useful flops; the 3-product split executes 3x)",
@@ -308,19 +339,31 @@ def run_ours(args):
     e2e_value = (whole_job_value(M * L, len(e2e_times), sum(e2e_times), world)[0]
                  if e2e_times else None)
 
+    # the workload's per-frequency solution, for the oracle comparison (untimed)
+    qhat_gpu = None
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        op = CqmBem(m.xyz, m.tri, dt, N, W["bdf"], **params)
+        g = op.forward_transform(rhs)
+        qhat_gpu = op.solve_frequencies(g)[0].cpu().numpy()
+        op.close()
+    tf32_measured = measure_tf32_peak() if rank == 0 else None
     if rank != 0:
         return
     peaks, src = _peaks()
     inf = infos[-1]
     dom = max(prof.items(), key=lambda kv: kv[1][1])
     p = W["cheb_m"] ** 3
-    models = kernel_models(inf, Ls, p, inf["tensor_cores"])
+    models = kernel_models(inf, Ls, p, inf["tensor_cores"], tf32_measured)
     lat = sorted(times)
     clocks = clk.summary()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": ("mixed: tf32x3 tensor-core far coupling and fp32 near field in the inner GMRES "
+                  "iterations, float-float (~48-bit) residual applies, fp64 MACA, DFTs, "
+                  "preconditioner and Krylov basis"),
+        "data": "synthetic",
         "config": {"workload": W["name"], "triangles": M, "N": N, "L": L, "Ls": Ls, "dt": dt,
                    "bdf": 2, "eta": W["eta"], "cheb_m": W["cheb_m"], "leaf": W["n_min"],
                    "aca_eps": W["aca_eps"], "mode": "h2maca", "parallelism": f"replicas{world}",
@@ -348,10 +391,19 @@ def run_ours(args):
                 "d2h_bytes_per_step": int(L * M * 8)},
         "peaks_source": src,
     }
+    line["roofline_peaks"] = {"tf32_tflops": tf32_measured}
     if args.dense_baseline:
         line["dense_fp64_gpu"] = dense_baseline(m, pulse, W, q)
     if not args.no_cpu_baseline and world == 1:  # rank 0 at N = 1 only
-        line["cpu_baseline"] = cpu_baseline(max_seconds=args.cpu_seconds)
+        cb, qref = cpu_baseline()
+        line["cpu_baseline"] = cb
+        errs = {int(l): float(np.max(np.abs(qhat_gpu[l] - ref)) / np.max(np.abs(ref)))
+                for l, ref in qref.items()}
+        line["accuracy"]["rel_err_vs_oracle"] = max(errs.values())
+        line["accuracy"]["rel_err_vs_oracle_per_frequency"] = errs
+        line["accuracy"]["oracle_note"] = (
+            "max_i |qhat_l[i] - ref_l[i]| / max_i |ref_l[i]| at the sampled solved frequencies, "
+            "ref = LU of the FP64 oracle's H^2-expanded V_l (same tree and interpolation, no MACA)")
     print(json.dumps(line), flush=True)
 
 
@@ -384,61 +436,52 @@ def dense_baseline(m, pulse, W, q_compressed):
             "note": "one pass, no warm-up; the difference is the H^2 interpolation error (eta = 1, m = 4)"}
 
 
-def cpu_baseline(max_seconds=20.0):
-    """The FP64 oracle as it stands on a bounded sample of the same workload:
-    H^2-expanded Galerkin assembly of a random sample of the near-field pairs
-    and of the far blocks at one frequency, plus one dense LU solve, scaled to
-    all pairs and all solved frequencies."""
-    from oracle import cluster, cqm, galerkin as G, h2
+def oracle_frequencies(freqs, workers=None):
+    """The FP64 oracle as it stands on solved frequencies `freqs` of the
+    benchmark workload: cluster tree and partition, plane-wave data and its
+    R-scaled transform, H^2-expanded assembly of V_l (every near-field pair by
+    its quadrature rule, every far block as U_r S_b U_c^T) and one LAPACK LU
+    per frequency, evaluated over a process pool on the host cores.
+    Returns (qhat (len(freqs), M), seconds, workers)."""
+    from oracle import cluster, cqm, incident, pool
     from paper_2006_05186_gb300 import synth
     W = WORKLOAD
+    workers = workers or pool.default_workers()
     m = synth.icosphere(W["level"])
-    M = m.nt
-    N = W["N"]
-    L = N + 1
-    Ls = L // 2 + 1
+    p = synth.plane_wave_pulse()
+    t0 = time.perf_counter()
     t = cluster.build_tree(m.xyz, m.tri, W["n_min"])
     near, far = cluster.partition(t, W["eta"])
-    s = cqm.frequencies(N, W["dt"], 2)[[Ls // 2]]
-    sizes = t.end - t.begin
-    n_pairs = int(sum(sizes[r] * sizes[c] for r, c in near))
-    rng = np.random.default_rng(0)
-    I, J = [], []
-    for r, c in near:
-        a, b = np.meshgrid(t.indices(r), t.indices(c), indexing="ij")
-        I.append(a.ravel())
-        J.append(b.ravel())
-    I = np.concatenate(I)
-    J = np.concatenate(J)
-    budget = max_seconds / 3
-    k = 2048
-    t0 = time.perf_counter()
-    sel = rng.choice(n_pairs, k, replace=False)
-    G.pair_entries(m.xyz, m.tri, I[sel], J[sel], s)
-    t_near = (time.perf_counter() - t0) * n_pairs / k
-    fb = far[rng.choice(len(far), 64, replace=False)]
-    t0 = time.perf_counter()
-    cache = {}
-    for r, c in fb:
-        S = h2.coupling(t, r, c, s, W["cheb_m"])
-        for x in (r, c):
-            if x not in cache:
-                cache[x] = h2.cluster_basis(m.xyz, m.tri, t, x, W["cheb_m"])
-        np.einsum("im,lmn,jn->lij", cache[r], S, cache[c])
-    t_far = (time.perf_counter() - t0) * len(far) / len(fb)
-    A = rng.standard_normal((M, M)) + 1j * rng.standard_normal((M, M))
-    bvec = rng.standard_normal(M) + 0j
-    t0 = time.perf_counter()
-    np.linalg.solve(A, bvec)
-    t_lu = time.perf_counter() - t0
-    per_freq = t_near + t_far + t_lu
-    est = Ls * per_freq
-    return {"value": M * L / est, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-            "sample": (f"one frequency of the {W['name']} workload: {k} of {n_pairs} near-field "
-                       f"pairs and 64 of {len(far)} far blocks (H^2-expanded assembly) plus one "
-                       f"{M}x{M} LU; scaled to all pairs and {Ls} solved frequencies; est. "
-                       f"{est:.0f} s per job; the assembly runs on one thread (numpy), the LU "
-                       f"on the BLAS threads (up to cores)")}
+    b = incident.rhs_plane_wave(m.xyz, m.tri, W["N"], W["dt"], p.direction, p.width, p.delay)
+    g = cqm.forward(b, cqm.default_R(W["N"]))[freqs]
+    s = cqm.frequencies(W["N"], W["dt"], W["bdf"])[freqs]
+    q = pool.h2_solve_frequencies(m.xyz, m.tri, s, t, near, far, W["cheb_m"], g, workers=workers)
+    return q, time.perf_counter() - t0, workers
+
+
+def cpu_baseline():
+    """The oracle on a bounded sample of the workload: one run on the middle
+    solved frequency and one on the first and last, each timed whole.  The
+    job time a + b Ls is fitted from the two runs (a: tree, data and set-up
+    shared by all frequencies; b: assembly and LU of one frequency).  Also
+    returns the oracle's qhat at the three frequencies."""
+    W = WORKLOAD
+    L = W["N"] + 1
+    Ls = L // 2 + 1
+    M = 20 * 4 ** W["level"]
+    f1, f2 = [Ls // 2], [0, Ls - 1]
+    q1, t1, workers = oracle_frequencies(f1)
+    q2, t2, _ = oracle_frequencies(f2)
+    b = t2 - t1 if t2 > t1 else t1
+    a = max(0.0, t1 - b)
+    est = a + b * Ls
+    qref = {f1[0]: q1[0], f2[0]: q2[0], f2[1]: q2[1]}
+    return {"value": M * L / est, "unit": UNIT, "cores": workers, "kind": "oracle",
+            "sample": (f"the {W['name']} workload on 3 of its {Ls} solved frequencies (l = {f2[0]}, "
+                       f"{f1[0]}, {f2[1]}) in two timed runs ({t1:.1f} s for one frequency, {t2:.1f} s "
+                       f"for two): the FP64 oracle's H^2-expanded assembly and LU per frequency over "
+                       f"a spawn process pool of {workers} workers (one BLAS thread each); job time "
+                       f"a + b Ls with a = {a:.1f} s, b = {b:.1f} s per frequency, est. {est:.0f} s")}, qref
 
 
 def run_reference(args):
@@ -449,7 +492,7 @@ def run_reference(args):
     cb = None
     for i in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        cb = cpu_baseline(max_seconds=args.cpu_seconds)
+        cb, _ = cpu_baseline()
         if i >= args.warmup:
             times.append(time.perf_counter() - t0)
     W = WORKLOAD
@@ -460,7 +503,7 @@ def run_reference(args):
             "ms_per_step": 1e3 * sum(times) / max(1, len(times)), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": W["name"], "triangles": M, "N": W["N"], "L": L,
-                       "mode": "oracle H^2-expanded + LU (sampled)"},
+                       "mode": "oracle H^2-expanded + LU (3 sampled frequencies per step)"},
             "cpu_baseline": cb,
             "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -474,7 +517,6 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--dense-baseline", action="store_true",
                     help="also time one pass of the dense FP64 GPU path on the same workload")

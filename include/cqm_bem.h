@@ -52,6 +52,10 @@ extern "C" {
 #define CQM_ECUDA     5   /* a CUDA runtime error; see cqm_bem_last_error() */
 #define CQM_ECAPACITY 6   /* a fixed device capacity (rank slots, block lists) was exceeded */
 
+/* Largest step count N: the transforms hold 24 (N + 1) bytes of twiddle and
+ * R-power tables in one CTA's shared memory (at most 227 KB). */
+#define CQM_MAX_STEPS 9000
+
 /* Operator representations. */
 #define CQM_MODE_DENSE  0 /* dense V_l for every solved frequency (Sec. 3.2) */
 #define CQM_MODE_H2MACA 1 /* near field + H^2 far field, both MACA-compressed in frequency (eq. lrfinal) */
@@ -161,7 +165,7 @@ int cqm_params_default(cqm_params* p);
 
 /* Build the operator for a mesh (Alg. 3: cluster, cluster bases, partition,
  * MACA per block -- or the dense V_l in CQM_MODE_DENSE).
- * dt > 0 time step, N >= 1 steps (L = N + 1 frequencies), bdf_order 1 or 2
+ * dt > 0 time step, 1 <= N <= CQM_MAX_STEPS steps (L = N + 1 frequencies), bdf_order 1 or 2
  * (chi of BDF-k: sum_{j=1..k} (1 - z)^j / j).  cuda_stream is a cudaStream_t
  * (NULL: the legacy default stream).  On success *out owns the device state.
  * Errors: CQM_EINVAL (arguments, mesh indices, zero-area triangles),
@@ -185,6 +189,21 @@ int cqm_bem_solve(cqm_handle* h, const double* rhs, double* density, int32_t mem
  * dir: 3 doubles (host, normalised inside).  rhs: (N+1) x nt float64 in `mem`. */
 int cqm_bem_rhs_plane_wave(cqm_handle* h, const double dir[3], double width, double delay,
                            double* rhs, int32_t mem);
+
+/* Time limit, in nanoseconds, of every bounded device wait of the handle's
+ * pipelined kernels (the mbarrier waits of the tensor-core far coupling);
+ * 0 restores the default of one second.  A wait that runs out makes its
+ * kernel record the expiry, stop issuing work, let what it issued finish,
+ * free its tensor memory and return; the GMRES loop stops at its next check
+ * and the call returns CQM_ETIMEOUT (cqm_bem_last_error names the limit).
+ * The handle stays usable: the next call starts with the expiry cleared.
+ * expire_next != 0 arms a one-shot check of that path: in the next launch of
+ * the pipelined kernel one thread first waits on a barrier that nothing
+ * completes, so that this wait runs out after `ns` (nothing faults or hangs;
+ * the expiry is reported as above).
+ * Errors: CQM_EINVAL (NULL, ns < 0).  (Sec. 6.2 names no device waits; this
+ * is the failure path of the solver's pipelined kernels.) */
+int cqm_bem_set_wait_limit(cqm_handle* h, int64_t ns, int32_t expire_next);
 
 /* Release everything the handle owns.  NULL is accepted. */
 int cqm_bem_destroy(cqm_handle* h);
@@ -316,6 +335,13 @@ const char* cqm_bem_kernel_name(int32_t id);
  *
  * The first call on a device looks the scratch address up (once per device,
  * with that device current); make that first call before any stream capture.
+ * The address is kept for the life of the process: it assumes the device's
+ * primary context is not torn down in between (after a cudaDeviceReset on
+ * that device the cached address is stale and must not be used).
+ * Work: one CTA of 1024 threads builds the whole tree.  A node whose
+ * centroids all fall on one side of its box midpoint is split at the median,
+ * ranking each element against the whole node (quadratic in the node size),
+ * so a degenerate mesh near the size limit can keep one SM busy for seconds.
  * Every call shares the one scratch array per device, so calls whose work
  * overlaps on the GPU (other threads, other streams) race: serialise them.
  * Errors: CQM_EINVAL (NULL, sizes, vertex indices out of range -- checked on

@@ -30,7 +30,7 @@ EXPORTED = [
     "cqm_bem_get_block_factors", "cqm_bem_entries", "cqm_bem_apply", "cqm_bem_apply_inner",
     "cqm_bem_solve_frequencies", "cqm_bem_forward_transform", "cqm_bem_inverse_transform",
     "cqm_bem_profile", "cqm_bem_profile_read", "cqm_bem_kernel_name",
-    "cqm_cluster_tree_noalloc",
+    "cqm_cluster_tree_noalloc", "cqm_bem_set_wait_limit",
 ]
 K_COUNT = 25
 
@@ -130,6 +130,7 @@ def load(build_if_missing: bool = False):
         "cqm_bem_profile": (C.c_int, [vp, i32]),
         "cqm_bem_profile_read": (C.c_int, [vp, i32, vp, vp]),
         "cqm_bem_kernel_name": (C.c_char_p, [i32]),
+        "cqm_bem_set_wait_limit": (C.c_int, [vp, i64, i32]),
         "cqm_cluster_tree_noalloc": (C.c_int, [vp, i32, vp, i32, i32] + [vp] * 9 + [C.POINTER(i32), vp]),
     }
     for name, (res, args) in sig.items():
@@ -286,6 +287,12 @@ class CqmBem:
                                                    C.byref(cols), Cm.ctypes.data, D.ctypes.data),
                "block_factors")
         return Cm, D
+
+    def set_wait_limit(self, ns: int, expire_next: bool = False):
+        """Time limit of the bounded device waits (0: the default, one second);
+        expire_next arms a one-shot wait that runs out (failure-path check)."""
+        _check(self._lib.cqm_bem_set_wait_limit(self._h, int(ns), 1 if expire_next else 0),
+               "set_wait_limit")
 
     def profile(self, enable: bool = True):
         """Reset the kernel timers; time every launch from now on if enable."""

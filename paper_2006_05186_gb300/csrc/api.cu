@@ -17,9 +17,16 @@ int check_wait_flag(cqm_handle* h) {
   CQM_CUDA_TRY(cudaMemcpyAsync(&w, h->flag.p + 1, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   CQM_CUDA_TRY(cudaStreamSynchronize(h->stream));
   if (w != 0) {
-    set_last_error("a bounded device wait expired in the tensor-core far coupling");
+    CQM_TRY(clear_wait_flag(h));
+    set_last_error("a bounded device wait expired in the tensor-core far coupling (limit " +
+                   std::to_string(h->wait_limit_ns) + " ns)");
     return CQM_ETIMEOUT;
   }
+  return CQM_OK;
+}
+
+int clear_wait_flag(cqm_handle* h) {
+  CQM_CUDA_TRY(cudaMemsetAsync(h->flag.p + 1, 0, sizeof(int), h->stream));
   return CQM_OK;
 }
 
@@ -136,6 +143,11 @@ int cqm_bem_setup(const cqm_mesh* mesh, double dt, int32_t N, int32_t bdf_order,
   }
   if (!(dt > 0.0) || N < 1 || (bdf_order != 1 && bdf_order != 2)) {
     set_last_error("need dt > 0, N >= 1, bdf_order in {1, 2}");
+    return CQM_EINVAL;
+  }
+  if (N > CQM_MAX_STEPS) {
+    set_last_error("N = " + std::to_string(N) + " exceeds CQM_MAX_STEPS = " +
+                   std::to_string(CQM_MAX_STEPS) + " (transform tables in shared memory)");
     return CQM_EINVAL;
   }
   for (int64_t k = 0; k < 3 * (int64_t)mesh->nt; ++k) {
@@ -380,6 +392,7 @@ int cqm_bem_apply_inner(cqm_handle* h, const double* x, double* y, int32_t mem) 
     dx = t;
     CQM_TRY(S.get(&dy, n));
   }
+  CQM_TRY(clear_wait_flag(h));
   CQM_TRY(apply_operator_inner(h, dx, dy));
   if (mem == CQM_MEM_HOST)
     CQM_CUDA_TRY(cudaMemcpyAsync(y, dy, n * sizeof(double2), cudaMemcpyDeviceToHost, h->stream));
@@ -608,6 +621,13 @@ static const char* k_names[CQM_K_COUNT] = {
 
 const char* cqm_bem_kernel_name(int32_t id) {
   return (id >= 0 && id < CQM_K_COUNT) ? k_names[id] : "";
+}
+
+int cqm_bem_set_wait_limit(cqm_handle* h, int64_t ns, int32_t expire_next) {
+  if (!h || ns < 0) return CQM_EINVAL;
+  h->wait_limit_ns = ns == 0 ? 1000000000ull : (uint64_t)ns;
+  h->wait_probe = expire_next != 0;
+  return CQM_OK;
 }
 
 int cqm_bem_profile(cqm_handle* h, int32_t enable) {

@@ -221,7 +221,11 @@ int gmres_solve(cqm_handle* h, const double2* d_b, double2* d_x, cqm_solve_info*
   Allocator& A = h->alloc;
   GmresWork W;
   int st = CQM_OK;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
   auto cleanup = [&]() {
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    e0 = e1 = nullptr;
     W.Vb.free(A); W.r.free(A); W.Z.free(A); W.H.free(A); W.sn.free(A); W.g.free(A); W.y.free(A);
     W.cs.free(A); W.bnorm.free(A); W.beta.free(A); W.thr.free(A); W.active.free(A); W.kdim.free(A);
     W.converged.free(A); W.counters.free(A);
@@ -260,12 +264,12 @@ int gmres_solve(cqm_handle* h, const double2* d_b, double2* d_x, cqm_solve_info*
     return CQM_OK;
   };
   GM_TRY(cu(cudaMemsetAsync(d_x, 0, sizeof(double2) * Ls * M, S)));
-  cudaEvent_t e0, e1;
-  cudaEventCreate(&e0);
-  cudaEventCreate(&e1);
+  GM_TRY(clear_wait_flag(h));
+  GM_TRY(cu(cudaEventCreate(&e0)));
+  GM_TRY(cu(cudaEventCreate(&e1)));
   cudaEventRecord(e0, S);
   int iters = 0, restarts = 0;
-  bool first = true;
+  bool first = true, timed_out = false;
   const int maxit = std::max(1, h->params.gmres_max_iter);
   int status = CQM_OK;
   while (true) {
@@ -304,10 +308,17 @@ int gmres_solve(cqm_handle* h, const double2* d_b, double2* d_x, cqm_solve_info*
       ++iters;
       if ((j % 4) == 3 || j == m - 1) {
         GM_TRY(cu(cudaMemcpyAsync(W.h_counters, W.counters.p, sizeof(int), cudaMemcpyDeviceToHost, S)));
+        // a bounded wait that ran out leaves the inner products unusable: stop
+        GM_TRY(cu(cudaMemcpyAsync(W.h_counters + 1, h->flag.p + 1, sizeof(int), cudaMemcpyDeviceToHost, S)));
         GM_TRY(cu(cudaStreamSynchronize(S)));
+        if (W.h_counters[1] != 0) {
+          timed_out = true;
+          break;
+        }
         if (W.h_counters[0] == 0) break;
       }
     }
+    if (timed_out) break;
     {
       ProfScope ps_(h, CQM_K_GMRES_OTHER);
       k_update_x<<<Ls, 256, 0, S>>>(M, Ls, m, W.Vb.p, W.H.p, W.g.p, W.kdim.p, W.converged.p, W.y.p,
@@ -334,8 +345,6 @@ int gmres_solve(cqm_handle* h, const double2* d_b, double2* d_x, cqm_solve_info*
   for (int l = 0; l < Ls; ++l) rel[l] = bn[l] > 0.0 ? rel[l] / bn[l] : 0.0;
   float ms = 0.f;
   cudaEventElapsedTime(&ms, e0, e1);
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   if (info) {
     info->iterations = iters;
     info->restarts = restarts;

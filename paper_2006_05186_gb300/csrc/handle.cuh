@@ -17,6 +17,9 @@ struct cqm_handle {
   cqm::DArray<int> tri;
   cqm::DArray<double> xyz, P, area, cen, diam;
   cqm::DArray<int> flag;  // device status word (degenerate input, capacity, ...)
+  // time limit of the bounded device waits of the pipelined kernels (ns)
+  uint64_t wait_limit_ns = 1000000000ull;
+  bool wait_probe = false;  // next pipelined launch makes one wait that runs out
 
   // quadrature tables
   cqm::DArray<double4> near_pt, ss_pt[3];
@@ -193,8 +196,10 @@ void prof_resolve(cqm_handle* h);
 void prof_release(cqm_handle* h);
 
 // flag[1]: a kernel's bounded wait expired (it recorded the error and returned).
-// Reads the word after the stream's work so far; CQM_ETIMEOUT if it is set.
+// Reads the word after the stream's work so far and clears it; CQM_ETIMEOUT if
+// it was set.  clear_wait_flag resets it before a call's first launch.
 int check_wait_flag(cqm_handle* h);
+int clear_wait_flag(cqm_handle* h);
 
 // operator dispatch: FP64 operator, and the operator of the inner GMRES
 // iterations (its FP32 copy when mixed precision is on)

@@ -24,7 +24,9 @@
 // the item's partial tile, which the per-row reduction adds in item order (as
 // for the SIMT kernel).  Every wait is bounded in time; on expiry the kernel
 // records an error in *err, stops issuing work, lets issued copies and MMAs
-// drain, frees TMEM and returns.
+// drain, frees TMEM and returns.  The time limit of the waits of the main
+// loop is the handle's (cqm_bem_set_wait_limit); the drain at the end waits
+// for copies and MMAs already issued, with the default limit of one second.
 #include <algorithm>
 
 #include "handle.cuh"
@@ -92,7 +94,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     k_far_coupling_tc(int Ls, int cap, const int4* __restrict__ items, const int2* __restrict__ blocks,
                       const int* __restrict__ rank, const float2* __restrict__ Cf,
                       const float2* __restrict__ Df, const float2* __restrict__ xhat,
-                      float2* __restrict__ part, int* __restrict__ err) {
+                      float2* __restrict__ part, int* __restrict__ err, uint64_t lim,
+                      int probe) {
   using namespace umma;
   using K = TcCfg<NT>;
   constexpr int NC = K::NC;
@@ -104,6 +107,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   __shared__ __align__(8) uint64_t cempty_bar[NCS];
   __shared__ __align__(8) uint64_t done_bar;
   __shared__ __align__(8) uint64_t fin_bar;
+  __shared__ __align__(8) uint64_t probe_bar;  // never completed (failure-path check)
   __shared__ uint32_t tmem_sh;
   __shared__ volatile int abort_sh;
   __shared__ volatile int never_sh;
@@ -123,6 +127,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
     mbar_init(&done_bar, 1);
     mbar_init(&fin_bar, 1);
+    mbar_init(&probe_bar, 1);
     abort_sh = 0;
     never_sh = 0;
     mbar_init_fence();
@@ -132,6 +137,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_sh;
+
+  // Check of the failure path, armed from the host: the first CTA waits on a
+  // barrier that nothing completes; the wait runs out after `lim` and the
+  // whole CTA takes the abort path below.
+  if (probe && blockIdx.x == 0 && warp == 0) mbar_wait(&probe_bar, 0u, &abort_sh, err, ERR_TIMEOUT, lim);
 
   int nwork = 0;  // rank terms of the item; none leaves the tile zero
   for (int bi = it.y; bi < it.z; ++bi) nwork += rank[bi];
@@ -147,7 +157,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       uint32_t acc = 0;
       for (int k = 0; k < 4 * nwork; ++k, ++use) {
         const int s = (int)(use % NSTAGE);
-        const bool ok = mbar_wait(&full_bar[s], (use / NSTAGE) & 1u, &abort_sh, err, ERR_TIMEOUT);
+        const bool ok = mbar_wait(&full_bar[s], (use / NSTAGE) & 1u, &abort_sh, err, ERR_TIMEOUT, lim);
         tc_fence_after();
         if (ok && lane == 0) {
           const uint32_t a_hi = tmem + ACOL + 64u * s, a_lo = a_hi + 32u;
@@ -173,7 +183,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         for (; sp.bi < it.z; sp.next(it.z, rank), ++c_issued) {
           const int sc = (int)(c_issued % NCS);
           if (c_issued >= NCS &&
-              !mbar_wait(&cempty_bar[sc], (c_issued / NCS - 1) & 1u, &abort_sh, err, ERR_TIMEOUT))
+              !mbar_wait(&cempty_bar[sc], (c_issued / NCS - 1) & 1u, &abort_sh, err, ERR_TIMEOUT, lim))
             break;
           mbar_arrive_expect_tx(&cfull_bar[sc], CSLAB);
           bulk_g2s(cstage + (size_t)sc * CSLAB,
@@ -192,7 +202,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       for (int k = 0; k < 4 * nwork; ++k, ++use) {
         const int sc = (int)(use % NCS);
         float2 c[16];
-        const bool cok = mbar_wait(&cfull_bar[sc], (use / NCS) & 1u, &abort_sh, err, ERR_TIMEOUT);
+        const bool cok = mbar_wait(&cfull_bar[sc], (use / NCS) & 1u, &abort_sh, err, ERR_TIMEOUT, lim);
         if (cok) {
           const float2* cs = (const float2*)(cstage + (size_t)sc * CSLAB) + mu;
 #pragma unroll
@@ -202,7 +212,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         if (lane == 0) mbar_arrive(&cempty_bar[sc]);
         const int s = (int)(use % NSTAGE);
         const uint32_t round = use / NSTAGE;
-        if (round > 0) mbar_wait(&empty_bar[s], (round - 1) & 1u, &abort_sh, err, ERR_TIMEOUT);
+        if (round > 0) mbar_wait(&empty_bar[s], (round - 1) & 1u, &abort_sh, err, ERR_TIMEOUT, lim);
         if (!__any_sync(0xffffffffu, abort_sh != 0)) {
           tc_fence_after();
           uint32_t hi[16], lo[16];
@@ -273,7 +283,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       for (; cur.bi < it.z; ++use) {
         const int s = (int)(use % NSTAGE);
         const uint32_t round = use / NSTAGE;
-        if (round > 0) mbar_wait(&empty_bar[s], (round - 1) & 1u, &abort_sh, err, ERR_TIMEOUT);
+        if (round > 0) mbar_wait(&empty_bar[s], (round - 1) & 1u, &abort_sh, err, ERR_TIMEOUT, lim);
         if (!abort_sh) {
           unsigned char* Bhi = ring + (size_t)s * K::STAGE;
           unsigned char* Blo = Bhi + K::B_PLANE;
@@ -312,7 +322,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     if (warp >= 1 && warp <= 4) {
       const int qd = warp & 3;  // TMEM lanes 32 qd .. 32 qd + 31 belong to this warp
       const int m = 32 * qd + lane, mu = m & 63, im = m >> 6;
-      bool ok = nwork > 0 && mbar_wait(&done_bar, (uint32_t)chunk & 1u, &abort_sh, err, ERR_TIMEOUT);
+      bool ok = nwork > 0 && mbar_wait(&done_bar, (uint32_t)chunk & 1u, &abort_sh, err, ERR_TIMEOUT, lim);
       ok = __all_sync(0xffffffffu, ok);
       tc_fence_after();
       float* dst = (float*)(part + ((size_t)blockIdx.x * TP + mu) * Ls) + im;
@@ -377,7 +387,7 @@ int far_coupling_tc(cqm_handle* h) {
   case N:                                                                                          \
     k_far_coupling_tc<N><<<n, NTHREADS, TcCfg<N>::SMEM, h->stream>>>(                              \
         h->Ls, h->rank_cap, h->far_items.p, h->far_rc.p, h->far_rank.p, h->farC_f.p, h->farD_f.p,  \
-        h->xhat_f.p, h->part_f.p, h->flag.p + 1);                                                      \
+        h->xhat_f.p, h->part_f.p, h->flag.p + 1, h->wait_limit_ns, h->wait_probe ? 1 : 0);            \
     break;
   switch (nt_for(h->Ls)) {
     TC_CASE(1) TC_CASE(2) TC_CASE(3) TC_CASE(4) TC_CASE(5)
@@ -385,6 +395,7 @@ int far_coupling_tc(cqm_handle* h) {
     default: break;
   }
 #undef TC_CASE
+  h->wait_probe = false;  // one-shot
   CQM_CHECK_LAUNCH();
   return CQM_OK;
 }

@@ -89,10 +89,22 @@ __global__ void k_inverse(int M, int L, int Ls, double R, const double2* __restr
   }
 }
 
+// Shared memory of the tables: 24 L bytes (L <= CQM_MAX_STEPS + 1, checked
+// at setup); above the default 48 KB the kernels opt in to more.
+static size_t table_bytes(int L) { return (size_t)L * (sizeof(double2) + sizeof(double)); }
+
+template <class K>
+static int opt_in(K kernel, size_t sh) {
+  if (sh > 48 * 1024)
+    CQM_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+  return CQM_OK;
+}
+
 int forward_transform(cqm_handle* h, const double* d_b, double2* d_ghat) {
   constexpr int FT = 8;
   dim3 grid(grid_for(h->M, 128), grid_for(h->Ls, FT));
-  size_t sh = h->L * (sizeof(double2) + sizeof(double));
+  const size_t sh = table_bytes(h->L);
+  CQM_TRY(opt_in(k_forward<FT>, sh));
   {
     ProfScope ps_(h, CQM_K_FORWARD_DFT);
     k_forward<FT><<<grid, 128, sh, h->stream>>>(h->M, h->L, h->Ls, h->R, d_b, d_ghat);
@@ -104,7 +116,8 @@ int forward_transform(cqm_handle* h, const double* d_b, double2* d_ghat) {
 int inverse_transform(cqm_handle* h, const double2* d_qhat, double* d_q) {
   constexpr int NT = 8;
   dim3 grid(grid_for(h->M, 128), grid_for(h->L, NT));
-  size_t sh = h->L * (sizeof(double2) + sizeof(double));
+  const size_t sh = table_bytes(h->L);
+  CQM_TRY(opt_in(k_inverse<NT>, sh));
   {
     ProfScope ps_(h, CQM_K_INVERSE_DFT);
     k_inverse<NT><<<grid, 128, sh, h->stream>>>(h->M, h->L, h->Ls, h->R, d_qhat, d_q);

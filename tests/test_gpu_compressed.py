@@ -8,12 +8,12 @@ CPU oracle, through the C ABI.
 * MACA factors of sampled blocks approximate the exact block tensors to the
   stated tolerance;
 * the compressed solve matches the H^2-expanded oracle solve (time domain on
-  1280 triangles; sampled frequencies on the 5120-triangle, N = 256 workload).
+  1280 triangles; the 5120-triangle, N = 256 workload is in test_gpu_headline).
 """
 import numpy as np
 import pytest
 
-from oracle import cluster, cqm, dense, galerkin as G, h2, incident, maca
+from oracle import cluster, cqm, dense, galerkin as G, h2, incident, maca, pool
 from paper_2006_05186_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -61,7 +61,7 @@ def test_tree_and_partition_bit_exact(lib, name):
 
 def _h2_reference(m, N, dt, freqs, tree_ref, near, far, cheb_m=4):
     s = cqm.frequencies(N, dt, 2)[freqs]
-    return h2.h2_matrices(m.xyz, m.tri, s, tree_ref, near, far, cheb_m)
+    return pool.h2_matrices(m.xyz, m.tri, s, tree_ref, near, far, cheb_m)
 
 
 @pytest.mark.parametrize("cheb_m", [4, 3, 2])
@@ -131,7 +131,7 @@ def ref1280():
     t_ref = cluster.build_tree(m.xyz, m.tri, 32)
     near, far = cluster.partition(t_ref, 1.0)
     q_ref, _ = dense.solve(m.xyz, m.tri, N, dt, 2, b,
-                           matrices=lambda ss: h2.h2_matrices(m.xyz, m.tri, ss, t_ref, near, far, 4))
+                           matrices=lambda ss: pool.h2_matrices(m.xyz, m.tri, ss, t_ref, near, far, 4))
     return dict(m=m, N=N, dt=dt, b=b, q_ref=q_ref)
 
 
@@ -147,30 +147,6 @@ def test_compressed_solve_time_domain_1280(lib, ref1280, eps, tol):
     err = dense.rel_err(q, r["q_ref"])
     print(f"eps={eps}: time-domain rel err vs H2-expanded oracle {err:.3e}")
     assert err <= tol, err
-    op.close()
-
-
-def test_sphere5120_N256_sampled_frequencies(lib):
-    """The N = 256 workload on 5120 triangles: per-frequency solutions at the
-    smallest and the largest solved frequency against LU of the oracle's
-    H^2-expanded matrices."""
-    m = synth.icosphere(4)
-    N, dt = 256, 0.1
-    p = synth.plane_wave_pulse()
-    op = _op(m, dt, N, aca_eps=1e-7)
-    inf = op.info()
-    assert inf["n_near"] == 7938 and inf["n_far"] == 11208
-    b = op.rhs_plane_wave(p.direction, p.width, p.delay)
-    g = op.forward_transform(b)
-    qh, sinfo = op.solve_frequencies(g)
-    assert sinfo["converged"] == op.Ls
-    t_ref = cluster.build_tree(m.xyz, m.tri, 32)
-    near, far = cluster.partition(t_ref, 1.0)
-    for l in (0, op.Ls - 1):
-        V = _h2_reference(m, N, dt, np.array([l]), t_ref, near, far)[0]
-        ref = np.linalg.solve(V, g[l])
-        err = np.linalg.norm(qh[l] - ref) / np.linalg.norm(ref)
-        assert err <= 1e-6, (l, err)
     op.close()
 
 

@@ -69,6 +69,24 @@ def test_transforms(c1):
     assert np.max(np.abs(back - q_ref)) <= 1e-15 * R ** (-N) * (N + 1) * 10
 
 
+@pytest.mark.parametrize("N", [2048, 4095])
+def test_transforms_long(lib, N):
+    """The transforms keep their twiddle and R-power tables (24 L bytes) in
+    shared memory, which exceeds the default 48 KB from L = 2049 on: long step
+    counts (N = 2048 of the serving workload) still match the oracle."""
+    m = synth.icosphere(0)
+    op = _op(m, 0.05, N)
+    R = cqm.default_R(N)
+    rng = np.random.default_rng(7)
+    b = rng.standard_normal((N + 1, op.M))
+    g = op.forward_transform(b)
+    g_ref = cqm.forward(b, R)[: op.Ls]
+    assert np.max(np.abs(g - g_ref)) <= 1e-12 * np.max(np.abs(g_ref))
+    back = op.inverse_transform(g)
+    assert np.max(np.abs(back - b)) <= 1e-15 * R ** (-N) * (N + 1) * 10
+    op.close()
+
+
 def test_entries_every_case(c1):
     m, op = c1["m"], c1["op"]
     _, _, cen, diam = G.element_geometry(m.xyz, m.tri)
