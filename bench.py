@@ -6,7 +6,7 @@ of one full pass of the hot path -- geometry, cluster tree, partition,
 Chebyshev bases, MACA of every block, plane-wave data, forward R-scaled DFT,
 batched GMRES over the solved frequencies, inverse DFT -- on the 5120-triangle
 unit sphere, BDF2, N = 256, dt = 0.1, eta = 1, m = 4, leaf 32, MACA tolerance
-1e-7.  Arithmetic: tf32x3 tensor-core far coupling and fp32 near field in the
+1e-9.  Arithmetic: tf32x3 tensor-core far coupling and fp32 near field in the
 inner GMRES iterations, float-float residual applies, fp64 MACA, transforms and
 Krylov basis; the result meets the FP64 residual target.  Synthetic input:
 seeded icosphere and Gaussian plane-wave pulse.
@@ -33,11 +33,14 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# MACA tolerance 1e-7: the workload names 1e-6 as the accuracy of the result;
-# the solution error is about the conditioning times the MACA tolerance, so
-# 1e-7 keeps the result within 1e-6 of the H^2-expanded FP64 oracle.
+# MACA tolerance 1e-9: the metric is quoted at a relative error of 1e-6 in
+# the time domain.  The inverse transform scales per-frequency errors by up to
+# R^-N ~ 1e5 at the last steps; measured against the full FP64 oracle on this
+# workload (LU of its H^2-expanded V_l at all 129 solved frequencies), MACA
+# tolerances of 1e-7, 1e-8, 1e-9 give time-domain errors of 1.3e-5, 1.6e-6,
+# 3.4e-7.
 WORKLOAD = dict(name="sphere5120_N256", level=4, N=256, dt=0.1, bdf=2, eta=1.0, cheb_m=4,
-                n_min=32, aca_eps=1e-7)
+                n_min=32, aca_eps=1e-9)
 METRIC = "CQM-BEM solve throughput (triangle·freq/s), p50/p99 latency at rel err ≤1e-6"
 UNIT = "triangle*freq/s"
 
@@ -361,8 +364,8 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": ("mixed: tf32x3 tensor-core far coupling and fp32 near field in the inner GMRES "
-                  "iterations, float-float (~48-bit) residual applies, fp64 MACA, DFTs, "
-                  "preconditioner and Krylov basis"),
+                  "iterations, float-float (~48-bit) residual applies and MACA kernel evaluations, "
+                  "fp64 MACA pivots and updates, DFTs, preconditioner and Krylov basis"),
         "data": "synthetic",
         "config": {"workload": W["name"], "triangles": M, "N": N, "L": L, "Ls": Ls, "dt": dt,
                    "bdf": 2, "eta": W["eta"], "cheb_m": W["cheb_m"], "leaf": W["n_min"],

@@ -126,6 +126,10 @@ typedef struct cqm_params {
                              bytes per far block) for the FP64-accurate apply,
                              if that takes at most 40% of the device memory and
                              the allocation succeeds; 0 = keep it factored [1]   */
+  int32_t maca_ff;        /* H2MACA with cache_quadrature: the MACA slices and fibres
+                             evaluate the kernel at the cached points in float-float
+                             (~47 bits) on the FP32 pipes, exp(-s r0) of each pair's
+                             distance bound in FP64; 0 = FP64 throughout   [1]   */
   const cqm_allocator* allocator; /* NULL: stream-ordered CUDA pool        [NULL] */
 } cqm_params;
 

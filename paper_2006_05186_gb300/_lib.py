@@ -58,6 +58,7 @@ class cqm_params(C.Structure):
         ("exact_ff", C.c_int32),
         ("expand_near", C.c_int32),
         ("expand_far", C.c_int32),
+        ("maca_ff", C.c_int32),
         ("allocator", C.POINTER(cqm_allocator)),
     ]
 

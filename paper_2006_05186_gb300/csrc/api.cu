@@ -84,6 +84,7 @@ int cqm_params_default(cqm_params* p) {
   p->expand_near = 1;
   p->expand_far = 1;
   p->cache_quadrature = 1;
+  p->maca_ff = 1;
   p->tensor_cores = 1;
   p->allocator = nullptr;
   return CQM_OK;
@@ -109,6 +110,8 @@ int cqm_bem_destroy(cqm_handle* h) {
   Allocator& A = h->alloc;
   h->xyz.free(A); h->tri.free(A); h->P.free(A); h->area.free(A); h->cen.free(A);
   h->diam.free(A); h->flag.free(A); h->near_pt.free(A);
+  h->exp_t2_ff.free(A); h->exp_cs_ff.free(A); h->pt_r0.free(A);
+  h->fpt_d.free(A); h->fpt_c.free(A); h->fpt_r0.free(A);
   for (int t = 0; t < 3; ++t) { h->ss_pt[t].free(A); h->ss_w[t].free(A); }
   h->s.free(A); h->Vd.free(A); h->exp_t2.free(A); h->exp_cs.free(A);
   h->perm.free(A); h->node_begin.free(A); h->node_end.free(A); h->node_son0.free(A);

@@ -108,6 +108,17 @@ __global__ void k_exp_tables(double* t2, double2* cs) {
   cs[j] = make_double2(co, sn);
 }
 
+// Float-float copies of those tables: hi = the nearest float, lo = the rest.
+__global__ void k_exp_tables_ff(const double* __restrict__ t2, const double2* __restrict__ cs,
+                                float2* t2f, float4* csf) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= 1024) return;
+  const float a = (float)t2[j];
+  t2f[j] = make_float2(a, (float)(t2[j] - (double)a));
+  const float c = (float)cs[j].x, sn = (float)cs[j].y;
+  csf[j] = make_float4(c, (float)(cs[j].x - (double)c), sn, (float)(cs[j].y - (double)sn));
+}
+
 int build_quad_tables(cqm_handle* h) {
   const int gn = h->params.g_near, gs = h->params.g_sing;
   std::vector<double> x, w;
@@ -141,6 +152,10 @@ int build_quad_tables(cqm_handle* h) {
   CQM_TRY(h->exp_t2.allocate(h->alloc, 1024));
   CQM_TRY(h->exp_cs.allocate(h->alloc, 1024));
   k_exp_tables<<<4, 256, 0, h->stream>>>(h->exp_t2.p, h->exp_cs.p);
+  CQM_CHECK_LAUNCH();
+  CQM_TRY(h->exp_t2_ff.allocate(h->alloc, 1024));
+  CQM_TRY(h->exp_cs_ff.allocate(h->alloc, 1024));
+  k_exp_tables_ff<<<4, 256, 0, h->stream>>>(h->exp_t2.p, h->exp_cs.p, h->exp_t2_ff.p, h->exp_cs_ff.p);
   CQM_CHECK_LAUNCH();
   h->quad.t2 = h->exp_t2.p;
   h->quad.cs = h->exp_cs.p;

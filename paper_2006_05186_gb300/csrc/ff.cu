@@ -337,7 +337,7 @@ constexpr int FAR_NF = 8;
 __global__ void __launch_bounds__(256) k_far_expand_ff(int Ls, int p, int cap, const int* __restrict__ rank,
                                                        const ffc* __restrict__ Cf, const double2* __restrict__ Df,
                                                        ffc* __restrict__ S) {
-  __shared__ ffc Ds[32][FAR_NF];
+  __shared__ ffc Ds[64][FAR_NF];  // rank <= rank_cap <= 64
   const int b = blockIdx.y, l0 = blockIdx.x * FAR_NF;
   const int rk = rank[b], nf = min(FAR_NF, Ls - l0);
   for (int t = threadIdx.x; t < rk * FAR_NF; t += blockDim.x) {
@@ -459,7 +459,7 @@ __global__ void __launch_bounds__(256) k_near_expand_ff(int Ls, int cap, const i
                                                         const double2* __restrict__ D,
                                                         const int64_t* __restrict__ voff,
                                                         ffc* __restrict__ V, float2* __restrict__ Vf) {
-  __shared__ ffc Ds[32][FAR_NF];
+  __shared__ ffc Ds[64][FAR_NF];  // rank <= rank_cap <= 64
   const int b = blockIdx.y, l0 = blockIdx.x * FAR_NF;
   const int2 c2 = rc[b];
   const int nr = end[c2.x] - begin[c2.x], nc = end[c2.y] - begin[c2.y];

@@ -27,6 +27,8 @@ struct cqm_handle {
   cqm::Quad quad{};
   cqm::DArray<double> exp_t2;
   cqm::DArray<double2> exp_cs;
+  cqm::DArray<float2> exp_t2_ff;  // the same tables as float-float pairs
+  cqm::DArray<float4> exp_cs_ff;
 
   // CQM frequencies s_l, l = 0..L-1 (eq. cqm_freq)
   cqm::DArray<double2> s;
@@ -66,7 +68,14 @@ struct cqm_handle {
   int64_t n_points = 0;
   cqm::DArray<int64_t> pt_off;
   cqm::DArray<int> pt_cnt;
-  cqm::DArray<double> pt_r, pt_c;
+  cqm::DArray<double> pt_r, pt_c;  // FP64 r and c; with maca_ff the same bytes hold
+                                   // float-float d = r - r0 and c
+  cqm::DArray<double> pt_r0;       // maca_ff: distance bound r0 of each pair
+  // maca_ff: far blocks' kernel points (Chebyshev pairs), float-float d and c,
+  // entry (mu, nu) of block b at b p^2 + mu p + nu, bound r0 per block
+  cqm::DArray<float2> fpt_d, fpt_c;
+  cqm::DArray<double> fpt_r0;
+  bool cache_far_points = false;
 
   // apply plan: leaf clusters and row clusters owning far blocks
   std::vector<int> h_leaves, h_far_rows;

@@ -19,6 +19,7 @@
 #include <unordered_map>
 #include <vector>
 
+#include "ffexp.cuh"
 #include "handle.cuh"
 
 namespace cqm {
@@ -53,7 +54,60 @@ struct MacaBlocks {
   const int* pt_cnt;
   const double* pt_r;
   const double* pt_c;
+  // maca_ff: the cached near points hold float-float d = r - r0 and c (same
+  // bytes as pt_r, pt_c), r0 per pair; far blocks' points in fpt_*; the
+  // exponential tables as float-float pairs
+  int ff;
+  const double* pt_r0;
+  const float2* fpt_d;
+  const float2* fpt_c;
+  const double* fpt_r0;
+  const float2* t2ff;
+  const float4* csff;
 };
+
+// The float-float exponential tables of a block, in shared memory.
+struct FFTables {
+  float2 t2[1024];
+  float4 cs[1024];
+};
+__device__ __forceinline__ void load_ff_tables(FFTables& T, const MacaBlocks& B) {
+  for (int k = threadIdx.x; k < 1024; k += blockDim.x) {
+    T.t2[k] = B.t2ff[k];
+    T.cs[k] = B.csff[k];
+  }
+  __syncthreads();
+}
+
+// Warp sum of a float-float value (result in every lane).
+__device__ __forceinline__ ff warp_sum_ff(ff a) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const ff b = {__shfl_xor_sync(0xffffffffu, a.h, o), __shfl_xor_sync(0xffffffffu, a.l, o)};
+    a = ff_add(a, b);
+  }
+  return a;
+}
+
+// sum over this lane's points k = lane, lane + 32, ... of c_k exp(-s d_k)
+__device__ __forceinline__ void lane_points_ff(const float2* __restrict__ pd, const float2* __restrict__ pc,
+                                               int n, int lane, const ffs& sf, const FFTables& T, ff& ar,
+                                               ff& ai) {
+  int cnt = 0;
+  for (int k = lane; k < n; k += 32) {
+    const float2 dd = pd[k], cc = pc[k];
+    ff vr, vi;
+    cexp_ff(ff{dd.x, dd.y}, ff{cc.x, cc.y}, sf, T.t2, T.cs, vr, vi);
+    ff_acc(ar, vr);
+    ff_acc(ai, vi);
+    if ((++cnt & 15) == 0) {
+      ff_norm(ar);
+      ff_norm(ai);
+    }
+  }
+  ff_norm(ar);
+  ff_norm(ai);
+}
 
 __device__ __forceinline__ int rows_of(const MacaBlocks& B, int b) {
   return B.kind == 0 ? B.end[B.rc[b].x] - B.begin[B.rc[b].x] : B.p;
@@ -88,6 +142,61 @@ __global__ void __launch_bounds__(256) k_maca_slice(MacaBlocks B, Geom g, Quad q
   double2* out = slot(B, b, t, nr, nc);
   const double2 sk = s[B.kcur[b]];
   const int2 rc = B.rc[b];
+  if (B.ff) {
+    // entries E0 * sum_k c_k exp(-s d_k), E0 = exp(-s r0) in FP64, the sum in
+    // float-float from the cached points
+    __shared__ FFTables T;
+    __shared__ double2 E0s;
+    load_ff_tables(T, B);
+    const ffs sf = ffs_of(sk);
+    if (B.kind == 1) {
+      if (threadIdx.x == 0) E0s = cexp_c(B.fpt_r0[b], 1.0, sk, q);
+      __syncthreads();
+      const double2 E0 = E0s;
+      const size_t pp = (size_t)B.p * B.p;
+      for (int e = threadIdx.x; e < nr * nc; e += blockDim.x) {
+        const float2 dd = B.fpt_d[(size_t)b * pp + e], cc = B.fpt_c[(size_t)b * pp + e];
+        ff vr, vi;
+        cexp_ff(ff{dd.x, dd.y}, ff{cc.x, cc.y}, sf, T.t2, T.cs, vr, vi);
+        out[e] = cmul(make_double2(ff_to_double(vr), ff_to_double(vi)), E0);
+      }
+      return;
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int64_t base = B.off[b] / B.cap;
+    const bool diag = rc.x == rc.y;
+    const int npair = diag ? nr * (nr + 1) / 2 : nr * nc;
+    const float2* pd = (const float2*)B.pt_r;
+    const float2* pc = (const float2*)B.pt_c;
+    for (int e2 = w; e2 < npair; e2 += nw) {
+      int i, j;
+      if (diag) {
+        i = 0;
+        int rem = e2;
+        while (rem >= nr - i) {
+          rem -= nr - i;
+          ++i;
+        }
+        j = i + rem;
+      } else {
+        i = e2 / nc;
+        j = e2 - i * nc;
+      }
+      const int e = i * nc + j;
+      const int64_t o = B.pt_off[base + e];
+      ff ar = {0.f, 0.f}, ai = {0.f, 0.f};
+      lane_points_ff(pd + o, pc + o, B.pt_cnt[base + e], lane, sf, T, ar, ai);
+      ar = warp_sum_ff(ar);
+      ai = warp_sum_ff(ai);
+      if (lane == 0) {
+        const double2 E0 = cexp_c(B.pt_r0[base + e], 1.0, sk, q);
+        const double2 v = cmul(make_double2(ff_to_double(ar), ff_to_double(ai)), E0);
+        out[e] = v;
+        if (diag) out[j * nc + i] = v;
+      }
+    }
+    return;
+  }
   if (B.kind == 1) {
     for (int e = threadIdx.x; e < nr * nc; e += blockDim.x) {
       const int mu = e / nc, nu = e - mu * nc;
@@ -245,6 +354,60 @@ __global__ void __launch_bounds__(256) k_maca_fibre(MacaBlocks B, Geom g, Quad q
   const int cse = pair_case(g, q, I, J);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   constexpr int NF = 8;
+  if (B.ff) {
+    __shared__ FFTables T;
+    load_ff_tables(T, B);
+    const int nc = B.end[rc.y] - B.begin[rc.y];
+    const bool swap = rc.x == rc.y && pv.x > pv.y;
+    const int64_t k = B.off[b] / B.cap + (swap ? (int64_t)pv.y * nc + pv.x : (int64_t)pv.x * nc + pv.y);
+    const int64_t o = B.pt_off[k];
+    const int n = B.pt_cnt[k];
+    const double r0 = B.pt_r0[k];
+    const float2* pd = (const float2*)B.pt_r + o;
+    const float2* pc = (const float2*)B.pt_c + o;
+    for (int f0 = w * NF; f0 < B.Ls; f0 += nw * NF) {
+      const int nf = min(NF, B.Ls - f0);
+      ffs sv[NF];
+      ff ar[NF], ai[NF];
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        sv[f] = ffs_of(f < nf ? s[f0 + f] : make_double2(0.0, 0.0));
+        ar[f] = ai[f] = ff{0.f, 0.f};
+      }
+      int cnt = 0;
+      for (int p = lane; p < n; p += 32) {
+        const float2 dd = pd[p], cc = pc[p];
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+          ff vr, vi;
+          cexp_ff(ff{dd.x, dd.y}, ff{cc.x, cc.y}, sv[f], T.t2, T.cs, vr, vi);
+          ff_acc(ar[f], vr);
+          ff_acc(ai[f], vi);
+        }
+        if ((++cnt & 15) == 0) {
+#pragma unroll
+          for (int f = 0; f < NF; ++f) {
+            ff_norm(ar[f]);
+            ff_norm(ai[f]);
+          }
+        }
+      }
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        ff_norm(ar[f]);
+        ff_norm(ai[f]);
+        ar[f] = warp_sum_ff(ar[f]);
+        ai[f] = warp_sum_ff(ai[f]);
+      }
+      // lane f < nf scales frequency f by exp(-s_f r0)
+#pragma unroll
+      for (int f = 0; f < NF; ++f)
+        if (lane == f && f < nf)
+          out[f0 + f] = cmul(make_double2(ff_to_double(ar[f]), ff_to_double(ai[f])),
+                             cexp_c(r0, 1.0, s[f0 + f], q));
+    }
+    return;
+  }
   if (B.pt_r) {
     const int nc = B.end[rc.y] - B.begin[rc.y];
     // a diagonal block caches its pairs i <= j only; (i, j) and (j, i) are one pair
@@ -487,12 +650,29 @@ __global__ void __launch_bounds__(1024) k_scan_i64(int n, const int64_t* __restr
   if (threadIdx.x == 0) out[n] = carry;
 }
 
+// Radius of the ball about the centroid that holds triangle t.
+__device__ __forceinline__ double tri_radius(const Geom& g, int t) {
+  const double* P = g.P + 9 * t;
+  const double* c = g.cen + 3 * t;
+  double r2 = 0.0;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const double dx = P[3 * k] - c[0], dy = P[3 * k + 1] - c[1], dz = P[3 * k + 2] - c[2];
+    r2 = fmax(r2, dx * dx + dy * dy + dz * dz);
+  }
+  return sqrt(r2) * (1.0 + 1e-12);
+}
+
 // Geometry of every point of every pair of near block b: one warp per pair.
+// With ff, the points hold float-float d = r - r0 and c (in the bytes of
+// pt_r and pt_c) and pt_r0 the pair's bound r0 <= r: 0 for pairs that share a
+// vertex, else the centroid distance minus the two triangles' radii.
 __global__ void __launch_bounds__(256) k_pair_geometry(const int2* __restrict__ rc, const int* __restrict__ begin,
                                                       const int* __restrict__ end, const int* __restrict__ perm,
                                                       const int64_t* __restrict__ off, int cap, Geom g, Quad q,
                                                       const int64_t* __restrict__ block_base,
-                                                      int64_t* pt_off, double* pt_r, double* pt_c) {
+                                                      int64_t* pt_off, double* pt_r, double* pt_c,
+                                                      int ff_mode, double* pt_r0) {
   const int b = blockIdx.x;
   const int2 c2 = rc[b];
   if (c2.x > c2.y) return;  // mirrored block: no points
@@ -507,10 +687,70 @@ __global__ void __launch_bounds__(256) k_pair_geometry(const int2* __restrict__ 
     __syncwarp();
     if (lane == 0) pt_off[base + e] = o;
     const int cse = pair_case(g, q, I, J);
+    if (!ff_mode) {
+      pair_points(g, q, I, J, cse, lane, 32, [&](int k, double r, double c) {
+        pt_r[o + k] = r;
+        pt_c[o + k] = c;
+      });
+      continue;
+    }
+    double r0 = 0.0;
+    if (cse == CASE_REGULAR || cse == CASE_NEAR) {
+      const double* ci = g.cen + 3 * I;
+      const double* cj = g.cen + 3 * J;
+      const double dx = ci[0] - cj[0], dy = ci[1] - cj[1], dz = ci[2] - cj[2];
+      r0 = fmax(0.0, sqrt(dx * dx + dy * dy + dz * dz) * (1.0 - 1e-12) - tri_radius(g, I) - tri_radius(g, J));
+    }
+    if (lane == 0) pt_r0[base + e] = r0;
+    float2* pd = (float2*)pt_r;
+    float2* pc = (float2*)pt_c;
     pair_points(g, q, I, J, cse, lane, 32, [&](int k, double r, double c) {
-      pt_r[o + k] = r;
-      pt_c[o + k] = c;
+      const ff d = ff_of(fmax(r - r0, 0.0)), cf = ff_of(c);
+      pd[o + k] = make_float2(d.h, d.l);
+      pc[o + k] = make_float2(cf.h, cf.l);
     });
+  }
+}
+
+// Kernel points of the far blocks (the Chebyshev pairs, Alg. 3 FAR) for the
+// float-float slices: entry (mu, nu) of upper block b holds d = |xi_nu -
+// xi_mu| - r0 and c = 1 / (4 pi |xi_nu - xi_mu|), r0 the distance of the
+// boxes of the two clusters' Chebyshev points (a bound of every entry's).
+__global__ void __launch_bounds__(256) k_far_points(const int2* __restrict__ rc, const double* __restrict__ cheb,
+                                                   int m, int p, float2* fd, float2* fc, double* fr0) {
+  const int b = blockIdx.x;
+  const int2 c2 = rc[b];
+  if (c2.x > c2.y) return;  // mirrored block: no MACA
+  __shared__ double s_r0;
+  if (threadIdx.x == 0) {
+    const double* a = cheb + (size_t)c2.x * 3 * m;
+    const double* z = cheb + (size_t)c2.y * 3 * m;
+    double d2 = 0.0;
+    for (int ax = 0; ax < 3; ++ax) {
+      double alo = a[ax * m], ahi = alo, zlo = z[ax * m], zhi = zlo;
+      for (int k = 1; k < m; ++k) {
+        alo = fmin(alo, a[ax * m + k]); ahi = fmax(ahi, a[ax * m + k]);
+        zlo = fmin(zlo, z[ax * m + k]); zhi = fmax(zhi, z[ax * m + k]);
+      }
+      const double gap = fmax(0.0, fmax(zlo - ahi, alo - zhi));
+      d2 += gap * gap;
+    }
+    s_r0 = sqrt(d2) * (1.0 - 1e-12);
+    fr0[b] = s_r0;
+  }
+  __syncthreads();
+  const double r0 = s_r0;
+  const size_t pp = (size_t)p * p;
+  for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+    const int mu = e / p, nu = e - mu * p;
+    double xr[3], xc[3];
+    cheb_point(cheb, c2.x, m, mu, xr);
+    cheb_point(cheb, c2.y, m, nu, xc);
+    const double d0 = xc[0] - xr[0], d1 = xc[1] - xr[1], d2 = xc[2] - xr[2];
+    const double r = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+    const ff d = ff_of(fmax(r - r0, 0.0)), c = ff_of(1.0 / (CQM_FOUR_PI * r));
+    fd[(size_t)b * pp + e] = make_float2(d.h, d.l);
+    fc[(size_t)b * pp + e] = make_float2(c.h, c.l);
   }
 }
 
@@ -547,9 +787,13 @@ static int build_point_cache(cqm_handle* h, int64_t n_pairs) {
     if (st == CQM_OK) st = h->pt_c.allocate(h->alloc, std::max<int64_t>(npts, 1));
     if (st == CQM_OK) {
       ProfScope ps_(h, CQM_K_MACA_SLICE);
-      k_pair_geometry<<<nb, 256, 0, h->stream>>>(h->near_rc.p, h->node_begin.p, h->node_end.p, h->perm.p,
-                                                h->near_off.p, h->rank_cap, g, h->quad, bbase.p,
-                                                h->pt_off.p, h->pt_r.p, h->pt_c.p);
+      const bool ffm = h->params.maca_ff != 0;
+      if (ffm) st = h->pt_r0.allocate(h->alloc, std::max<int64_t>(n_pairs, 1));
+      if (st == CQM_OK)
+        k_pair_geometry<<<nb, 256, 0, h->stream>>>(h->near_rc.p, h->node_begin.p, h->node_end.p, h->perm.p,
+                                                  h->near_off.p, h->rank_cap, g, h->quad, bbase.p,
+                                                  h->pt_off.p, h->pt_r.p, h->pt_c.p, ffm ? 1 : 0,
+                                                  h->pt_r0.p);
       if (cudaGetLastError() != cudaSuccess) st = CQM_ECUDA;
     }
   }
@@ -633,6 +877,22 @@ static int run_maca(cqm_handle* h, int kind, int n, const int2* rc, DArray<doubl
   B.pt_cnt = cached ? h->pt_cnt.p : nullptr;
   B.pt_r = cached ? h->pt_r.p : nullptr;
   B.pt_c = cached ? h->pt_c.p : nullptr;
+  B.ff = 0;
+  B.pt_r0 = nullptr;
+  B.fpt_d = B.fpt_c = nullptr;
+  B.fpt_r0 = nullptr;
+  B.t2ff = h->exp_t2_ff.p;
+  B.csff = h->exp_cs_ff.p;
+  if (h->params.maca_ff && kind == 0 && cached) {
+    B.ff = 1;
+    B.pt_r0 = h->pt_r0.p;
+  }
+  if (h->params.maca_ff && kind == 1 && h->cache_far_points) {
+    B.ff = 1;
+    B.fpt_d = h->fpt_d.p;
+    B.fpt_c = h->fpt_c.p;
+    B.fpt_r0 = h->fpt_r0.p;
+  }
   cudaStream_t S = h->stream;
   const Geom g = geom_from(h);
   {
@@ -714,8 +974,27 @@ int build_maca(cqm_handle* h) {
   h->pt_c.free(h->alloc);
   h->pt_off.free(h->alloc);
   h->pt_cnt.free(h->alloc);
+  h->pt_r0.free(h->alloc);
+  h->cache_far_points = false;
+  if (h->params.maca_ff && h->params.cache_quadrature && h->n_far > 0) {
+    const size_t n = (size_t)h->n_far * h->p * h->p;
+    CQM_TRY(h->fpt_d.allocate(h->alloc, n));
+    CQM_TRY(h->fpt_c.allocate(h->alloc, n));
+    CQM_TRY(h->fpt_r0.allocate(h->alloc, h->n_far));
+    {
+      ProfScope ps_(h, CQM_K_MACA_SLICE);
+      k_far_points<<<h->n_far, 256, 0, h->stream>>>(h->far_rc.p, h->cheb.p, h->m, h->p, h->fpt_d.p,
+                                                    h->fpt_c.p, h->fpt_r0.p);
+    }
+    CQM_CHECK_LAUNCH();
+    h->cache_far_points = true;
+  }
   CQM_TRY(run_maca(h, 1, h->n_far, h->far_rc.p, h->farC, h->farD, h->far_rank, nullptr,
                    (size_t)h->n_far * h->rank_cap * h->p * h->p, h->h_far, h->h_far_rank));
+  h->fpt_d.free(h->alloc);
+  h->fpt_c.free(h->alloc);
+  h->fpt_r0.free(h->alloc);
+  h->cache_far_points = false;
   cqm_setup_info& I = h->info;
   I.near_entries = 0;
   I.near_rank_entries = 0;

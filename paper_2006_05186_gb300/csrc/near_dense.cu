@@ -33,7 +33,7 @@ __global__ void __launch_bounds__(256) k_near_expand(int Ls, int cap, const int2
                                                      const double2* __restrict__ D,
                                                      const int64_t* __restrict__ voff,
                                                      double2* __restrict__ V, float2* __restrict__ Vf) {
-  __shared__ double2 Ds[32][EXP_NF];
+  __shared__ double2 Ds[64][EXP_NF];  // rank <= rank_cap <= 64
   const int b = blockIdx.y, l0 = blockIdx.x * EXP_NF;
   const int2 c2 = rc[b];
   const int nr = end[c2.x] - begin[c2.x], nc = end[c2.y] - begin[c2.y];

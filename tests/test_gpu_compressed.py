@@ -176,7 +176,7 @@ def test_point_cache_matches_direct_quadrature(lib):
     direct quadrature (same pivots and ranks, entries equal to rounding)."""
     m = synth.icosphere(3)
     N, dt = 24, 0.1
-    a = _op(m, dt, N, cache_quadrature=1)
+    a = _op(m, dt, N, cache_quadrature=1, maca_ff=0)
     b = _op(m, dt, N, cache_quadrature=0)
     ba, bb = a.blocks(), b.blocks()
     assert np.array_equal(ba["near_rank"], bb["near_rank"])
@@ -235,3 +235,54 @@ def test_expanded_near_field_equals_factored(lib):
         assert e_exp <= 1e-5 and e_exp <= 2.0 * e_fact + 1e-7, (l, e_exp, e_fact)
     for op in ops.values():
         op.close()
+
+
+@pytest.mark.parametrize("maca_ff", [1, 0])
+def test_maca_full_rank_reproduces_entries(lib, maca_ff):
+    """With every solved frequency taken as a slice, the MACA reproduces the
+    block tensors exactly; the float-float (maca_ff = 1) and FP64 slice and
+    fibre evaluations both match the oracle's entries and Chebyshev
+    couplings to 1e-11 at 33 frequencies up to |s| = 40."""
+    m = synth.icosphere(3)
+    N, dt = 64, 0.1
+    op = _op(m, dt, N, aca_eps=1e-15, rank_cap=33, maca_ff=maca_ff)
+    t_ref = cluster.build_tree(m.xyz, m.tri, 32)
+    near, far = cluster.partition(t_ref, 1.0)
+    s = cqm.frequencies(N, dt, 2)[: op.Ls]
+    rng = np.random.default_rng(21)
+    worst = 0.0
+    for b in rng.choice(len(near), 12, replace=False):
+        r, c = near[b]
+        ir, ic = t_ref.indices(r), t_ref.indices(c)
+        I, J = np.meshgrid(ir, ic, indexing="ij")
+        Gt = G.pair_entries(m.xyz, m.tri, I.ravel(), J.ravel(), s).reshape(len(ir), len(ic), -1)
+        Cg, Dg = op.block_factors(0, int(b))
+        worst = max(worst, np.linalg.norm(np.einsum("tij,tk->ijk", Cg, Dg) - Gt) / np.linalg.norm(Gt))
+    for b in rng.choice(len(far), 12, replace=False):
+        r, c = far[b]
+        St = np.moveaxis(h2.coupling(t_ref, r, c, s, 4), 0, 2)
+        Cg, Dg = op.block_factors(1, int(b))
+        worst = max(worst, np.linalg.norm(np.einsum("tij,tk->ijk", Cg, Dg) - St) / np.linalg.norm(St))
+    op.close()
+    print(f"maca_ff={maca_ff}: worst block error {worst:.2e}")
+    assert worst <= 1e-11, worst
+
+
+def test_maca_ff_matches_fp64_maca(lib):
+    """The float-float slices and fibres change the MACA's entries only at
+    rounding level: the ranks agree to one and the two compressed operators
+    agree to a few times the MACA tolerance at every frequency."""
+    m = synth.icosphere(3)
+    N, dt, eps = 64, 0.1, 1e-9
+    a = _op(m, dt, N, aca_eps=eps, maca_ff=1)
+    b = _op(m, dt, N, aca_eps=eps, maca_ff=0)
+    ba, bb = a.blocks(), b.blocks()
+    assert np.max(np.abs(ba["near_rank"] - bb["near_rank"])) <= 1
+    assert np.max(np.abs(ba["far_rank"] - bb["far_rank"])) <= 1
+    rng = np.random.default_rng(5)
+    x = rng.standard_normal((a.Ls, m.nt)) + 1j * rng.standard_normal((a.Ls, m.nt))
+    ya, yb = a.apply(x), b.apply(x)
+    err = np.linalg.norm(ya - yb, axis=1) / np.linalg.norm(yb, axis=1)
+    a.close()
+    b.close()
+    assert np.max(err) <= 20 * eps, err

@@ -1,17 +1,19 @@
 """Parity at the configuration the throughput is quoted on: the 5120-triangle
 unit sphere, BDF2, N = 256 (L = 257, 129 solved frequencies), dt = 0.1,
-eta = 1, m = 4, leaf 32, MACA tolerance 1e-7, every other parameter at its
+eta = 1, m = 4, leaf 32, MACA tolerance 1e-9, every other parameter at its
 default (the launch configuration of the benchmark).
 
-* Nine solved frequencies spread over [0, Ls), including Ls / 2: the GPU's
-  qhat_l against LU of the oracle's H^2-expanded V_l (same tree and
-  interpolation, no frequency compression; the oracle's own data and forward
-  transform), element by element to 1e-6 of max |qhat_l|.
-* The time-domain densities against the same path with the MACA at 1e-12,
-  whose frequencies are first checked against the oracle to 1e-8.  The
-  inverse transform scales rounding that differs between frequencies by up
-  to R^-N ~ 1e5 (eq. omega_n), so the sampled frequencies alone do not bound
-  the time-domain error; this comparison covers all 257 steps.
+The oracle solves the same problem from scratch: its own plane-wave data and
+forward transform, LU of its H^2-expanded V_l (same tree and interpolation,
+no frequency compression) at all 129 solved frequencies, and its inverse
+transform (about five minutes on 16 cores through the process pool).
+
+* Every solved frequency: qhat_l element by element to 1e-6 of max |qhat_l|.
+* The time-domain densities to 1e-6 (max over steps of the step error over
+  the largest step norm).  The inverse transform scales rounding that differs
+  between frequencies by up to R^-N ~ 1e5 (eq. omega_n), so this is the
+  binding gate: measured against this oracle, MACA tolerances of 1e-7, 1e-8
+  and 1e-9 give 1.3e-5, 1.6e-6 and 3.4e-7, all from the last steps.
 """
 import numpy as np
 import pytest
@@ -22,12 +24,16 @@ from paper_2006_05186_gb300 import synth
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
-N, DT, LEVEL = 256, 0.1, 4
+N, DT, LEVEL, EPS = 256, 0.1, 4, 1e-9
 
 
-def _run(m, p, **kw):
-    from paper_2006_05186_gb300 import CqmBem
-    op = CqmBem(m.xyz, m.tri, DT, N, 2, mode="h2maca", eta=1.0, cheb_m=4, n_min=32, **kw)
+@pytest.fixture(scope="module")
+def headline():
+    from paper_2006_05186_gb300 import CqmBem, build
+    build.build()
+    m = synth.icosphere(LEVEL)
+    p = synth.plane_wave_pulse()
+    op = CqmBem(m.xyz, m.tri, DT, N, 2, mode="h2maca", eta=1.0, cheb_m=4, n_min=32, aca_eps=EPS)
     b = op.rhs_plane_wave(p.direction, p.width, p.delay)
     g = op.forward_transform(b)
     qh, info = op.solve_frequencies(g)
@@ -35,55 +41,46 @@ def _run(m, p, **kw):
     q_solve = op.solve(b)
     op.close()
     torch.cuda.empty_cache()
-    return dict(b=b, qh=qh, q=q, q_solve=q_solve, info=info)
-
-
-@pytest.fixture(scope="module")
-def headline():
-    from paper_2006_05186_gb300 import build
-    build.build()
-    m = synth.icosphere(LEVEL)
-    p = synth.plane_wave_pulse()
-    bench = _run(m, p, aca_eps=1e-7)
-    tight = _run(m, p, aca_eps=1e-12, rank_cap=64)
-    Ls = (N + 1) // 2 + 1
-    freqs = np.unique(np.concatenate([np.round(np.linspace(0, Ls - 1, 8)).astype(int), [Ls // 2]]))
+    L = N + 1
+    Ls = L // 2 + 1
+    R = cqm.default_R(N)
     t = cluster.build_tree(m.xyz, m.tri, 32)
     near, far = cluster.partition(t, 1.0)
     b_ref = incident.rhs_plane_wave(m.xyz, m.tri, N, DT, p.direction, p.width, p.delay)
-    g_ref = cqm.forward(b_ref, cqm.default_R(N))[freqs]
-    s = cqm.frequencies(N, DT, 2)[freqs]
-    q_ref = pool.h2_solve_frequencies(m.xyz, m.tri, s, t, near, far, 4, g_ref)
-    return dict(bench=bench, tight=tight, freqs=freqs, q_ref=q_ref, b_ref=b_ref, Ls=Ls)
+    g_ref = cqm.forward(b_ref, R)
+    s = cqm.frequencies(N, DT, 2)
+    qh_ref = np.zeros((Ls, m.nt), dtype=np.complex128)
+    for l0 in range(0, Ls, 16):
+        ls = np.arange(l0, min(Ls, l0 + 16))
+        qh_ref[ls] = pool.h2_solve_frequencies(m.xyz, m.tri, s[ls], t, near, far, 4, g_ref[ls])
+    q_ref = cqm.inverse(dense.fill_conjugate(qh_ref, L), R).real
+    return dict(b=b, qh=qh, q=q, q_solve=q_solve, info=info, Ls=Ls, b_ref=b_ref, qh_ref=qh_ref,
+                q_ref=q_ref)
 
 
 def test_solve_composes_the_three_steps(headline):
     """cqm_bem_solve = forward transform, batched GMRES, inverse transform."""
-    for run in (headline["bench"], headline["tight"]):
-        assert dense.rel_err(run["q_solve"], run["q"]) <= 1e-13
-        assert run["info"]["converged"] == headline["Ls"]
-        assert run["info"]["max_rel_residual"] <= 1e-13
+    assert dense.rel_err(headline["q_solve"], headline["q"]) <= 1e-13
+    assert headline["info"]["converged"] == headline["Ls"]
+    assert headline["info"]["max_rel_residual"] <= 1e-13
 
 
 def test_data_matches_oracle(headline):
-    b = headline["bench"]["b"]
-    assert np.max(np.abs(b - headline["b_ref"])) <= 1e-14 * np.max(np.abs(headline["b_ref"]))
+    b, b_ref = headline["b"], headline["b_ref"]
+    assert np.max(np.abs(b - b_ref)) <= 1e-14 * np.max(np.abs(b_ref))
 
 
-@pytest.mark.parametrize("which,tol", [("bench", 1e-6), ("tight", 1e-8)])
-def test_sampled_frequencies_vs_oracle(headline, which, tol):
-    qh = headline[which]["qh"]
-    worst = 0.0
-    for k, l in enumerate(headline["freqs"]):
-        ref = headline["q_ref"][k]
-        e_max = np.max(np.abs(qh[l] - ref)) / np.max(np.abs(ref))
-        e_2 = np.linalg.norm(qh[l] - ref) / np.linalg.norm(ref)
-        print(f"{which} l={l}: max-norm {e_max:.2e}, 2-norm {e_2:.2e}")
-        worst = max(worst, e_max, e_2)
-    assert worst <= tol, worst
+def test_every_frequency_vs_oracle(headline):
+    qh, ref = headline["qh"], headline["qh_ref"]
+    err = np.max(np.abs(qh - ref), axis=1) / np.max(np.abs(ref), axis=1)
+    print("per-frequency max-norm error: max %.2e at l = %d, median %.2e"
+          % (err.max(), int(np.argmax(err)), np.median(err)))
+    assert np.max(err) <= 1e-6, err
 
 
-def test_time_domain_vs_tight_maca(headline):
-    err = dense.rel_err(headline["bench"]["q"], headline["tight"]["q"])
-    print(f"time-domain rel err, MACA 1e-7 vs 1e-12: {err:.3e}")
+def test_time_domain_vs_oracle(headline):
+    q, q_ref = headline["q"], headline["q_ref"]
+    err = dense.rel_err(q, q_ref)
+    steps = np.linalg.norm(q - q_ref, axis=1) / np.max(np.linalg.norm(q_ref, axis=1))
+    print(f"time-domain rel err vs the oracle {err:.3e} (worst step {int(np.argmax(steps))})")
     assert err <= 1e-6, err
