@@ -6,7 +6,7 @@ of one full pass of the hot path -- geometry, cluster tree, partition,
 Chebyshev bases, MACA of every block, plane-wave data, forward R-scaled DFT,
 batched GMRES over the solved frequencies, inverse DFT -- on the 5120-triangle
 unit sphere, BDF2, N = 256, dt = 0.1, eta = 1, m = 4, leaf 32, MACA tolerance
-1e-9.  Arithmetic: tf32x3 tensor-core far coupling and fp32 near field in the
+1e-9.  Arithmetic: bf16x3 tensor-core far coupling and fp32 near field in the
 inner GMRES iterations, float-float residual applies, fp64 MACA, transforms and
 Krylov basis; the result meets the FP64 residual target.  Synthetic input:
 seeded icosphere and Gaussian plane-wave pulse.
@@ -64,15 +64,13 @@ FP32_PEAK_SOURCE = "unit counts x max SM clock (152 SMs x 128 FP32 lanes x 2 x 2
 TF32_OVER_BF16 = 1.1 / 2.25
 
 
-# DRAM bytes (read + write) of one launch of the tensor-core coupling per far
-# rank term, from the ncu capture of that kernel (commit 8b60da1) on the
-# 1280-triangle sphere with N = 64: 351.6 MB read + 8.2 MB written for 10586
-# rank terms.  The traffic is the FP32 coupling factors read once (32 KB per
-# rank term) plus the small d_t, xhat and partial-tile terms, so it grows with
-# the rank terms; the bench scales it to the workload's rank-term count.
-TC_DRAM_BYTES_PER_RANK_TERM = (351.601152e6 + 8.199936e6) / 10586
-TC_DRAM_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of k_far_coupling_tc (commit 8b60da1, "
-                  "1280-triangle sphere, N = 64), scaled by far rank terms")
+# DRAM bytes (read + write) of one launch of the bf16 tensor-core coupling per
+# far rank term, from an ncu capture of that kernel; None until one is taken
+# of the current kernel.  The traffic is the 32 KB bf16 image of each rank
+# term read once plus the small d_t, xhat and partial-tile terms, so it grows
+# with the rank terms and the bench scales it to the workload's count.
+TC2_DRAM_BYTES_PER_RANK_TERM = None
+TC2_DRAM_SOURCE = "ncu dram__bytes_read.sum + dram__bytes_write.sum of k_far_coupling_tc2, scaled by far rank terms"
 
 
 def tf32_peak():
@@ -214,14 +212,23 @@ def kernel_models(info, Ls, p, tensor_cores, tf32=None):
         "far_exact": dict(fp32, work=2.0 * 48 * cmac_far, what="float-float complex MAC (FP32 issue)"),
         "near_exact": dict(fp32, work=2.0 * 48 * cmac_near, what="float-float complex MAC (FP32 issue)"),
     }
-    if tensor_cores and p == 64:
+    if tensor_cores == 2 and p == 64:
         peak, src = tf32_peak() if tf32 is None else (
             tf32, "measured here: cuBLAS TF32 GEMM 8192^3 (torch.matmul, allow_tf32), best of 10")
         models["far_coupling"] = dict(
             bound="tensor", peak=peak, peak_source=src, unit="TFLOP/s", work=8.0 * cmac_far,
             what="complex MAC on tcgen05 TF32 (useful flops; the 3-product split executes 3x)",
-            traffic=TC_DRAM_BYTES_PER_RANK_TERM * info["rank_sum_far"],
-            traffic_source=TC_DRAM_SOURCE)
+            traffic=None)
+    elif tensor_cores == 1 and p == 64:
+        pk, src = _peaks()
+        bf16 = pk.get("bf16_tflops_sustained", pk["bf16_tflops"])
+        models["far_coupling"] = dict(
+            bound="tensor", peak=bf16, unit="TFLOP/s", work=8.0 * cmac_far,
+            peak_source=f"{src} cuBLAS bf16 GEMM, sustained (MEASURED_PEAKS.json bf16_tflops_sustained)",
+            what=("complex MAC on tcgen05 bf16 (useful flops; the hi/lo three-product split "
+                  "executes 3x, and frequencies are padded to 128-row chunks)"),
+            traffic=TC2_DRAM_BYTES_PER_RANK_TERM * info["rank_sum_far"] if TC2_DRAM_BYTES_PER_RANK_TERM else None,
+            traffic_source=TC2_DRAM_SOURCE)
     pk, src = _peaks()
     hbm = dict(bound="hbm", peak=pk["hbm_gbs"], unit="GB/s",
                peak_source=f"{src} STREAM-style copy, MEASURED_PEAKS.json hbm_gbs")
@@ -363,14 +370,14 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": ("mixed: tf32x3 tensor-core far coupling and fp32 near field in the inner GMRES "
+        "dtype": ("mixed: bf16x3 tensor-core far coupling and fp32 near field in the inner GMRES "
                   "iterations, float-float (~48-bit) residual applies and MACA kernel evaluations, "
                   "fp64 MACA pivots and updates, DFTs, preconditioner and Krylov basis"),
         "data": "synthetic",
         "config": {"workload": W["name"], "triangles": M, "N": N, "L": L, "Ls": Ls, "dt": dt,
                    "bdf": 2, "eta": W["eta"], "cheb_m": W["cheb_m"], "leaf": W["n_min"],
                    "aca_eps": W["aca_eps"], "mode": "h2maca", "parallelism": f"replicas{world}",
-                   "far_coupling": "tcgen05 tf32 x3" if inf["tensor_cores"] else "fp32 simt",
+                   "far_coupling": {1: "tcgen05 bf16 x3", 2: "tcgen05 tf32 x3"}.get(inf["tensor_cores"], "fp32 simt"),
                    "l2": "256 MB buffer written between timed steps; working set "
                          f"{inf['device_bytes'] / 2**30:.1f} GiB > L2"},
         "latency_ms": {"p50": 1e3 * lat[len(lat) // 2],

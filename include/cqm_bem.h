@@ -107,8 +107,12 @@ typedef struct cqm_params {
   double inner_rtol;      /* with inner_fp32: a cycle ends once its residual
                              estimate fell by this factor                 [1e-5] */
   int32_t tensor_cores;   /* H2MACA with inner_fp32, m = 4: far coupling of the inner
-                             operator on the tcgen05 tensor cores (TF32, three-product
-                             split, TMEM accumulator); 0 = FP32 SIMT       [1]   */
+                             operator on the tcgen05 tensor cores.  1: bf16 hi/lo
+                             three-product split, frequencies on the MMA rows, the
+                             C factors streamed as precomputed images, d_t applied
+                             to each term's TMEM accumulator; 2: TF32 three-product
+                             split with d_t folded into the B operand;
+                             0 = FP32 SIMT                                 [1]   */
   int32_t cache_quadrature; /* H2MACA: keep every near-field quadrature point (r and
                              weight / (4 pi r)) in device memory for the MACA
                              slices and fibres (16 bytes per point)       [1]   */

@@ -112,6 +112,7 @@ int cqm_bem_destroy(cqm_handle* h) {
   h->diam.free(A); h->flag.free(A); h->near_pt.free(A);
   h->exp_t2_ff.free(A); h->exp_cs_ff.free(A); h->pt_r0.free(A);
   h->fpt_d.free(A); h->fpt_c.free(A); h->fpt_r0.free(A);
+  h->tc2_first.free(A); h->tc2_img.free(A); h->tc2_tail.free(A);
   for (int t = 0; t < 3; ++t) { h->ss_pt[t].free(A); h->ss_w[t].free(A); }
   h->s.free(A); h->Vd.free(A); h->exp_t2.free(A); h->exp_cs.free(A);
   h->perm.free(A); h->node_begin.free(A); h->node_end.free(A); h->node_son0.free(A);

@@ -86,13 +86,14 @@ __global__ void __launch_bounds__(256) k_far_coupling_f32(int Ls, int cap,
 }
 
 // yhat_r[mu][l] += sum of the partial tiles of row r's items, in item order.
-__global__ void k_far_reduce_f32(int Ls, const int* __restrict__ rows,
+__global__ void k_far_reduce_f32(int Ls, int lmax, const int* __restrict__ rows,
                                  const int* __restrict__ item_ptr, const float2* __restrict__ part,
                                  float2* __restrict__ yhat) {
   constexpr int P = 64;
   const int k = blockIdx.x;  // index into the list of far rows
   const int r = rows[k];
   for (int e = threadIdx.x; e < P * Ls; e += blockDim.x) {
+    if (e % Ls >= lmax) continue;  // frequencies the partial tiles do not hold
     float2 a = make_float2(0.f, 0.f);
     for (int it = item_ptr[k]; it < item_ptr[k + 1]; ++it) a = cadd(a, part[(size_t)it * P * Ls + e]);
     float2* o = yhat + (size_t)r * P * Ls + e;
@@ -196,16 +197,25 @@ int setup_f32_kernels(cqm_handle* h) {
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)far_smem<N>()));
   SETUP_NLT(1) SETUP_NLT(2) SETUP_NLT(3) SETUP_NLT(4) SETUP_NLT(5)
 #undef SETUP_NLT
+  CQM_TRY(setup_tc2(h));
   return setup_tc_kernels(h);
 }
 
 int far_coupling_f32(cqm_handle* h) {
   const int n = h->n_far_items;
   if (h->p != 64) return far_coupling_generic_f32(h);  // the tiled kernels are written for m = 4
-  if (h->params.tensor_cores && h->p == 64) {
+  if (h->params.tensor_cores == 1 && h->p == 64) {
+    int l_tail = h->Ls;
+    CQM_TRY(far_coupling_tc2(h, &l_tail));
+    k_far_reduce_f32<<<(unsigned)h->h_far_rows.size(), 256, 0, h->stream>>>(
+        h->Ls, l_tail, h->d_far_rows.p, h->far_item_ptr.p, h->part_f.p, h->yhat_f.p);
+    CQM_CHECK_LAUNCH();
+    return CQM_OK;
+  }
+  if (h->params.tensor_cores == 2 && h->p == 64) {
     CQM_TRY(far_coupling_tc(h));
     k_far_reduce_f32<<<(unsigned)h->h_far_rows.size(), 256, 0, h->stream>>>(
-        h->Ls, h->d_far_rows.p, h->far_item_ptr.p, h->part_f.p, h->yhat_f.p);
+        h->Ls, h->Ls, h->d_far_rows.p, h->far_item_ptr.p, h->part_f.p, h->yhat_f.p);
     CQM_CHECK_LAUNCH();
     return CQM_OK;
   }
@@ -223,7 +233,7 @@ int far_coupling_f32(cqm_handle* h) {
   }
 #undef LAUNCH_NLT
   k_far_reduce_f32<<<(unsigned)h->h_far_rows.size(), 256, 0, h->stream>>>(
-      h->Ls, h->d_far_rows.p, h->far_item_ptr.p, h->part_f.p, h->yhat_f.p);
+      h->Ls, h->Ls, h->d_far_rows.p, h->far_item_ptr.p, h->part_f.p, h->yhat_f.p);
   CQM_CHECK_LAUNCH();
   return CQM_OK;
 }

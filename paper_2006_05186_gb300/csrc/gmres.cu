@@ -15,8 +15,8 @@ namespace cqm {
 
 struct GmresWork {
   int m = 0;
-  DArray<double2> Vb, r, H, sn, g, y, Z;
-  DArray<double> cs, bnorm, beta, thr;
+  DArray<double2> Vb, r, H, sn, g, y, Z, p1, p2;  // p1, p2: partial dot products
+  DArray<double> cs, bnorm, beta, thr, nrm;
   DArray<int> active, kdim, converged, counters;
   int* h_counters = nullptr;  // pinned
 };
@@ -66,112 +66,174 @@ __global__ void k_restart(int M, int m, const double2* __restrict__ b, const dou
   for (int i = threadIdx.x; i < M; i += blockDim.x) v0[i] = cscale(rl[i], inv);
 }
 
-// One Arnoldi step j for every active frequency (one block per l): w = basis
-// slot j+1 (already holds V v_j), CGS2 against v_0..v_j, normalise, Givens.
+// One Arnoldi step j for every active frequency: w = basis slot j+1 (already
+// holds V v_j) is orthogonalised against v_0..v_j by classical Gram-Schmidt
+// applied twice (CGS2), normalised, and the new Hessenberg column is reduced
+// by the Givens rotations.  Each frequency's rows are split into nch chunks,
+// one block per (chunk, frequency), so that the whole GPU streams the basis;
+// the partial sums of a pass are reduced in chunk order by the next kernel
+// (no atomics: the result does not depend on the schedule).
+//   k_gs_dots:   part[l][ch][k] = sum over the chunk of conj(v_k) w
+//   k_gs_update: h = sum_ch part; w -= sum_k h_k v_k on the chunk; the first
+//                pass writes H[:, j] = h and the partial dots of the second
+//                pass, the second adds h to H[:, j] and writes ||w||^2 partials
+//   k_gs_finish: normalise the chunk; chunk 0 applies the rotations.
+__device__ __forceinline__ void chunk_rows(int M, int nch, int ch, int& i0, int& i1) {
+  const int CH = (M + nch - 1) / nch;
+  i0 = ch * CH;
+  i1 = min(M, i0 + CH);
+}
+
 template <int KB>
-__global__ void k_arnoldi(int M, int Ls, int m, int j, double2* __restrict__ Vb,
-                          double2* __restrict__ H, double* __restrict__ cs,
-                          double2* __restrict__ sn, double2* __restrict__ g,
-                          const double* __restrict__ thr, int* active, int* kdim, int* counters) {
-  __shared__ double sh[32];
-  __shared__ double2 hloc[64];
-  const int l = blockIdx.x;
-  if (!active[l]) return;
-  const size_t stride = (size_t)Ls * M;  // between basis vectors
-  double2* w = Vb + (size_t)(j + 1) * stride + (size_t)l * M;
-  const double2* v = Vb + (size_t)l * M;
-  double2* Hl = H + (size_t)l * (m + 1) * m;  // column-major (m+1) x m
-  for (int k = threadIdx.x; k <= j; k += blockDim.x) hloc[k] = make_double2(0.0, 0.0);
-  __syncthreads();
-  for (int pass = 0; pass < 2; ++pass) {
-    // h_k = <v_k, w>, KB at a time
-    for (int k0 = 0; k0 <= j; k0 += KB) {
-      double2 acc[KB];
+__device__ __forceinline__ void chunk_dots(int i0, int i1, int j, size_t stride, const double2* __restrict__ v,
+                                           const double2* __restrict__ w, double2* __restrict__ out,
+                                           double* sh) {
+  for (int k0 = 0; k0 <= j; k0 += KB) {
+    double2 acc[KB];
 #pragma unroll
-      for (int t = 0; t < KB; ++t) acc[t] = make_double2(0.0, 0.0);
-      for (int i = threadIdx.x; i < M; i += blockDim.x) {
-        const double2 wi = w[i];
+    for (int t = 0; t < KB; ++t) acc[t] = make_double2(0.0, 0.0);
+    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+      const double2 wi = w[i];
 #pragma unroll
-        for (int t = 0; t < KB; ++t)
-          if (k0 + t <= j) {
-            double2 vk = v[(size_t)(k0 + t) * stride + i];
-            acc[t].x += vk.x * wi.x + vk.y * wi.y;
-            acc[t].y += vk.x * wi.y - vk.y * wi.x;
-          }
-      }
-#pragma unroll
-      for (int t = 0; t < KB; ++t) {
+      for (int t = 0; t < KB; ++t)
         if (k0 + t <= j) {
-          double re = block_sum(acc[t].x, sh);
-          double im = block_sum(acc[t].y, sh);
-          if (threadIdx.x == 0) hloc[k0 + t] = make_double2(re, im);
+          const double2 vk = v[(size_t)(k0 + t) * stride + i];
+          acc[t].x += vk.x * wi.x + vk.y * wi.y;
+          acc[t].y += vk.x * wi.y - vk.y * wi.x;
         }
+    }
+#pragma unroll
+    for (int t = 0; t < KB; ++t) {
+      if (k0 + t <= j) {
+        const double re = block_sum(acc[t].x, sh);
+        const double im = block_sum(acc[t].y, sh);
+        if (threadIdx.x == 0) out[k0 + t] = make_double2(re, im);
       }
     }
-    __syncthreads();
-    // w -= sum_k h_k v_k
-    for (int i = threadIdx.x; i < M; i += blockDim.x) {
-      double2 wi = w[i];
-      for (int k = 0; k <= j; ++k) {
-        double2 vk = v[(size_t)k * stride + i];
-        double2 hk = hloc[k];
-        wi.x -= hk.x * vk.x - hk.y * vk.y;
-        wi.y -= hk.x * vk.y + hk.y * vk.x;
-      }
-      w[i] = wi;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0)
-      for (int k = 0; k <= j; ++k) Hl[(size_t)j * (m + 1) + k] = pass == 0 ? hloc[k] : cadd(Hl[(size_t)j * (m + 1) + k], hloc[k]);
-    __syncthreads();
   }
+}
+
+template <int KB>
+__global__ void __launch_bounds__(256) k_gs_dots(int M, int Ls, int m, int j, int nch,
+                                                 const double2* __restrict__ Vb,
+                                                 const int* __restrict__ active,
+                                                 double2* __restrict__ part) {
+  __shared__ double sh[32];
+  const int ch = blockIdx.x, l = blockIdx.y;
+  if (!active[l]) return;
+  int i0, i1;
+  chunk_rows(M, nch, ch, i0, i1);
+  const size_t stride = (size_t)Ls * M;
+  chunk_dots<KB>(i0, i1, j, stride, Vb + (size_t)l * M, Vb + (size_t)(j + 1) * stride + (size_t)l * M,
+                 part + ((size_t)l * nch + ch) * (m + 1), sh);
+}
+
+template <int KB>
+__global__ void __launch_bounds__(256) k_gs_update(int M, int Ls, int m, int j, int nch, int pass,
+                                                   double2* __restrict__ Vb, double2* __restrict__ H,
+                                                   const int* __restrict__ active,
+                                                   const double2* __restrict__ part_in,
+                                                   double2* __restrict__ part_out,
+                                                   double* __restrict__ nrm) {
+  __shared__ double sh[32];
+  __shared__ double2 h[64];
+  const int ch = blockIdx.x, l = blockIdx.y;
+  if (!active[l]) return;
+  for (int k = threadIdx.x; k <= j; k += blockDim.x) {
+    double2 a = make_double2(0.0, 0.0);
+    for (int c = 0; c < nch; ++c) a = cadd(a, part_in[((size_t)l * nch + c) * (m + 1) + k]);
+    h[k] = a;
+    if (ch == 0) {
+      double2* Hc = H + (size_t)l * (m + 1) * m + (size_t)j * (m + 1);
+      Hc[k] = pass == 0 ? a : cadd(Hc[k], a);
+    }
+  }
+  __syncthreads();
+  int i0, i1;
+  chunk_rows(M, nch, ch, i0, i1);
+  const size_t stride = (size_t)Ls * M;
+  const double2* v = Vb + (size_t)l * M;
+  double2* w = Vb + (size_t)(j + 1) * stride + (size_t)l * M;
   double s2 = 0.0;
-  for (int i = threadIdx.x; i < M; i += blockDim.x) s2 += cabs2(w[i]);
-  const double hn = sqrt(block_sum(s2, sh));
+  for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+    double2 wi = w[i];
+    for (int k = 0; k <= j; ++k) {
+      const double2 vk = v[(size_t)k * stride + i];
+      const double2 hk = h[k];
+      wi.x -= hk.x * vk.x - hk.y * vk.y;
+      wi.y -= hk.x * vk.y + hk.y * vk.x;
+    }
+    w[i] = wi;
+    s2 += cabs2(wi);
+  }
+  if (pass == 0) {
+    __syncthreads();  // this block's rows of w are final before the dots read them
+    chunk_dots<KB>(i0, i1, j, stride, v, w, part_out + ((size_t)l * nch + ch) * (m + 1), sh);
+  } else {
+    s2 = block_sum(s2, sh);
+    if (threadIdx.x == 0) nrm[(size_t)l * nch + ch] = s2;
+  }
+}
+
+// Normalise w; chunk 0 of each frequency closes the Hessenberg column with
+// the Givens rotations and decides whether the frequency stays active.
+__global__ void __launch_bounds__(256) k_gs_finish(int M, int Ls, int m, int j, int nch,
+                                                   double2* __restrict__ Vb, double2* __restrict__ H,
+                                                   double* __restrict__ cs, double2* __restrict__ sn,
+                                                   double2* __restrict__ g, const double* __restrict__ thr,
+                                                   const double* __restrict__ nrm, int* active, int* kdim,
+                                                   int* counters) {
+  const int ch = blockIdx.x, l = blockIdx.y;
+  if (!active[l]) return;
+  double s2 = 0.0;
+  for (int c = 0; c < nch; ++c) s2 += nrm[(size_t)l * nch + c];
+  const double hn = sqrt(s2);
+  int i0, i1;
+  chunk_rows(M, nch, ch, i0, i1);
+  double2* w = Vb + (size_t)(j + 1) * Ls * M + (size_t)l * M;
   if (hn > 0.0) {
     const double inv = 1.0 / hn;
-    for (int i = threadIdx.x; i < M; i += blockDim.x) w[i] = cscale(w[i], inv);
+    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) w[i] = cscale(w[i], inv);
   }
-  if (threadIdx.x == 0) {
-    double2* col = Hl + (size_t)j * (m + 1);
-    col[j + 1] = make_double2(hn, 0.0);
-    double* csl = cs + (size_t)l * m;
-    double2* snl = sn + (size_t)l * m;
-    for (int k = 0; k < j; ++k) {  // previous rotations
-      double2 a = col[k], b = col[k + 1];
-      col[k] = cadd(cscale(a, csl[k]), cmul(snl[k], b));
-      col[k + 1] = csub(cscale(b, csl[k]), cmulc(snl[k], a));  // -conj(s) a + c b
-    }
-    double2 a = col[j], b = col[j + 1];
-    double aa = sqrt(cabs2(a)), bb = sqrt(cabs2(b));
-    double c;
-    double2 s;
-    if (bb == 0.0) {
-      c = 1.0;
-      s = make_double2(0.0, 0.0);
-    } else if (aa == 0.0) {
-      c = 0.0;
-      s = make_double2(1.0, 0.0);
-    } else {
-      double t = hypot(aa, bb);
-      c = aa / t;
-      double2 ph = cscale(a, 1.0 / aa);
-      s = cscale(cmul(ph, make_double2(b.x, -b.y)), 1.0 / t);
-    }
-    csl[j] = c;
-    snl[j] = s;
-    col[j] = cadd(cscale(a, c), cmul(s, b));
-    col[j + 1] = make_double2(0.0, 0.0);
-    double2* gl = g + (size_t)l * (m + 1);
-    double2 gj = gl[j];
-    gl[j] = cscale(gj, c);
-    gl[j + 1] = make_double2(-(s.x * gj.x + s.y * gj.y), -(s.x * gj.y - s.y * gj.x));  // -conj(s) g_j
-    kdim[l] = j + 1;
-    const double res = sqrt(cabs2(gl[j + 1]));
-    if (!(res > thr[l]) || hn == 0.0) {
-      active[l] = 0;
-      atomicSub(&counters[0], 1);
-    }
+  if (ch != 0 || threadIdx.x != 0) return;
+  double2* col = H + (size_t)l * (m + 1) * m + (size_t)j * (m + 1);
+  col[j + 1] = make_double2(hn, 0.0);
+  double* csl = cs + (size_t)l * m;
+  double2* snl = sn + (size_t)l * m;
+  for (int k = 0; k < j; ++k) {  // previous rotations
+    const double2 a = col[k], b = col[k + 1];
+    col[k] = cadd(cscale(a, csl[k]), cmul(snl[k], b));
+    col[k + 1] = csub(cscale(b, csl[k]), cmulc(snl[k], a));  // -conj(s) a + c b
+  }
+  const double2 a = col[j], b = col[j + 1];
+  const double aa = sqrt(cabs2(a)), bb = sqrt(cabs2(b));
+  double c;
+  double2 s;
+  if (bb == 0.0) {
+    c = 1.0;
+    s = make_double2(0.0, 0.0);
+  } else if (aa == 0.0) {
+    c = 0.0;
+    s = make_double2(1.0, 0.0);
+  } else {
+    const double t = hypot(aa, bb);
+    c = aa / t;
+    const double2 ph = cscale(a, 1.0 / aa);
+    s = cscale(cmul(ph, make_double2(b.x, -b.y)), 1.0 / t);
+  }
+  csl[j] = c;
+  snl[j] = s;
+  col[j] = cadd(cscale(a, c), cmul(s, b));
+  col[j + 1] = make_double2(0.0, 0.0);
+  double2* gl = g + (size_t)l * (m + 1);
+  const double2 gj = gl[j];
+  gl[j] = cscale(gj, c);
+  gl[j + 1] = make_double2(-(s.x * gj.x + s.y * gj.y), -(s.x * gj.y - s.y * gj.x));  // -conj(s) g_j
+  kdim[l] = j + 1;
+  const double res = sqrt(cabs2(gl[j + 1]));
+  if (!(res > thr[l]) || hn == 0.0) {
+    active[l] = 0;
+    atomicSub(&counters[0], 1);
   }
 }
 
@@ -227,6 +289,7 @@ int gmres_solve(cqm_handle* h, const double2* d_b, double2* d_x, cqm_solve_info*
     if (e1) cudaEventDestroy(e1);
     e0 = e1 = nullptr;
     W.Vb.free(A); W.r.free(A); W.Z.free(A); W.H.free(A); W.sn.free(A); W.g.free(A); W.y.free(A);
+    W.p1.free(A); W.p2.free(A); W.nrm.free(A);
     W.cs.free(A); W.bnorm.free(A); W.beta.free(A); W.thr.free(A); W.active.free(A); W.kdim.free(A);
     W.converged.free(A); W.counters.free(A);
     if (W.h_counters) cudaFreeHost(W.h_counters);
@@ -248,6 +311,12 @@ int gmres_solve(cqm_handle* h, const double2* d_b, double2* d_x, cqm_solve_info*
   GM_TRY(W.kdim.allocate(A, Ls));
   GM_TRY(W.converged.allocate(A, Ls));
   GM_TRY(W.counters.allocate(A, 4));
+  // row chunks per frequency for the Arnoldi kernels: about 4 blocks per SM in
+  // all, at least 256 rows per chunk
+  const int nch = std::max(1, std::min((M + 255) / 256, (4 * 152 + Ls - 1) / Ls));
+  GM_TRY(W.p1.allocate(A, (size_t)Ls * nch * (m + 1)));
+  GM_TRY(W.p2.allocate(A, (size_t)Ls * nch * (m + 1)));
+  GM_TRY(W.nrm.allocate(A, (size_t)Ls * nch));
   if (cudaMallocHost(&W.h_counters, 4 * sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
     W.h_counters = nullptr;
@@ -301,8 +370,14 @@ int gmres_solve(cqm_handle* h, const double2* d_b, double2* d_x, cqm_solve_info*
       }
       {
         ProfScope ps_(h, CQM_K_ARNOLDI);
-        k_arnoldi<8><<<Ls, 256, 0, S>>>(M, Ls, m, j, W.Vb.p, W.H.p, W.cs.p, W.sn.p, W.g.p,
-                                        W.thr.p, W.active.p, W.kdim.p, W.counters.p);
+        const dim3 grid((unsigned)nch, (unsigned)Ls);
+        k_gs_dots<8><<<grid, 256, 0, S>>>(M, Ls, m, j, nch, W.Vb.p, W.active.p, W.p1.p);
+        k_gs_update<8><<<grid, 256, 0, S>>>(M, Ls, m, j, nch, 0, W.Vb.p, W.H.p, W.active.p, W.p1.p,
+                                            W.p2.p, W.nrm.p);
+        k_gs_update<8><<<grid, 256, 0, S>>>(M, Ls, m, j, nch, 1, W.Vb.p, W.H.p, W.active.p, W.p2.p,
+                                            W.p1.p, W.nrm.p);
+        k_gs_finish<<<grid, 256, 0, S>>>(M, Ls, m, j, nch, W.Vb.p, W.H.p, W.cs.p, W.sn.p, W.g.p,
+                                         W.thr.p, W.nrm.p, W.active.p, W.kdim.p, W.counters.p);
       }
       GM_TRY(cu(cudaGetLastError()));
       ++iters;

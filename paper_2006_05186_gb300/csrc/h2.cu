@@ -639,8 +639,10 @@ int build_f32_copy(cqm_handle* h) {
     CQM_TRY(cc(h->nearC, h->nearC_f));
     CQM_TRY(cc(h->nearD, h->nearD_f));
   }
-  h->farC_f_transposed = h->params.tensor_cores != 0 && h->p == 64;
-  if (h->farC_f_transposed) {
+  h->farC_f_transposed = h->params.tensor_cores == 2 && h->p == 64;
+  if (h->params.tensor_cores == 1 && h->p == 64) {
+    CQM_TRY(build_tc2(h));  // bf16 images of the far factors replace their FP32 copy
+  } else if (h->farC_f_transposed) {
     CQM_TRY(h->farC_f.allocate(h->alloc, std::max<size_t>(1, h->farC.n)));
     if (h->farC.n >= 4096) {
       ProfScope ps_(h, CQM_K_BASES);

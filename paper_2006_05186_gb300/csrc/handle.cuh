@@ -110,6 +110,12 @@ struct cqm_handle {
   bool far_expanded = false;
   cqm::DArray<double2> farS;
   cqm::DArray<float2> nearC_f, nearD_f, farC_f, farD_f, xhat_f, yhat_f;
+  // bf16 images of the far factors for the tensor-core coupling (32 KB per rank
+  // term, term t of block b at tc2_first[b] + t) and the FP32 expanded
+  // couplings of its tail frequencies
+  cqm::DArray<int64_t> tc2_first;
+  cqm::DArray<unsigned char> tc2_img;
+  cqm::DArray<float2> tc2_tail;
   cqm::DArray<float> Uleaf_f, Etr_f;
 
   // solver workspace
@@ -164,9 +170,13 @@ int near_apply_f32(cqm_handle* h, const double2* x, double2* y);
 int far_coupling_f32(cqm_handle* h);
 int far_coupling_generic_f32(cqm_handle* h);
 
-// tc.cu (tensor-core far coupling of the inner operator)
+// tc.cu (tensor-core far coupling of the inner operator, TF32, tensor_cores = 2)
 int setup_tc_kernels(cqm_handle* h);
 int far_coupling_tc(cqm_handle* h);
+// tc2.cu (tensor-core far coupling of the inner operator, bf16, tensor_cores = 1)
+int setup_tc2(cqm_handle* h);
+int build_tc2(cqm_handle* h);  // from the FP64 far factors, before factors_to_ff
+int far_coupling_tc2(cqm_handle* h, int* l_tail);
 
 // ff.cu (float-float contractions of the FP64-accurate apply)
 int setup_ff(cqm_handle* h);

@@ -1,0 +1,494 @@
+// Far-field coupling of the inner operator on the tcgen05 tensor cores, with
+// the frequencies on the MMA's M dimension (eq. lrfinal for all frequencies):
+//
+//   yhat_r[mu][l] += sum_{b=(r,c)} sum_t d_{b,t}[l] Z_{b,t}[mu][l],
+//   Z_{b,t} = C_{b,t} xhat_c  (64 x 64 times 64 x Ls, complex).
+//
+// Z does not depend on d_t, so the operand xhat_c is formed once per block
+// and the rank terms of the block stream past it; d_t[l] scales row l of Z^T,
+// which is one value per TMEM lane, in the epilogue.  In real arithmetic, with
+// A = [Re xhat_c^T | Im xhat_c^T] (128 frequencies x K = 128) and
+// B = [Re C_t | Im C_t] (N = 64 x K = 128):
+//   Re Z^T = A[:, :64] Re C^T - A[:, 64:] Im C^T   (B's second K half negated),
+//   Im Z^T = A[:, :64] Im C^T + A[:, 64:] Re C^T   (B's K halves swapped),
+// two GEMMs of M = 128, N = 64, K = 128 per rank term.  Operands are split
+// as hi + lo in bf16 and the products hi*hi + hi*lo + lo*hi are accumulated
+// in fp32 (about 2^-17 per product; the inner operator only steers GMRES,
+// whose restarts recompute the residual in float-float).
+//
+// Layout and roles (one CTA per work item: a row cluster and a run of its far
+// blocks; 1 CTA per SM, which owns the 512 TMEM columns):
+//   TMEM columns [0, 256): A, two buffers of 128 (bf16 hi 64 + lo 64; lane l
+//     holds frequency l0 + l, two bf16 per column, lower K in the low half);
+//   TMEM columns [256, 512): accumulators, two buffers of 128 (Re Z^T 64 +
+//     Im Z^T 64 columns, one per mu).
+//   shared memory: a ring of NSTAGE B images of 32 KB, copied whole from the
+//     precomputed images in HBM by one bulk copy each (warp 9); an image holds
+//     the hi and lo planes of [Re C_t | Im C_t] in the canonical K-major
+//     layout without swizzle (core matrices of 8 rows x 16 bytes, K-adjacent
+//     ones 128 bytes apart, 8-row groups 2048 bytes apart).
+//   warps 4-7 build A for each block from xhat_c (one lane per frequency);
+//   warp 8 (one thread) issues 48 MMAs per rank term and frees each B stage,
+//     accumulator and A buffer with tcgen05.commit;
+//   warps 0-3 read each term's accumulator (one lane per frequency), multiply
+//     by d_t[l] and keep the row's sum over all terms in registers, then write
+//     the item's partial tile, which the per-row reduction adds in item order.
+// Frequencies go in chunks of 128 lanes (the last one padded); when Ls mod 128
+// is 1 to TAIL_MAX the remaining frequencies are applied from an FP32 table of
+// the expanded couplings S_b(l) = sum_t d_t[l] C_t instead (k_far_tail_f32).
+// Every wait of the main loop has the handle's time limit; on expiry the kernel
+// records it, stops issuing work, lets issued copies and MMAs drain, frees its
+// tensor memory and returns (the drain waits keep the one-second default).
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "handle.cuh"
+#include "umma.cuh"
+
+namespace cqm {
+
+namespace {
+constexpr int TP = 64;                 // Chebyshev points per cluster (m = 4)
+constexpr int NSTAGE = 6;              // B stages
+constexpr uint32_t BIMG = 32768;       // bytes of one B image (hi + lo planes)
+constexpr uint32_t BPLANE = 16384;     // one plane: 64 rows x 128 bf16
+constexpr uint32_t B_SBO = 2048;       // 8-row groups
+constexpr uint32_t B_LBO = 128;        // K-adjacent core matrices
+constexpr int NTHREADS = 320;          // warps 0-3 epilogue, 4-7 A, 8 MMA, 9 loader
+constexpr int W_A0 = 4, W_MMA = 8, W_LOAD = 9;
+constexpr uint32_t TCOLS = 512;
+constexpr uint32_t ACC0 = 256;         // first accumulator column
+constexpr int ERR_TIMEOUT = 1;
+constexpr size_t SMEM = (size_t)NSTAGE * BIMG + 1024;
+}  // namespace
+
+constexpr int TC2_TAIL_MAX = 4;
+
+// Byte offset of element (row, k) in one plane of a B image.
+__host__ __device__ constexpr uint32_t bimg_off(int row, int k) {
+  return (uint32_t)((row >> 3) * B_SBO + (k >> 3) * B_LBO + (row & 7) * 16 + (k & 7) * 2);
+}
+
+__device__ __forceinline__ void split_bf16(float x, uint16_t& hi, uint16_t& lo) {
+  const __nv_bfloat16 h = __float2bfloat16_rn(x);
+  const __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
+  hi = __bfloat16_as_ushort(h);
+  lo = __bfloat16_as_ushort(l);
+}
+
+// B images of every rank term: image (b, t) at (first[b] + t) * BIMG bytes,
+// element (mu, k) = Re C_t[mu][k] (k < 64) or Im C_t[mu][k - 64], split into
+// the hi and lo planes.  One block per (term, block).
+__global__ void __launch_bounds__(256) k_tc2_images(int cap, const int* __restrict__ rank,
+                                                    const int64_t* __restrict__ first,
+                                                    const double2* __restrict__ C,
+                                                    unsigned char* __restrict__ img) {
+  const int b = blockIdx.y, t = blockIdx.x;
+  if (t >= rank[b]) return;
+  const double2* Ct = C + ((size_t)b * cap + t) * TP * TP;
+  unsigned char* dst = img + (size_t)(first[b] + t) * BIMG;
+  for (int e = threadIdx.x; e < TP * 128; e += blockDim.x) {
+    const int mu = e >> 7, k = e & 127;
+    const double2 c = Ct[mu * TP + (k & 63)];
+    uint16_t hi, lo;
+    split_bf16((float)(k < 64 ? c.x : c.y), hi, lo);
+    const uint32_t o = bimg_off(mu, k);
+    *(uint16_t*)(dst + o) = hi;
+    *(uint16_t*)(dst + BPLANE + o) = lo;
+  }
+}
+
+// Expanded couplings of the tail frequencies: S[(b * ntail + f) * 4096 + mu * 64 + nu]
+// = sum_t d_t[l0 + f] C_t[mu][nu] (FP32 from the FP64 factors).
+__global__ void __launch_bounds__(256) k_tc2_tail_table(int Ls, int cap, int l0, int ntail,
+                                                        const int* __restrict__ rank,
+                                                        const double2* __restrict__ C,
+                                                        const double2* __restrict__ D,
+                                                        float2* __restrict__ S) {
+  const int b = blockIdx.x;
+  const int rk = rank[b];
+  for (int e = threadIdx.x; e < TP * TP * ntail; e += blockDim.x) {
+    const int f = e / (TP * TP), en = e - f * TP * TP;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int t = 0; t < rk; ++t)
+      cfma(acc, C[((size_t)b * cap + t) * TP * TP + en], D[((size_t)b * cap + t) * Ls + l0 + f]);
+    S[((size_t)b * ntail + f) * TP * TP + en] = make_float2((float)acc.x, (float)acc.y);
+  }
+}
+
+// Tail frequencies: yhat_r(l)[mu] += sum over the far blocks (r, c) of row r of
+// sum_nu S_b(l)[mu][nu] xhat_c(l)[nu].  One warp per (far row, tail frequency),
+// lane owns mu = lane and lane + 32.
+__global__ void __launch_bounds__(256) k_far_tail_f32(int Ls, int l0, int ntail, int nrows,
+                                                      const int* __restrict__ rows,
+                                                      const int* __restrict__ rowptr,
+                                                      const int2* __restrict__ rc,
+                                                      const float2* __restrict__ S,
+                                                      const float2* __restrict__ xhat,
+                                                      float2* __restrict__ yhat) {
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (w >= nrows * ntail) return;
+  const int k = w / ntail, f = w - k * ntail, l = l0 + f;
+  const int r = rows[k];
+  float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
+  for (int bi = rowptr[r]; bi < rowptr[r + 1]; ++bi) {
+    const float2* xc = xhat + (size_t)rc[bi].y * TP * Ls + l;
+    const float2 x0 = xc[(size_t)lane * Ls], x1 = xc[(size_t)(lane + 32) * Ls];
+    const float2* Sb = S + ((size_t)bi * ntail + f) * TP * TP;
+    for (int nu = 0; nu < TP; ++nu) {
+      const float2 xv = make_float2(__shfl_sync(0xffffffffu, nu < 32 ? x0.x : x1.x, nu & 31),
+                                    __shfl_sync(0xffffffffu, nu < 32 ? x0.y : x1.y, nu & 31));
+      cfma(a0, Sb[lane * TP + nu], xv);
+      cfma(a1, Sb[(lane + 32) * TP + nu], xv);
+    }
+  }
+  float2* yr = yhat + (size_t)r * TP * Ls + l;
+  yr[(size_t)lane * Ls] = cadd(yr[(size_t)lane * Ls], a0);
+  yr[(size_t)(lane + 32) * Ls] = cadd(yr[(size_t)(lane + 32) * Ls], a1);
+}
+
+// Position in the sequence (chunk, block, term) of an item, blocks of rank 0
+// skipped; done() once the chunks are exhausted.
+struct Seq {
+  int ch, bi, t;
+  int b0, b1, nch;
+  const int* rank;
+  __device__ void start(int b0_, int b1_, int nch_, const int* rank_) {
+    b0 = b0_; b1 = b1_; nch = nch_; rank = rank_;
+    ch = 0;
+    bi = b0;
+    t = 0;
+    skip();
+  }
+  __device__ void skip() {
+    while (ch < nch) {
+      while (bi < b1 && rank[bi] == 0) ++bi;
+      if (bi < b1) return;
+      ++ch;
+      bi = b0;
+    }
+  }
+  __device__ bool done() const { return ch >= nch; }
+  // advance by one term; returns true if the block changed
+  __device__ bool next() {
+    if (++t < rank[bi]) return false;
+    t = 0;
+    ++bi;
+    skip();
+    return true;
+  }
+};
+
+__global__ void __launch_bounds__(NTHREADS, 1)
+    k_far_coupling_tc2(int Ls, int nch, int cap, const int4* __restrict__ items,
+                       const int2* __restrict__ blocks, const int* __restrict__ rank,
+                       const int64_t* __restrict__ first, const unsigned char* __restrict__ img,
+                       const float2* __restrict__ Df, const float2* __restrict__ xhat,
+                       float2* __restrict__ part, int* __restrict__ err, uint64_t lim, int probe) {
+  using namespace umma;
+  extern __shared__ unsigned char smraw[];
+  __shared__ __align__(8) uint64_t b_full[NSTAGE], b_empty[NSTAGE];
+  __shared__ __align__(8) uint64_t a_full[2], a_empty[2];
+  __shared__ __align__(8) uint64_t c_full[2], c_empty[2];
+  __shared__ __align__(8) uint64_t fin_bar, probe_bar;
+  __shared__ uint32_t tmem_sh;
+  __shared__ volatile int abort_sh;
+  __shared__ volatile int never_sh;
+  unsigned char* ring = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int4 it = items[blockIdx.x];  // (row, first block, end block, -)
+
+  if (tid == 0) {
+    for (int s = 0; s < NSTAGE; ++s) {
+      mbar_init(&b_full[s], 1);
+      mbar_init(&b_empty[s], 1);
+    }
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(&a_full[s], 4);  // one arrival per A warp
+      mbar_init(&a_empty[s], 1);
+      mbar_init(&c_full[s], 1);
+      mbar_init(&c_empty[s], 4);  // one arrival per epilogue warp
+    }
+    mbar_init(&fin_bar, 1);
+    mbar_init(&probe_bar, 1);
+    abort_sh = 0;
+    never_sh = 0;
+    mbar_init_fence();
+  }
+  if (warp == W_MMA) tmem_alloc(&tmem_sh, TCOLS);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_sh;
+  // failure-path check armed from the host: a wait on a barrier nothing completes
+  if (probe && blockIdx.x == 0 && warp == W_MMA) mbar_wait(&probe_bar, 0u, &abort_sh, err, ERR_TIMEOUT, lim);
+
+  uint32_t n_issued = 0;  // loader: images copied
+  if (warp == W_MMA) {
+    // -------------------------------------------------------------- MMA issue
+    constexpr uint32_t ID_RE = idesc_bf16(128, 64, false);
+    constexpr uint32_t ID_NEG = idesc_bf16(128, 64, true);
+    Seq q;
+    q.start(it.y, it.z, nch, rank);
+    uint32_t ib = 0, ia = 0;
+    bool first_term = true;
+    while (!q.done()) {
+      const int s = (int)(ib % NSTAGE), cb = (int)(ib & 1u), ab = (int)(ia & 1u);
+      bool ok = mbar_wait(&b_full[s], (ib / NSTAGE) & 1u, &abort_sh, err, ERR_TIMEOUT, lim);
+      if (first_term) ok = mbar_wait(&a_full[ab], (ia >> 1) & 1u, &abort_sh, err, ERR_TIMEOUT, lim) && ok;
+      if (ib >= 2) ok = mbar_wait(&c_empty[cb], ((ib >> 1) - 1) & 1u, &abort_sh, err, ERR_TIMEOUT, lim) && ok;
+      ok = __all_sync(0xffffffffu, ok);
+      tc_fence_after();
+      const bool last_term = q.t + 1 == rank[q.bi];
+      if (lane == 0) {
+        if (ok) {
+          const uint32_t a_hi = tmem + 128u * ab, a_lo = a_hi + 64u;
+          const uint32_t zr = tmem + ACC0 + 128u * cb, zi = zr + 64u;
+          const uint32_t bh = smem_u32(ring + (size_t)s * BIMG), bl = bh + BPLANE;
+          // products hi*hi, hi*lo, lo*hi over K = 128 in 8 steps of 16
+#pragma unroll
+          for (int pr = 0; pr < 3; ++pr) {
+            const uint32_t aa = pr == 2 ? a_lo : a_hi;
+            const uint32_t bb = pr == 1 ? bl : bh;
+#pragma unroll
+            for (int ks = 0; ks < 8; ++ks) {
+              const uint32_t acc = (pr == 0 && ks == 0) ? 0u : 1u;
+              mma_bf16_ts(zr, aa + 8u * ks, sdesc_lbo_sbo(bb + 256u * ks, B_LBO, B_SBO),
+                          ks < 4 ? ID_RE : ID_NEG, acc);
+              mma_bf16_ts(zi, aa + 8u * ks, sdesc_lbo_sbo(bb + 256u * ((ks + 4) & 7), B_LBO, B_SBO),
+                          ID_RE, acc);
+            }
+          }
+        }
+        mma_commit(&b_empty[s]);
+        mma_commit(&c_full[cb]);
+        if (last_term) mma_commit(&a_empty[ab]);
+      }
+      __syncwarp();
+      ++ib;
+      const bool newblock = q.next();
+      if (newblock) ++ia;
+      first_term = newblock;
+    }
+  } else if (warp == W_LOAD) {
+    // ------------------------------------------------------------ B loader
+    if (lane == 0) {
+      Seq q;
+      q.start(it.y, it.z, nch, rank);
+      for (; !q.done(); q.next(), ++n_issued) {
+        const int s = (int)(n_issued % NSTAGE);
+        if (n_issued >= NSTAGE &&
+            !mbar_wait(&b_empty[s], (n_issued / NSTAGE - 1) & 1u, &abort_sh, err, ERR_TIMEOUT, lim))
+          break;
+        mbar_arrive_expect_tx(&b_full[s], BIMG);
+        bulk_g2s(ring + (size_t)s * BIMG, img + (size_t)(first[q.bi] + q.t) * BIMG, BIMG, &b_full[s]);
+      }
+    }
+    __syncwarp();
+  } else if (warp >= W_A0 && warp < W_A0 + 4) {
+    // ------------------------------------------------------------ A builders
+    const int qd = warp & 3;
+    const uint32_t trow = tmem + ((uint32_t)(32 * qd) << 16);
+    Seq q;
+    q.start(it.y, it.z, nch, rank);
+    uint32_t ia = 0;
+    while (!q.done()) {
+      const int ab = (int)(ia & 1u);
+      if (ia >= 2) mbar_wait(&a_empty[ab], ((ia >> 1) - 1) & 1u, &abort_sh, err, ERR_TIMEOUT, lim);
+      const bool go = !__any_sync(0xffffffffu, abort_sh != 0);
+      if (go) {
+        tc_fence_after();
+        const int l = 128 * q.ch + 32 * qd + lane;
+        const float2* xc = xhat + (size_t)blocks[q.bi].y * TP * Ls + l;
+        // K order: 0..63 Re xhat[nu], 64..127 Im xhat[nu]; two bf16 per column
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {  // half 0: K 0..63 (Re), 1: K 64..127 (Im)
+#pragma unroll
+          for (int c16 = 0; c16 < 2; ++c16) {  // 16 columns = 32 K values per store
+            uint32_t vh[16], vl[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const int nu0 = 32 * c16 + 2 * j;
+              float x0 = 0.f, x1 = 0.f;
+              if (l < Ls) {
+                const float2 p0 = xc[(size_t)nu0 * Ls], p1 = xc[(size_t)(nu0 + 1) * Ls];
+                x0 = half ? p0.y : p0.x;
+                x1 = half ? p1.y : p1.x;
+              }
+              uint16_t h0, l0v, h1, l1v;
+              split_bf16(x0, h0, l0v);
+              split_bf16(x1, h1, l1v);
+              vh[j] = (uint32_t)h0 | ((uint32_t)h1 << 16);
+              vl[j] = (uint32_t)l0v | ((uint32_t)l1v << 16);
+            }
+            const uint32_t col = 128u * ab + 32u * half + 16u * c16;
+            tmem_st16(trow + col, vh);
+            tmem_st16(trow + col + 64u, vl);
+          }
+        }
+        tmem_wait_st();
+        tc_fence_before();
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&a_full[ab]);
+      ++ia;
+      // skip to the next block (or chunk)
+      const int bcur = q.bi, ccur = q.ch;
+      while (!q.done() && q.bi == bcur && q.ch == ccur) q.next();
+    }
+  } else if (warp < 4) {
+    // ------------------------------------------------------------- epilogue
+    const int qd = warp;
+    const uint32_t trow = tmem + ((uint32_t)(32 * qd) << 16);
+    float yr[TP], yi[TP];
+#pragma unroll
+    for (int mu = 0; mu < TP; ++mu) yr[mu] = yi[mu] = 0.f;
+    Seq q;
+    q.start(it.y, it.z, nch, rank);
+    uint32_t ic = 0;
+    int ch_cur = q.done() ? nch : q.ch;
+    auto flush = [&](int ch) {  // the item's partial tile of chunk ch
+      const int l = 128 * ch + 32 * qd + lane;
+      if (l < Ls) {
+        float2* dst = part + (size_t)blockIdx.x * TP * Ls + l;
+#pragma unroll
+        for (int mu = 0; mu < TP; ++mu) dst[(size_t)mu * Ls] = make_float2(yr[mu], yi[mu]);
+      }
+#pragma unroll
+      for (int mu = 0; mu < TP; ++mu) yr[mu] = yi[mu] = 0.f;
+    };
+    // chunks before the first term (none for items with work) and empty items
+    for (int ch = 0; ch < ch_cur; ++ch) flush(ch);
+    while (!q.done()) {
+      const int cb = (int)(ic & 1u);
+      bool ok = mbar_wait(&c_full[cb], (ic >> 1) & 1u, &abort_sh, err, ERR_TIMEOUT, lim);
+      ok = __all_sync(0xffffffffu, ok);
+      tc_fence_after();
+      const int l = 128 * q.ch + 32 * qd + lane;
+      const float2 d = (l < Ls) ? Df[((size_t)q.bi * cap + q.t) * Ls + l] : make_float2(0.f, 0.f);
+      if (ok) {
+        const uint32_t zr = trow + ACC0 + 128u * cb, zi = zr + 64u;
+#pragma unroll
+        for (int m0 = 0; m0 < TP; m0 += 16) {
+          uint32_t vr[16], vi[16];
+          tmem_ld16(zr + (uint32_t)m0, vr);
+          tmem_ld16(zi + (uint32_t)m0, vi);
+          tmem_wait_ld();
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const float a = __uint_as_float(vr[j]), bq = __uint_as_float(vi[j]);
+            yr[m0 + j] = fmaf(d.x, a, fmaf(-d.y, bq, yr[m0 + j]));
+            yi[m0 + j] = fmaf(d.x, bq, fmaf(d.y, a, yi[m0 + j]));
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&c_empty[cb]);
+      ++ic;
+      q.next();
+      const int ch_next = q.done() ? nch : q.ch;
+      for (; ch_cur < ch_next; ++ch_cur) flush(ch_cur);
+    }
+    for (; ch_cur < nch; ++ch_cur) flush(ch_cur);
+  }
+  // ------------------------------------------------------------------ teardown
+  __syncthreads();
+  if (warp == W_LOAD && lane == 0) {
+    // every copy issued has landed before the CTA's shared memory is released
+    const uint32_t from = n_issued > NSTAGE ? n_issued - NSTAGE : 0;
+    for (uint32_t u = from; u < n_issued; ++u)
+      mbar_wait(&b_full[u % NSTAGE], (u / NSTAGE) & 1u, &never_sh, err, ERR_TIMEOUT);
+  }
+  if (warp == W_MMA) {
+    // every MMA issued has finished before TMEM is released
+    if (lane == 0) mma_commit(&fin_bar);
+    __syncwarp();
+    mbar_wait(&fin_bar, 0u, &never_sh, err, ERR_TIMEOUT);
+    tc_fence_after();
+    __syncwarp();
+    tmem_dealloc(tmem, TCOLS);
+  }
+}
+
+// Chunks of 128 frequencies on the tensor cores and the tail frequencies
+// applied from the expanded FP32 table.
+static void tc2_split(int Ls, int& nch, int& l_tail, int& ntail) {
+  const int rem = Ls % 128;
+  if (Ls > 128 && rem >= 1 && rem <= TC2_TAIL_MAX) {
+    nch = Ls / 128;
+    l_tail = 128 * nch;
+    ntail = rem;
+  } else {
+    nch = (Ls + 127) / 128;
+    l_tail = Ls;
+    ntail = 0;
+  }
+}
+
+int setup_tc2(cqm_handle* h) {
+  CQM_CUDA_TRY(cudaFuncSetAttribute(k_far_coupling_tc2, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)SMEM));
+  return CQM_OK;
+}
+
+// B images and tail table from the FP64 factors (before they become
+// float-float pairs).
+int build_tc2(cqm_handle* h) {
+  if (h->n_far == 0) return CQM_OK;
+  std::vector<int64_t> first(h->n_far + 1, 0);
+  for (int b = 0; b < h->n_far; ++b) first[b + 1] = first[b] + h->h_far_rank[b];
+  CQM_TRY(h->tc2_first.allocate(h->alloc, h->n_far + 1));
+  CQM_CUDA_TRY(cudaMemcpyAsync(h->tc2_first.p, first.data(), sizeof(int64_t) * (h->n_far + 1),
+                               cudaMemcpyHostToDevice, h->stream));
+  CQM_TRY(h->tc2_img.allocate(h->alloc, (size_t)std::max<int64_t>(1, first[h->n_far]) * BIMG));
+  {
+    ProfScope ps_(h, CQM_K_BASES);
+    dim3 g((unsigned)std::max(1, h->info.rank_max), (unsigned)h->n_far);
+    k_tc2_images<<<g, 256, 0, h->stream>>>(h->rank_cap, h->far_rank.p, h->tc2_first.p, h->farC.p,
+                                          h->tc2_img.p);
+  }
+  CQM_CHECK_LAUNCH();
+  int nch, l_tail, ntail;
+  tc2_split(h->Ls, nch, l_tail, ntail);
+  if (ntail > 0) {
+    CQM_TRY(h->tc2_tail.allocate(h->alloc, (size_t)h->n_far * ntail * TP * TP));
+    ProfScope ps_(h, CQM_K_BASES);
+    k_tc2_tail_table<<<h->n_far, 256, 0, h->stream>>>(h->Ls, h->rank_cap, l_tail, ntail, h->far_rank.p,
+                                                     h->farC.p, h->farD.p, h->tc2_tail.p);
+    CQM_CHECK_LAUNCH();
+  }
+  CQM_CUDA_TRY(cudaStreamSynchronize(h->stream));  // `first` goes out of scope
+  return CQM_OK;
+}
+
+// Writes the item partial tiles of frequencies [0, l_tail) and adds the tail
+// frequencies to yhat_f directly; returns the first tail frequency.
+int far_coupling_tc2(cqm_handle* h, int* l_tail_out) {
+  int nch, l_tail, ntail;
+  tc2_split(h->Ls, nch, l_tail, ntail);
+  {
+    ProfScope ps_(h, CQM_K_FAR_COUPLING);
+    k_far_coupling_tc2<<<h->n_far_items, NTHREADS, SMEM, h->stream>>>(
+        h->Ls, nch, h->rank_cap, h->far_items.p, h->far_rc.p, h->far_rank.p, h->tc2_first.p,
+        h->tc2_img.p, h->farD_f.p, h->xhat_f.p, h->part_f.p, h->flag.p + 1, h->wait_limit_ns,
+        h->wait_probe ? 1 : 0);
+    h->wait_probe = false;  // one-shot
+  }
+  CQM_CHECK_LAUNCH();
+  if (ntail > 0) {
+    const int nfr = (int)h->h_far_rows.size();
+    const int warps = nfr * ntail;
+    ProfScope ps_(h, CQM_K_FAR_COUPLING);
+    k_far_tail_f32<<<(unsigned)((warps + 7) / 8), 256, 0, h->stream>>>(
+        h->Ls, l_tail, ntail, nfr, h->d_far_rows.p, h->far_rowptr.p, h->far_rc.p, h->tc2_tail.p,
+        h->xhat_f.p, h->yhat_f.p);
+    CQM_CHECK_LAUNCH();
+  }
+  *l_tail_out = l_tail;
+  return CQM_OK;
+}
+
+}  // namespace cqm

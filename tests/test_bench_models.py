@@ -30,10 +30,14 @@ def test_factored_models_count_complex_macs(bench):
 
 
 def test_tensor_and_expanded_models(bench):
-    m = bench.kernel_models(dict(INFO, near_expanded=1, far_expanded=1), Ls=129, p=64, tensor_cores=1)
+    m = bench.kernel_models(dict(INFO, near_expanded=1, far_expanded=1), Ls=129, p=64, tensor_cores=2)
     assert m["far_coupling"]["bound"] == "tensor"
     peak, _ = bench.tf32_peak()
     assert m["far_coupling"]["peak"] == pytest.approx(peak)
+    m1 = bench.kernel_models(dict(INFO, near_expanded=1, far_expanded=1), Ls=129, p=64, tensor_cores=1)
+    pk, _ = bench._peaks()
+    assert m1["far_coupling"]["peak"] == pytest.approx(pk.get("bf16_tflops_sustained", pk["bf16_tflops"]))
+    assert m1["far_coupling"]["work"] == 8.0 * 1000 * 64 * 64 * 129
     assert m["near_apply"]["bound"] == "hbm" and m["near_apply"]["work"] == 8.0 * 8000 * 129
     assert m["near_exact"]["work"] == 16.0 * 8000 * 129
     assert m["far_exact"]["bound"] == "hbm" and m["far_exact"]["work"] == 16.0 * 20 * 4096 * 129

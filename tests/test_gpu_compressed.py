@@ -151,7 +151,7 @@ def test_compressed_solve_time_domain_1280(lib, ref1280, eps, tol):
 
 
 @pytest.mark.parametrize("precond,inner_fp32,tensor_cores",
-                         [(0, 0, 1), (1, 0, 1), (0, 1, 1), (1, 1, 1), (1, 1, 0)])
+                         [(0, 0, 1), (1, 0, 1), (0, 1, 1), (1, 1, 1), (1, 1, 2), (1, 1, 0)])
 def test_solver_variants_agree(lib, precond, inner_fp32, tensor_cores):
     """Preconditioning and the FP32 inner operator change the iteration, not
     the answer: every variant meets the FP64 residual target and agrees with
@@ -192,11 +192,11 @@ def test_point_cache_matches_direct_quadrature(lib):
     b.close()
 
 
-@pytest.mark.parametrize("tensor_cores", [0, 1])
+@pytest.mark.parametrize("tensor_cores", [0, 1, 2])
 def test_inner_operator_fp32_accuracy(lib, tensor_cores):
-    """The FP32 inner operator (SIMT, or TF32 tensor cores with the three-product
-    split) agrees with the FP64-accurate apply to FP32 accuracy, frequency by
-    frequency."""
+    """The inner operator (FP32 SIMT; bf16 or TF32 tensor cores with the
+    hi/lo three-product split) agrees with the FP64-accurate apply to 1e-5,
+    frequency by frequency (N = 40: one padded 128-frequency chunk)."""
     m = synth.icosphere(4)
     N, dt = 40, 0.1
     op = _op(m, dt, N, tensor_cores=tensor_cores)
@@ -206,8 +206,9 @@ def test_inner_operator_fp32_accuracy(lib, tensor_cores):
     yi = op.apply_inner(x)
     op.close()
     err = np.linalg.norm(yi - y, axis=1) / np.linalg.norm(y, axis=1)
-    # FP32-class: the three-product TF32 split keeps ~21 bits per operand; a
-    # wrong fragment layout would give errors of order one
+    # the three-product split keeps ~17 (bf16) or ~21 (TF32) bits per operand;
+    # a wrong fragment layout would give errors of order one
+    print(f"tensor_cores={tensor_cores}: max per-frequency error {np.max(err):.2e}")
     assert np.max(err) < 1e-5, err
 
 
