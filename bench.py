@@ -41,6 +41,25 @@ sys.path.insert(0, ROOT)
 # 3.4e-7.
 WORKLOAD = dict(name="sphere5120_N256", level=4, N=256, dt=0.1, bdf=2, eta=1.0, cheb_m=4,
                 n_min=32, aca_eps=1e-9)
+# Other workloads (--workload): the mixed-precision torus (major radius 1, minor
+# 0.3, 20480 triangles, n_u = 160, n_v = 64), BDF2, N = 1024, dt = 0.4 times the
+# mean edge length (Courant number 0.4); its per-step error is measured against
+# the same path with the MACA at 1e-10 (--step-error; 32 rank slots per block
+# are what the device holds at this size).
+WORKLOADS = {
+    "sphere5120_N256": WORKLOAD,
+    "torus20480_N1024": dict(name="torus20480_N1024", torus=20480, N=1024, courant=0.4, bdf=2,
+                             eta=1.0, cheb_m=4, n_min=32, aca_eps=1e-8, ref_eps=1e-10, ref_cap=32),
+}
+
+
+def workload_mesh(W):
+    """Mesh and time step of a workload."""
+    from paper_2006_05186_gb300 import synth
+    if "torus" in W:
+        m = synth.torus_for(W["torus"])
+        return m, W["courant"] * synth.mean_edge_length(m)
+    return synth.icosphere(W["level"]), W["dt"]
 METRIC = "CQM-BEM solve throughput (triangle·freq/s), p50/p99 latency at rel err ≤1e-6"
 UNIT = "triangle*freq/s"
 
@@ -282,9 +301,9 @@ def run_ours(args):
     from paper_2006_05186_gb300 import CqmBem, synth
     rank, world = dist_init(args.gpus)
     W = WORKLOAD
-    m = synth.icosphere(W["level"])
+    m, dt = workload_mesh(W)
     pulse = synth.plane_wave_pulse(seed=synth.SEED_BASE + rank)
-    N, dt = W["N"], W["dt"]
+    N = W["N"]
     L = N + 1
     Ls = L // 2 + 1
     M = m.nt
@@ -402,6 +421,11 @@ def run_ours(args):
         "peaks_source": src,
     }
     line["roofline_peaks"] = {"tf32_tflops": tf32_measured}
+    if args.step_error:
+        try:
+            line["step_error"] = step_error(m, dt, pulse, W, params, q)
+        except Exception as e:  # the reference did not fit or failed: report it
+            line["step_error"] = {"error": str(e)}
     if args.dense_baseline:
         line["dense_fp64_gpu"] = dense_baseline(m, pulse, W, q)
     if not args.no_cpu_baseline and world == 1:  # rank 0 at N = 1 only
@@ -417,13 +441,36 @@ def run_ours(args):
     print(json.dumps(line), flush=True)
 
 
+def step_error(m, dt, pulse, W, params, q):
+    """Error of the timed path per time step against the same solver with the
+    MACA at 1e-11 (its residuals are FP64-accurate; the path is pinned to the
+    oracle at smaller sizes): max_n and selected steps of
+    ||q_n - q_n^ref|| / max_n ||q_n^ref||."""
+    import torch
+    from paper_2006_05186_gb300 import CqmBem
+    N = W["N"]
+    kw = dict(params, aca_eps=W.get("ref_eps", 1e-11), rank_cap=W.get("ref_cap", 64), profile=0)
+    op = CqmBem(m.xyz, m.tri, dt, N, W["bdf"], **kw)
+    rhs = op.rhs_plane_wave(pulse.direction, pulse.width, pulse.delay)
+    qr = op.solve(rhs)
+    op.close()
+    torch.cuda.empty_cache()
+    a = q.cpu().numpy()
+    e = np.linalg.norm(a - qr, axis=1) / np.max(np.linalg.norm(qr, axis=1))
+    picks = sorted(set([0, N // 4, N // 2, 3 * N // 4, N, int(np.argmax(e))]))
+    return {"max": float(e.max()), "worst_step": int(np.argmax(e)),
+            "steps": {int(n): float(e[n]) for n in picks},
+            "reference": f"same path, MACA {kw['aca_eps']:g}, rank_cap {kw['rank_cap']}"}
+
+
 def dense_baseline(m, pulse, W, q_compressed):
     """One timed pass of the plain dense FP64 GPU path (dense V_l for every
     solved frequency, FP64 GMRES) on the same workload, and the time-domain
     difference of the two solutions (the H^2 interpolation error)."""
     import torch
     from paper_2006_05186_gb300 import CqmBem
-    N, dt = W["N"], W["dt"]
+    N = W["N"]
+    _, dt = workload_mesh(W)
     L, M = N + 1, m.nt
     rhs = torch.empty((L, M), dtype=torch.float64, device="cuda")
     qd = torch.empty((L, M), dtype=torch.float64, device="cuda")
@@ -457,14 +504,14 @@ def oracle_frequencies(freqs, workers=None):
     from paper_2006_05186_gb300 import synth
     W = WORKLOAD
     workers = workers or pool.default_workers()
-    m = synth.icosphere(W["level"])
+    m, dt = workload_mesh(W)
     p = synth.plane_wave_pulse()
     t0 = time.perf_counter()
     t = cluster.build_tree(m.xyz, m.tri, W["n_min"])
     near, far = cluster.partition(t, W["eta"])
-    b = incident.rhs_plane_wave(m.xyz, m.tri, W["N"], W["dt"], p.direction, p.width, p.delay)
+    b = incident.rhs_plane_wave(m.xyz, m.tri, W["N"], dt, p.direction, p.width, p.delay)
     g = cqm.forward(b, cqm.default_R(W["N"]))[freqs]
-    s = cqm.frequencies(W["N"], W["dt"], W["bdf"])[freqs]
+    s = cqm.frequencies(W["N"], dt, W["bdf"])[freqs]
     q = pool.h2_solve_frequencies(m.xyz, m.tri, s, t, near, far, W["cheb_m"], g, workers=workers)
     return q, time.perf_counter() - t0, workers
 
@@ -478,7 +525,7 @@ def cpu_baseline():
     W = WORKLOAD
     L = W["N"] + 1
     Ls = L // 2 + 1
-    M = 20 * 4 ** W["level"]
+    M = workload_mesh(W)[0].nt
     f1, f2 = [Ls // 2], [0, Ls - 1]
     q1, t1, workers = oracle_frequencies(f1)
     q2, t2, _ = oracle_frequencies(f2)
@@ -506,7 +553,7 @@ def run_reference(args):
         if i >= args.warmup:
             times.append(time.perf_counter() - t0)
     W = WORKLOAD
-    M = 20 * 4 ** W["level"]
+    M = workload_mesh(W)[0].nt
     L = W["N"] + 1
     line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -517,6 +564,110 @@ def run_reference(args):
             "cpu_baseline": cb,
             "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def draw_requests(kind, count, seed0=20060518):
+    """Seeded scatterers of the batched and serving workloads.  Draws per
+    request, in this order, from numpy.random.default_rng(seed0 + i): shape,
+    size, N, semi-axes (ellipsoid), direction (serving), width, delay."""
+    from paper_2006_05186_gb300 import synth
+    out = []
+    for i in range(count):
+        rng = np.random.default_rng(seed0 + i)
+        if kind == "batch":
+            shape = ["sphere", "ellipsoid", "cube"][rng.integers(3)]
+            level = [2, 3, 4][rng.integers(3)]
+            N = [64, 128, 256, 512][rng.integers(4)]
+        else:
+            shape = ["sphere", "ellipsoid", "torus"][rng.integers(3)]
+            level = [3, 4][rng.integers(2)]
+            N = [128, 256, 512][rng.integers(3)]
+        axes = rng.uniform(0.5, 2.0, 3)
+        if shape == "sphere":
+            m = synth.icosphere(level)
+        elif shape == "ellipsoid":
+            m = synth.ellipsoid(level, axes)
+        elif shape == "cube":
+            m = synth.rounded_cube(level)
+        else:
+            m = synth.torus_for(20 * 4 ** level)
+        if kind == "batch":
+            d = np.array([0.0, 0.0, 1.0])
+            w = 0.5
+        else:
+            d = rng.standard_normal(3)
+            d /= np.linalg.norm(d)
+            w = float(rng.uniform(0.2, 1.0))
+        size = float(np.max(np.linalg.norm(m.xyz, axis=1)))
+        delay = size + 4.0 * w + float(rng.uniform(0.0, w))
+        out.append(dict(shape=shape, m=m, N=N, dt=0.4 * synth.mean_edge_length(m), dir=d, width=w,
+                        delay=delay))
+    return out
+
+
+def serve_requests(reqs, workers, arrivals=None):
+    """Runs the requests through a server; returns per-request infos and the
+    wall time from the first submit to the last result."""
+    from paper_2006_05186_gb300 import Server
+    srv = Server(workers=workers)
+    t0 = time.perf_counter()
+    tickets = []
+    for k, r in enumerate(reqs):
+        if arrivals is not None:
+            wait = t0 + arrivals[k] - time.perf_counter()
+            if wait > 0:
+                time.sleep(wait)
+        tickets.append(srv.submit(r["m"].xyz, r["m"].tri, r["dt"], r["N"], direction=r["dir"],
+                                  width=r["width"], delay=r["delay"], aca_eps=1e-9, expand_far=0))
+    infos = []
+    for t in tickets:
+        code, _, info = srv.poll(t)
+        if code != 0:
+            raise RuntimeError(f"request {t} failed with status {code}")
+        infos.append(info)
+    wall = time.perf_counter() - t0
+    srv.close()
+    return infos, wall
+
+
+def run_many(args):
+    """Batched (64 seeded scatterers, all submitted at once) or serving
+    (a Poisson stream of seeded requests, mean 20 per second) through the
+    request server, against the same requests run one at a time."""
+    import torch
+    torch.cuda.set_device(0)
+    kind = "batch" if args.workload == "batch64" else "serve"
+    count = 64 if kind == "batch" else args.requests
+    reqs = draw_requests(kind, count)
+    units = sum(r["m"].nt * (r["N"] + 1) for r in reqs)
+    arrivals = None
+    if kind == "serve":
+        gaps = np.random.default_rng(20060518 + 999).exponential(1.0 / 20.0, count)
+        arrivals = np.cumsum(gaps) - gaps[0]
+    serve_requests(reqs[:2], 1)  # warm-up: module load, pools
+    torch.cuda.synchronize()
+    with ClockSampler(0) as clk:
+        infos, wall = serve_requests(reqs, args.workers, arrivals)
+    seq_infos, seq_wall = serve_requests(reqs, 1, arrivals)
+    lat = sorted(i["t_total_ms"] for i in infos)
+    slat = sorted(i["t_total_ms"] for i in seq_infos)
+    pct = lambda v, q: v[min(len(v) - 1, int(q * len(v)))]
+    line = {
+        "metric": METRIC, "value": units / wall, "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 1,
+        "ms_per_step": 1e3 * wall, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "mixed (as the single-solve line)", "data": "synthetic",
+        "config": {"workload": args.workload, "requests": count, "workers": args.workers,
+                   "triangles": [r["m"].nt for r in reqs], "N": [r["N"] for r in reqs],
+                   "shapes": [r["shape"] for r in reqs], "aca_eps": 1e-9, "expand_far": 0,
+                   "arrivals": "Poisson, mean 20/s" if kind == "serve" else "all at t = 0"},
+        "latency_ms": {"p50": pct(lat, 0.5), "p99": pct(lat, 0.99)},
+        "sequential": {"value": units / seq_wall, "unit": UNIT, "seconds": seq_wall,
+                       "latency_ms": {"p50": pct(slat, 0.5), "p99": pct(slat, 0.99)},
+                       "note": "the same requests through one worker (one at a time)"},
+        "max_rel_residual": max(i["solve"]["max_rel_residual"] for i in infos),
+        "clocks": clk.summary(),
+    }
     print(json.dumps(line), flush=True)
 
 
@@ -533,9 +684,21 @@ def main():
     ap.add_argument("--level", type=int, default=None,
                     help="icosphere level override (smaller cases for profiler captures)")
     ap.add_argument("--N", type=int, default=None, help="time-step count override")
-    ap.add_argument("--tensor-cores", type=int, choices=[0, 1], default=None,
-                    help="far-field coupling on the TF32 tensor cores (1) or FP32 SIMT (0)")
+    ap.add_argument("--tensor-cores", type=int, choices=[0, 1, 2], default=None,
+                    help="far-field coupling on the tensor cores in bf16 (1), TF32 (2), or FP32 SIMT (0)")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batch64", "serve"],
+                    default="sphere5120_N256")
+    ap.add_argument("--workers", type=int, default=6, help="server workers (batch64, serve)")
+    ap.add_argument("--requests", type=int, default=40, help="requests of the serving stream")
+    ap.add_argument("--step-error", action="store_true",
+                    help="also solve with the MACA at 1e-11 and report the error per time step")
     args = ap.parse_args()
+    if args.workload in ("batch64", "serve"):
+        run_many(args)
+        return
+    if args.workload != "sphere5120_N256":
+        WORKLOAD.clear()
+        WORKLOAD.update(WORKLOADS[args.workload])
     if args.level is not None:
         WORKLOAD["level"] = args.level
         WORKLOAD["name"] = f"sphere{20 * 4 ** args.level}_N{WORKLOAD['N']}"

@@ -51,6 +51,7 @@ extern "C" {
 #define CQM_ETIMEOUT  4   /* a bounded device wait gave up */
 #define CQM_ECUDA     5   /* a CUDA runtime error; see cqm_bem_last_error() */
 #define CQM_ECAPACITY 6   /* a fixed device capacity (rank slots, block lists) was exceeded */
+#define CQM_EPENDING  7   /* a submitted request is still queued or running (cqm_bem_poll) */
 
 /* Largest step count N: the transforms hold 24 (N + 1) bytes of twiddle and
  * R-power tables in one CTA's shared memory (at most 227 KB). */
@@ -124,7 +125,8 @@ typedef struct cqm_params {
   int32_t expand_near;    /* H2MACA: after the MACA, expand every near block per
                              frequency (sum_t C_t d_t, FP64 with an FP32 copy,
                              Ls x #near entries x 24 bytes) and apply the near
-                             field from it; 0 = apply it from the factors  [1]   */
+                             field from it, if that takes at most a quarter of
+                             the device memory; 0 = apply it from the factors [1] */
   int32_t expand_far;     /* H2MACA with exact_ff: expand every far coupling per
                              frequency (sum_t C_t d_t, float-float, Ls x p^2 x 16
                              bytes per far block) for the FP64-accurate apply,
@@ -359,6 +361,79 @@ int cqm_cluster_tree_noalloc(const double* xyz, int32_t nv, const int32_t* tri, 
                              int32_t n_min, int32_t* perm, int32_t* begin, int32_t* end,
                              int32_t* son0, int32_t* son1, int32_t* parent, int32_t* level,
                              double* lo, double* hi, int32_t* n_nodes, void* cuda_stream);
+
+/* ---- Serving: many scattering problems on one GPU ---------------------- */
+
+/* The decoupled solve treats each frequency independently (Sec. 6.2), and
+ * each scattering problem is independent of the others; a server runs many
+ * problems concurrently on one GPU.  Each worker thread owns a CUDA stream and
+ * runs setup (Alg. 3) and solve of one request at a time, so requests that
+ * arrive while others are on the GPU start as soon as a worker and device
+ * memory are free, and their kernels overlap on the device.  Requests are
+ * admitted by their estimated device footprint (cqm_bem_estimate_bytes)
+ * against the server's byte budget, first fit in arrival order; a request
+ * runs with the same kernels and parameters it would have alone, so its
+ * result is the same alone and in the mix.  Device memory comes from the
+ * stream-ordered CUDA pool (a request's params.allocator is ignored). */
+typedef struct cqm_server cqm_server;
+
+/* One scattering problem.  mesh, rhs: copied at submit.  rhs: (N+1) x nt
+ * host float64 Galerkin data, or NULL to use the plane-wave pulse
+ * (dir, width, delay as in cqm_bem_rhs_plane_wave).  params: NULL = defaults
+ * with expand_far = 0 (the expanded far table trades a large footprint for a
+ * faster residual; a server favours concurrency). */
+typedef struct cqm_request {
+  cqm_mesh mesh;
+  double dt;
+  int32_t N, bdf_order;
+  const cqm_params* params;
+  const double* rhs;
+  double dir[3];
+  double width, delay;
+} cqm_request;
+
+/* Result of a request (filled by cqm_bem_poll). */
+typedef struct cqm_result_info {
+  int32_t status;               /* status of setup and solve */
+  int32_t worker;               /* worker thread that ran it */
+  int64_t bytes_estimate;       /* reserved at admission */
+  int64_t device_bytes;         /* held by the handle after setup */
+  double t_queue_ms;            /* submit -> admitted */
+  double t_setup_ms, t_solve_ms;
+  double t_total_ms;            /* submit -> done */
+  cqm_solve_info solve;
+} cqm_result_info;
+
+/* Upper estimate of the device memory of a request: every rank slot of the
+ * factors, their FP32 and bf16 copies, the quadrature point cache of the
+ * setup, the preconditioner, the solver workspace and the expanded tables the
+ * setup would admit.  Per triangle it uses bounds of the partition of closed
+ * surfaces with leaves of n_min triangles (at most 1000 near-field entries
+ * and 2.5 far blocks per triangle).  Errors: CQM_EINVAL. */
+int cqm_bem_estimate_bytes(int32_t nt, int32_t N, const cqm_params* params, int64_t* bytes);
+
+/* workers >= 1 threads on the current device; byte_budget > 0 bytes of
+ * device memory for admitted requests, or 0 for 90% of the free memory.
+ * Errors: CQM_EINVAL, CQM_ECUDA. */
+int cqm_server_create(int32_t workers, int64_t byte_budget, cqm_server** out);
+
+/* Queue a request; *ticket identifies it.  Returns CQM_ENOMEM (and queues
+ * nothing) when its estimate exceeds the whole budget, CQM_EINVAL for bad
+ * arguments (checked as in cqm_bem_setup). */
+int cqm_bem_submit(cqm_server* s, const cqm_request* req, int64_t* ticket);
+
+/* Result of a request.  wait = 0 returns CQM_EPENDING while it is queued or
+ * running; wait != 0 blocks until it is done.  When done: density (host,
+ * (N+1) x nt, may be NULL) and info (may be NULL) are filled, the request is
+ * released, and the return value is its status.  Unknown ticket: CQM_EINVAL. */
+int cqm_bem_poll(cqm_server* s, int64_t ticket, int32_t wait, double* density, cqm_result_info* info);
+
+/* Bytes reserved by admitted requests now, and requests queued or running. */
+int cqm_server_load(cqm_server* s, int64_t* bytes_in_use, int32_t* queued, int32_t* running);
+
+/* Wait for every submitted request, stop the workers and free the server
+ * (results not polled are dropped).  NULL is accepted. */
+int cqm_server_destroy(cqm_server* s);
 
 #ifdef __cplusplus
 }

@@ -19,7 +19,7 @@ import numpy as np
 
 from . import build as _build
 
-CQM_OK, CQM_EINVAL, CQM_ENOMEM, CQM_ENOCONV, CQM_ETIMEOUT, CQM_ECUDA, CQM_ECAPACITY = range(7)
+CQM_OK, CQM_EINVAL, CQM_ENOMEM, CQM_ENOCONV, CQM_ETIMEOUT, CQM_ECUDA, CQM_ECAPACITY, CQM_EPENDING = range(8)
 MODE_DENSE, MODE_H2MACA = 0, 1
 MEM_HOST, MEM_DEVICE = 0, 1
 
@@ -31,6 +31,8 @@ EXPORTED = [
     "cqm_bem_solve_frequencies", "cqm_bem_forward_transform", "cqm_bem_inverse_transform",
     "cqm_bem_profile", "cqm_bem_profile_read", "cqm_bem_kernel_name",
     "cqm_cluster_tree_noalloc", "cqm_bem_set_wait_limit",
+    "cqm_bem_estimate_bytes", "cqm_server_create", "cqm_bem_submit", "cqm_bem_poll",
+    "cqm_server_load", "cqm_server_destroy",
 ]
 K_COUNT = 25
 
@@ -84,6 +86,22 @@ class cqm_solve_info(C.Structure):
     ]
 
 
+class cqm_request(C.Structure):
+    _fields_ = [
+        ("mesh", cqm_mesh), ("dt", C.c_double), ("N", C.c_int32), ("bdf_order", C.c_int32),
+        ("params", C.c_void_p), ("rhs", C.c_void_p), ("dir", C.c_double * 3),
+        ("width", C.c_double), ("delay", C.c_double),
+    ]
+
+
+class cqm_result_info(C.Structure):
+    _fields_ = [
+        ("status", C.c_int32), ("worker", C.c_int32), ("bytes_estimate", C.c_int64),
+        ("device_bytes", C.c_int64), ("t_queue_ms", C.c_double), ("t_setup_ms", C.c_double),
+        ("t_solve_ms", C.c_double), ("t_total_ms", C.c_double), ("solve", cqm_solve_info),
+    ]
+
+
 def _struct_dict(s):
     return {k: getattr(s, k) for k, _ in s._fields_}
 
@@ -132,6 +150,12 @@ def load(build_if_missing: bool = False):
         "cqm_bem_profile_read": (C.c_int, [vp, i32, vp, vp]),
         "cqm_bem_kernel_name": (C.c_char_p, [i32]),
         "cqm_bem_set_wait_limit": (C.c_int, [vp, i64, i32]),
+        "cqm_bem_estimate_bytes": (C.c_int, [i32, i32, C.POINTER(cqm_params), C.POINTER(i64)]),
+        "cqm_server_create": (C.c_int, [i32, i64, C.POINTER(vp)]),
+        "cqm_bem_submit": (C.c_int, [vp, C.POINTER(cqm_request), C.POINTER(i64)]),
+        "cqm_bem_poll": (C.c_int, [vp, i64, i32, vp, C.POINTER(cqm_result_info)]),
+        "cqm_server_load": (C.c_int, [vp, C.POINTER(i64), C.POINTER(i32), C.POINTER(i32)]),
+        "cqm_server_destroy": (C.c_int, [vp]),
         "cqm_cluster_tree_noalloc": (C.c_int, [vp, i32, vp, i32, i32] + [vp] * 9 + [C.POINTER(i32), vp]),
     }
     for name, (res, args) in sig.items():
@@ -379,6 +403,83 @@ class CqmBem:
                allow=(CQM_ENOCONV,) if allow_noconv else ())
         self.last_solve_info = _struct_dict(inf)
         return out
+
+
+def _result_dict(inf):
+    d = _struct_dict(inf)
+    d["solve"] = _struct_dict(inf.solve)
+    return d
+
+
+class Server:
+    """Concurrent scattering solves on the current GPU (cqm_server_*): worker
+    threads with one CUDA stream each, admission by estimated device bytes."""
+
+    def __init__(self, workers: int = 4, byte_budget: int = 0):
+        import torch
+        torch.cuda.current_device()  # the server runs on the current device
+        lib = load()
+        self._lib = lib
+        s = C.c_void_p()
+        _check(lib.cqm_server_create(int(workers), int(byte_budget), C.byref(s)), "server_create")
+        self._s = s
+        self._shapes = {}
+
+    def submit(self, xyz, tri, dt: float, N: int, bdf: int = 2, rhs=None, direction=(0.0, 0.0, 1.0),
+               width: float = 0.5, delay: float = 3.0, **params) -> int:
+        xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+        tri = np.ascontiguousarray(tri, dtype=np.int32)
+        req = cqm_request()
+        req.mesh = cqm_mesh(len(xyz), xyz.ctypes.data, len(tri), tri.ctypes.data)
+        req.dt, req.N, req.bdf_order = float(dt), int(N), int(bdf)
+        p = None
+        if params:
+            p = default_params(**dict(dict(expand_far=0), **params))
+            req.params = C.cast(C.pointer(p), C.c_void_p)
+        if rhs is not None:
+            rhs = np.ascontiguousarray(rhs, dtype=np.float64)
+            req.rhs = rhs.ctypes.data
+        req.dir = (C.c_double * 3)(*[float(v) for v in direction])
+        req.width, req.delay = float(width), float(delay)
+        t = C.c_int64()
+        _check(self._lib.cqm_bem_submit(self._s, C.byref(req), C.byref(t)), "submit")
+        self._shapes[t.value] = (int(N) + 1, len(tri))
+        return t.value
+
+    def poll(self, ticket: int, wait: bool = True):
+        """(status, density or None, info dict); status CQM_EPENDING while not done."""
+        shape = self._shapes[ticket]
+        out = np.zeros(shape)
+        inf = cqm_result_info()
+        code = self._lib.cqm_bem_poll(self._s, int(ticket), 1 if wait else 0, out.ctypes.data,
+                                      C.byref(inf))
+        if code == CQM_EPENDING:
+            return code, None, None
+        del self._shapes[ticket]
+        return code, out, _result_dict(inf)
+
+    def load(self):
+        b, q, r = C.c_int64(), C.c_int32(), C.c_int32()
+        _check(self._lib.cqm_server_load(self._s, C.byref(b), C.byref(q), C.byref(r)), "server_load")
+        return dict(bytes_in_use=b.value, queued=q.value, running=r.value)
+
+    def close(self):
+        if getattr(self, "_s", None):
+            self._lib.cqm_server_destroy(self._s)
+            self._s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def estimate_bytes(nt: int, N: int, **params) -> int:
+    p = default_params(**params)
+    b = C.c_int64()
+    _check(load().cqm_bem_estimate_bytes(int(nt), int(N), C.byref(p), C.byref(b)), "estimate_bytes")
+    return b.value
 
 
 def _like(x, shape, complex_: bool):

@@ -218,13 +218,24 @@ int cqm_bem_setup(const cqm_mesh* mesh, double dt, int32_t N, int32_t bdf_order,
       if ((st = build_maca(h)) != CQM_OK) break;
       if ((st = build_work_items(h)) != CQM_OK) break;
       if (p.precond && (st = build_precond(h)) != CQM_OK) break;
-      if (p.expand_near && !p.exact_ff && (st = build_near_expanded(h)) != CQM_OK) break;
+      // the expanded near field (Ls x near entries x 24 bytes) is admitted when it
+      // takes at most a quarter of the device memory; otherwise it stays factored
+      {
+        size_t free_b = 0, total_b = 0;
+        if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+          st = CQM_ECUDA;
+          break;
+        }
+        const double bytes = 24.0 * (double)h->Ls * (double)h->info.near_entries;
+        h->expand_near_ok = p.expand_near && bytes <= 0.25 * (double)total_b;
+      }
+      if (h->expand_near_ok && !p.exact_ff && (st = build_near_expanded(h)) != CQM_OK) break;
       if (p.inner_fp32) {
         if ((st = build_f32_copy(h)) != CQM_OK) break;
         h->use_f32 = true;
       }
       if (p.exact_ff && (st = factors_to_ff(h)) != CQM_OK) break;
-      if (p.exact_ff && p.expand_near && (st = build_near_expanded_ff(h)) != CQM_OK) break;
+      if (p.exact_ff && h->expand_near_ok && (st = build_near_expanded_ff(h)) != CQM_OK) break;
       if (p.exact_ff && p.expand_far && (st = build_far_expanded(h)) != CQM_OK) break;
     }
     cudaEventRecord(ev[4], h->stream);

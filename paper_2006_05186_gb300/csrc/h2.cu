@@ -635,7 +635,7 @@ int build_f32_copy(cqm_handle* h) {
     }
     return CQM_OK;
   };
-  if (!h->params.expand_near) {  // the expanded near field replaces the factored FP32 near field
+  if (!h->expand_near_ok) {  // the expanded near field replaces the factored FP32 near field
     CQM_TRY(cc(h->nearC, h->nearC_f));
     CQM_TRY(cc(h->nearD, h->nearD_f));
   }

@@ -100,6 +100,7 @@ struct cqm_handle {
   // nearV_off[b] + (l #c + j) #r + i; nearV holds FP64 values, or float-float
   // pairs when nearV_ff, and nearV_f their FP32 values
   bool near_expanded = false;
+  bool expand_near_ok = false;  // expand_near and the table fits (a quarter of the device)
   bool nearV_ff = false;  // nearV holds float-float pairs (expanded after factors_to_ff)
   cqm::DArray<double2> nearV;
   cqm::DArray<float2> nearV_f;
@@ -116,6 +117,7 @@ struct cqm_handle {
   cqm::DArray<int64_t> tc2_first;
   cqm::DArray<unsigned char> tc2_img;
   cqm::DArray<float2> tc2_tail;
+  int n_sm = 1;  // multiprocessors of the handle's device (persistent grids)
   cqm::DArray<float> Uleaf_f, Etr_f;
 
   // solver workspace

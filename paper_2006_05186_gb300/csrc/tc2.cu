@@ -23,16 +23,19 @@
 //   TMEM columns [256, 512): accumulators, two buffers of 128 (Re Z^T 64 +
 //     Im Z^T 64 columns, one per mu).
 //   shared memory: a ring of NSTAGE B images of 32 KB, copied whole from the
-//     precomputed images in HBM by one bulk copy each (warp 9); an image holds
+//     precomputed images in HBM by one bulk copy each (warp 13); an image holds
 //     the hi and lo planes of [Re C_t | Im C_t] in the canonical K-major
 //     layout without swizzle (core matrices of 8 rows x 16 bytes, K-adjacent
 //     ones 128 bytes apart, 8-row groups 2048 bytes apart).
-//   warps 4-7 build A for each block from xhat_c (one lane per frequency);
-//   warp 8 (one thread) issues 48 MMAs per rank term and frees each B stage,
+//   warps 8-11 build A for each block from xhat_c (one lane per frequency);
+//   warp 12 (one thread) issues 48 MMAs per rank term and frees each B stage,
 //     accumulator and A buffer with tcgen05.commit;
-//   warps 0-3 read each term's accumulator (one lane per frequency), multiply
-//     by d_t[l] and keep the row's sum over all terms in registers, then write
-//     the item's partial tile, which the per-row reduction adds in item order.
+//   warps 0-7 (two per TMEM lane quadrant, 32 mu each) read each term's
+//     accumulator (one lane per frequency), multiply by d_t[l] (loaded three
+//     terms ahead) and keep the row's sum over all terms in registers, then
+//     write the item's partial tile, which the per-row reduction adds in item
+//     order.  CTA k takes items k, k + grid, ... (launched with one CTA per
+//     item, the hardware schedules the items as SMs free up).
 // Frequencies go in chunks of 128 lanes (the last one padded); when Ls mod 128
 // is 1 to TAIL_MAX the remaining frequencies are applied from an FP32 table of
 // the expanded couplings S_b(l) = sum_t d_t[l] C_t instead (k_far_tail_f32).
@@ -56,8 +59,10 @@ constexpr uint32_t BIMG = 32768;       // bytes of one B image (hi + lo planes)
 constexpr uint32_t BPLANE = 16384;     // one plane: 64 rows x 128 bf16
 constexpr uint32_t B_SBO = 2048;       // 8-row groups
 constexpr uint32_t B_LBO = 128;        // K-adjacent core matrices
-constexpr int NTHREADS = 320;          // warps 0-3 epilogue, 4-7 A, 8 MMA, 9 loader
-constexpr int W_A0 = 4, W_MMA = 8, W_LOAD = 9;
+constexpr int NTHREADS = 448;          // warps 0-7 epilogue, 8-11 A, 12 MMA, 13 loader
+constexpr int W_A0 = 8, W_MMA = 12, W_LOAD = 13;
+constexpr int NEPI = 8;                // epilogue warps: two per TMEM lane quadrant
+constexpr int MUE = TP / 2;            // mu columns per epilogue warp
 constexpr uint32_t TCOLS = 512;
 constexpr uint32_t ACC0 = 256;         // first accumulator column
 constexpr int ERR_TIMEOUT = 1;
@@ -149,29 +154,48 @@ __global__ void __launch_bounds__(256) k_far_tail_f32(int Ls, int l0, int ntail,
   yr[(size_t)(lane + 32) * Ls] = cadd(yr[(size_t)(lane + 32) * Ls], a1);
 }
 
-// Position in the sequence (chunk, block, term) of an item, blocks of rank 0
-// skipped; done() once the chunks are exhausted.
+// Position in the sequence (item, chunk, block, term) of one CTA: items
+// blockIdx.x, blockIdx.x + gridDim.x, ...; blocks of rank 0 skipped; done()
+// once the items are exhausted.
 struct Seq {
-  int ch, bi, t;
-  int b0, b1, nch;
+  int ii, ch, bi, t;
+  int b0, b1;
+  int n_items, stride, nch;
+  const int4* items;
   const int* rank;
-  __device__ void start(int b0_, int b1_, int nch_, const int* rank_) {
-    b0 = b0_; b1 = b1_; nch = nch_; rank = rank_;
-    ch = 0;
-    bi = b0;
+  __device__ void start(const int4* items_, int n_items_, int nch_, const int* rank_) {
+    items = items_; n_items = n_items_; nch = nch_; rank = rank_;
+    stride = gridDim.x;
+    ii = blockIdx.x;
     t = 0;
+    enter();
     skip();
   }
+  __device__ void enter() {  // first block of item ii
+    ch = 0;
+    if (ii < n_items) {
+      const int4 it = items[ii];
+      b0 = it.y;
+      b1 = it.z;
+    } else {
+      b0 = b1 = 0;
+    }
+    bi = b0;
+  }
   __device__ void skip() {
-    while (ch < nch) {
-      while (bi < b1 && rank[bi] == 0) ++bi;
-      if (bi < b1) return;
-      ++ch;
-      bi = b0;
+    while (ii < n_items) {
+      while (ch < nch) {
+        while (bi < b1 && rank[bi] == 0) ++bi;
+        if (bi < b1) return;
+        ++ch;
+        bi = b0;
+      }
+      ii += stride;
+      enter();
     }
   }
-  __device__ bool done() const { return ch >= nch; }
-  // advance by one term; returns true if the block changed
+  __device__ bool done() const { return ii >= n_items; }
+  // advance by one term; returns true if the block (or chunk, or item) changed
   __device__ bool next() {
     if (++t < rank[bi]) return false;
     t = 0;
@@ -179,10 +203,19 @@ struct Seq {
     skip();
     return true;
   }
+  __device__ bool same_block(const Seq& o) const { return ii == o.ii && ch == o.ch && bi == o.bi; }
 };
 
+// d_t[l] of the term at q for this lane's frequency of q's chunk (0 past the end)
+__device__ __forceinline__ float2 term_d(const Seq& q, const float2* __restrict__ Df, int cap, int Ls,
+                                         int qd, int lane) {
+  if (q.done()) return make_float2(0.f, 0.f);
+  const int l = 128 * q.ch + 32 * qd + lane;
+  return l < Ls ? __ldg(Df + ((size_t)q.bi * cap + q.t) * Ls + l) : make_float2(0.f, 0.f);
+}
+
 __global__ void __launch_bounds__(NTHREADS, 1)
-    k_far_coupling_tc2(int Ls, int nch, int cap, const int4* __restrict__ items,
+    k_far_coupling_tc2(int Ls, int nch, int cap, int n_items, const int4* __restrict__ items,
                        const int2* __restrict__ blocks, const int* __restrict__ rank,
                        const int64_t* __restrict__ first, const unsigned char* __restrict__ img,
                        const float2* __restrict__ Df, const float2* __restrict__ xhat,
@@ -198,7 +231,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   __shared__ volatile int never_sh;
   unsigned char* ring = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int4 it = items[blockIdx.x];  // (row, first block, end block, -)
 
   if (tid == 0) {
     for (int s = 0; s < NSTAGE; ++s) {
@@ -209,7 +241,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       mbar_init(&a_full[s], 4);  // one arrival per A warp
       mbar_init(&a_empty[s], 1);
       mbar_init(&c_full[s], 1);
-      mbar_init(&c_empty[s], 4);  // one arrival per epilogue warp
+      mbar_init(&c_empty[s], NEPI);  // one arrival per epilogue warp
     }
     mbar_init(&fin_bar, 1);
     mbar_init(&probe_bar, 1);
@@ -231,7 +263,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     constexpr uint32_t ID_RE = idesc_bf16(128, 64, false);
     constexpr uint32_t ID_NEG = idesc_bf16(128, 64, true);
     Seq q;
-    q.start(it.y, it.z, nch, rank);
+    q.start(items, n_items, nch, rank);
     uint32_t ib = 0, ia = 0;
     bool first_term = true;
     while (!q.done()) {
@@ -276,7 +308,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     // ------------------------------------------------------------ B loader
     if (lane == 0) {
       Seq q;
-      q.start(it.y, it.z, nch, rank);
+      q.start(items, n_items, nch, rank);
       for (; !q.done(); q.next(), ++n_issued) {
         const int s = (int)(n_issued % NSTAGE);
         if (n_issued >= NSTAGE &&
@@ -292,7 +324,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int qd = warp & 3;
     const uint32_t trow = tmem + ((uint32_t)(32 * qd) << 16);
     Seq q;
-    q.start(it.y, it.z, nch, rank);
+    q.start(items, n_items, nch, rank);
     uint32_t ia = 0;
     while (!q.done()) {
       const int ab = (int)(ia & 1u);
@@ -303,29 +335,28 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const int l = 128 * q.ch + 32 * qd + lane;
         const float2* xc = xhat + (size_t)blocks[q.bi].y * TP * Ls + l;
         // K order: 0..63 Re xhat[nu], 64..127 Im xhat[nu]; two bf16 per column
+#pragma unroll 1
+        for (int c8 = 0; c8 < 4; ++c8) {  // nu = 16 c8 .. 16 c8 + 15: 8 columns of Re, 8 of Im
+          float2 xv[16];
 #pragma unroll
-        for (int half = 0; half < 2; ++half) {  // half 0: K 0..63 (Re), 1: K 64..127 (Im)
+          for (int j = 0; j < 16; ++j)
+            xv[j] = l < Ls ? __ldg(xc + (size_t)(16 * c8 + j) * Ls) : make_float2(0.f, 0.f);
 #pragma unroll
-          for (int c16 = 0; c16 < 2; ++c16) {  // 16 columns = 32 K values per store
-            uint32_t vh[16], vl[16];
+          for (int part = 0; part < 2; ++part) {  // 0: Re (K 0..63), 1: Im (K 64..127)
+            uint32_t vh[8], vl[8];
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              const int nu0 = 32 * c16 + 2 * j;
-              float x0 = 0.f, x1 = 0.f;
-              if (l < Ls) {
-                const float2 p0 = xc[(size_t)nu0 * Ls], p1 = xc[(size_t)(nu0 + 1) * Ls];
-                x0 = half ? p0.y : p0.x;
-                x1 = half ? p1.y : p1.x;
-              }
+            for (int j = 0; j < 8; ++j) {
+              const float x0 = part ? xv[2 * j].y : xv[2 * j].x;
+              const float x1 = part ? xv[2 * j + 1].y : xv[2 * j + 1].x;
               uint16_t h0, l0v, h1, l1v;
               split_bf16(x0, h0, l0v);
               split_bf16(x1, h1, l1v);
               vh[j] = (uint32_t)h0 | ((uint32_t)h1 << 16);
               vl[j] = (uint32_t)l0v | ((uint32_t)l1v << 16);
             }
-            const uint32_t col = 128u * ab + 32u * half + 16u * c16;
-            tmem_st16(trow + col, vh);
-            tmem_st16(trow + col + 64u, vl);
+            const uint32_t col = 128u * ab + 32u * part + 8u * c8;
+            tmem_st8(trow + col, vh);
+            tmem_st8(trow + col + 64u, vl);
           }
         }
         tmem_wait_st();
@@ -334,65 +365,73 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       __syncwarp();
       if (lane == 0) mbar_arrive(&a_full[ab]);
       ++ia;
-      // skip to the next block (or chunk)
-      const int bcur = q.bi, ccur = q.ch;
-      while (!q.done() && q.bi == bcur && q.ch == ccur) q.next();
+      // skip to the next block (or chunk, or item)
+      const Seq cur = q;
+      while (!q.done() && q.same_block(cur)) q.next();
     }
-  } else if (warp < 4) {
+  } else if (warp < NEPI) {
     // ------------------------------------------------------------- epilogue
-    const int qd = warp;
+    const int qd = warp & 3, mu0 = MUE * (warp >> 2);  // lane quadrant, first mu
     const uint32_t trow = tmem + ((uint32_t)(32 * qd) << 16);
-    float yr[TP], yi[TP];
+    float yr[MUE], yi[MUE];
 #pragma unroll
-    for (int mu = 0; mu < TP; ++mu) yr[mu] = yi[mu] = 0.f;
-    Seq q;
-    q.start(it.y, it.z, nch, rank);
+    for (int mu = 0; mu < MUE; ++mu) yr[mu] = yi[mu] = 0.f;
+    Seq q, qp;
+    q.start(items, n_items, nch, rank);
+    qp = q;
+    // d_t of the next three terms, loaded ahead of their accumulators
+    float2 d0 = term_d(qp, Df, cap, Ls, qd, lane);
+    if (!qp.done()) qp.next();
+    float2 d1 = term_d(qp, Df, cap, Ls, qd, lane);
+    if (!qp.done()) qp.next();
+    float2 d2 = term_d(qp, Df, cap, Ls, qd, lane);
+    if (!qp.done()) qp.next();
     uint32_t ic = 0;
-    int ch_cur = q.done() ? nch : q.ch;
-    auto flush = [&](int ch) {  // the item's partial tile of chunk ch
-      const int l = 128 * ch + 32 * qd + lane;
-      if (l < Ls) {
-        float2* dst = part + (size_t)blockIdx.x * TP * Ls + l;
+    for (int ii = blockIdx.x; ii < n_items; ii += gridDim.x) {
+      for (int ch = 0; ch < nch; ++ch) {
+        while (!q.done() && q.ii == ii && q.ch == ch) {
+          const int cb = (int)(ic & 1u);
+          const float2 d = d0;
+          d0 = d1;
+          d1 = d2;
+          d2 = term_d(qp, Df, cap, Ls, qd, lane);
+          if (!qp.done()) qp.next();
+          bool ok = mbar_wait(&c_full[cb], (ic >> 1) & 1u, &abort_sh, err, ERR_TIMEOUT, lim);
+          ok = __all_sync(0xffffffffu, ok);
+          tc_fence_after();
+          if (ok) {
+            const uint32_t zr = trow + ACC0 + 128u * cb + (uint32_t)mu0, zi = zr + 64u;
 #pragma unroll
-        for (int mu = 0; mu < TP; ++mu) dst[(size_t)mu * Ls] = make_float2(yr[mu], yi[mu]);
-      }
+            for (int m0 = 0; m0 < MUE; m0 += 16) {
+              uint32_t vr[16], vi[16];
+              tmem_ld16(zr + (uint32_t)m0, vr);
+              tmem_ld16(zi + (uint32_t)m0, vi);
+              tmem_wait_ld();
 #pragma unroll
-      for (int mu = 0; mu < TP; ++mu) yr[mu] = yi[mu] = 0.f;
-    };
-    // chunks before the first term (none for items with work) and empty items
-    for (int ch = 0; ch < ch_cur; ++ch) flush(ch);
-    while (!q.done()) {
-      const int cb = (int)(ic & 1u);
-      bool ok = mbar_wait(&c_full[cb], (ic >> 1) & 1u, &abort_sh, err, ERR_TIMEOUT, lim);
-      ok = __all_sync(0xffffffffu, ok);
-      tc_fence_after();
-      const int l = 128 * q.ch + 32 * qd + lane;
-      const float2 d = (l < Ls) ? Df[((size_t)q.bi * cap + q.t) * Ls + l] : make_float2(0.f, 0.f);
-      if (ok) {
-        const uint32_t zr = trow + ACC0 + 128u * cb, zi = zr + 64u;
-#pragma unroll
-        for (int m0 = 0; m0 < TP; m0 += 16) {
-          uint32_t vr[16], vi[16];
-          tmem_ld16(zr + (uint32_t)m0, vr);
-          tmem_ld16(zi + (uint32_t)m0, vi);
-          tmem_wait_ld();
-#pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const float a = __uint_as_float(vr[j]), bq = __uint_as_float(vi[j]);
-            yr[m0 + j] = fmaf(d.x, a, fmaf(-d.y, bq, yr[m0 + j]));
-            yi[m0 + j] = fmaf(d.x, bq, fmaf(d.y, a, yi[m0 + j]));
+              for (int j = 0; j < 16; ++j) {
+                const float a = __uint_as_float(vr[j]), bq = __uint_as_float(vi[j]);
+                yr[m0 + j] = fmaf(d.x, a, fmaf(-d.y, bq, yr[m0 + j]));
+                yi[m0 + j] = fmaf(d.x, bq, fmaf(d.y, a, yi[m0 + j]));
+              }
+            }
           }
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&c_empty[cb]);
+          ++ic;
+          q.next();
         }
+        // the item's partial tile of this chunk (zero for an item without terms)
+        const int l = 128 * ch + 32 * qd + lane;
+        if (l < Ls) {
+          float2* dst = part + ((size_t)ii * TP + mu0) * Ls + l;
+#pragma unroll
+          for (int mu = 0; mu < MUE; ++mu) dst[(size_t)mu * Ls] = make_float2(yr[mu], yi[mu]);
+        }
+#pragma unroll
+        for (int mu = 0; mu < MUE; ++mu) yr[mu] = yi[mu] = 0.f;
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&c_empty[cb]);
-      ++ic;
-      q.next();
-      const int ch_next = q.done() ? nch : q.ch;
-      for (; ch_cur < ch_next; ++ch_cur) flush(ch_cur);
     }
-    for (; ch_cur < nch; ++ch_cur) flush(ch_cur);
   }
   // ------------------------------------------------------------------ teardown
   __syncthreads();
@@ -431,6 +470,9 @@ static void tc2_split(int Ls, int& nch, int& l_tail, int& ntail) {
 int setup_tc2(cqm_handle* h) {
   CQM_CUDA_TRY(cudaFuncSetAttribute(k_far_coupling_tc2, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)SMEM));
+  int dev = 0;
+  CQM_CUDA_TRY(cudaGetDevice(&dev));
+  CQM_CUDA_TRY(cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, dev));
   return CQM_OK;
 }
 
@@ -469,10 +511,10 @@ int build_tc2(cqm_handle* h) {
 int far_coupling_tc2(cqm_handle* h, int* l_tail_out) {
   int nch, l_tail, ntail;
   tc2_split(h->Ls, nch, l_tail, ntail);
+  ProfScope ps_(h, CQM_K_FAR_COUPLING);  // one timed unit: the chunks and the tail
   {
-    ProfScope ps_(h, CQM_K_FAR_COUPLING);
     k_far_coupling_tc2<<<h->n_far_items, NTHREADS, SMEM, h->stream>>>(
-        h->Ls, nch, h->rank_cap, h->far_items.p, h->far_rc.p, h->far_rank.p, h->tc2_first.p,
+        h->Ls, nch, h->rank_cap, h->n_far_items, h->far_items.p, h->far_rc.p, h->far_rank.p, h->tc2_first.p,
         h->tc2_img.p, h->farD_f.p, h->xhat_f.p, h->part_f.p, h->flag.p + 1, h->wait_limit_ns,
         h->wait_probe ? 1 : 0);
     h->wait_probe = false;  // one-shot
@@ -481,7 +523,6 @@ int far_coupling_tc2(cqm_handle* h, int* l_tail_out) {
   if (ntail > 0) {
     const int nfr = (int)h->h_far_rows.size();
     const int warps = nfr * ntail;
-    ProfScope ps_(h, CQM_K_FAR_COUPLING);
     k_far_tail_f32<<<(unsigned)((warps + 7) / 8), 256, 0, h->stream>>>(
         h->Ls, l_tail, ntail, nfr, h->d_far_rows.p, h->far_rowptr.p, h->far_rc.p, h->tc2_tail.p,
         h->xhat_f.p, h->yhat_f.p);
