@@ -81,6 +81,13 @@ FP32_PEAK_SOURCE = "unit counts x max SM clock (152 SMs x 128 FP32 lanes x 2 x 2
 # TF32 dense tensor peak: the measured bf16 cuBLAS rate (sustained: the kernel is
 # timed inside a seconds-long step) times the nominal tf32 / bf16 ratio 1.1 / 2.25.
 TF32_OVER_BF16 = 1.1 / 2.25
+# FP32 issue peak (thread instructions): 152 SMs x 128 lanes x 2.07 GHz.
+FP32_ISSUE_PEAK_T = 152 * 128 * 2.07e9 / 1e12
+# FP32-pipe instructions per float-float kernel evaluation c exp(-s d) of the
+# MACA slices and fibres (the table exponential and cis of csrc/ffexp.cuh, the
+# two final float-float products and the float-float accumulation), counted
+# from the source.
+MACA_FF_INSTR_PER_EVAL = 160
 
 
 # DRAM bytes (read + write) of one launch of the bf16 tensor-core coupling per
@@ -210,7 +217,7 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
-def kernel_models(info, Ls, p, tensor_cores, tf32=None):
+def kernel_models(info, Ls, p, tensor_cores, tf32=None, sinfo=None, launches_per_step=None):
     """Algorithmic work per launch of the contraction kernels and the peak
     that bounds each.  Complex multiply-add = 8 flops.  Factored forms:
     coupling sum_far rank * p^2 * Ls, near field sum_near rank * #r#c * Ls
@@ -260,6 +267,19 @@ def kernel_models(info, Ls, p, tensor_cores, tf32=None):
     if info.get("far_expanded"):
         models["far_exact"] = dict(hbm, work=16.0 * info["far_coupling"] * Ls,
                                    what="expanded float-float far couplings streamed (16 B per entry and frequency)")
+    lps = launches_per_step or {}
+    issue = dict(bound="alu", peak=FP32_ISSUE_PEAK_T, unit="Tinst/s",
+                 peak_source="FP32 issue: unit counts x max SM clock (152 SMs x 128 lanes x 2.07 GHz)")
+    for k, key in (("maca_slice", "maca_slice_evals"), ("maca_fibre", "maca_fibre_evals")):
+        if info.get(key) and lps.get(k):
+            models[k] = dict(issue, work=float(info[key]) * MACA_FF_INSTR_PER_EVAL / lps[k],
+                             what=(f"float-float kernel evaluations ({info[key]:.3e} per setup) x "
+                                   f"{MACA_FF_INSTR_PER_EVAL} FP32 instructions each"))
+    if sinfo and sinfo.get("iterations") and sinfo.get("arnoldi_vectors"):
+        byts = (4.0 * sinfo["arnoldi_vectors"] + 8.0 * sinfo["arnoldi_freq_steps"]) * info["nt"] * 16.0
+        models["arnoldi"] = dict(hbm, work=byts / sinfo["iterations"],
+                                 what=("CGS2 Arnoldi step: the basis read four times and w eight times "
+                                       "per active frequency (16 B complex entries)"))
     return models
 
 
@@ -311,6 +331,8 @@ def run_ours(args):
                   aca_eps=W["aca_eps"], profile=1)
     if args.tensor_cores is not None:
         params["tensor_cores"] = args.tensor_cores
+    if args.expand_far is not None:
+        params["expand_far"] = args.expand_far
     stream = torch.cuda.current_stream()
     rhs = torch.empty((L, M), dtype=torch.float64, device="cuda")
     q = torch.empty((L, M), dtype=torch.float64, device="cuda")
@@ -382,7 +404,8 @@ def run_ours(args):
     inf = infos[-1]
     dom = max(prof.items(), key=lambda kv: kv[1][1])
     p = W["cheb_m"] ** 3
-    models = kernel_models(inf, Ls, p, inf["tensor_cores"], tf32_measured)
+    lps = {k: v[0] / args.steps for k, v in prof.items()}
+    models = kernel_models(inf, Ls, p, inf["tensor_cores"], tf32_measured, sinfos[-1], lps)
     lat = sorted(times)
     clocks = clk.summary()
     line = {
@@ -686,6 +709,8 @@ def main():
     ap.add_argument("--N", type=int, default=None, help="time-step count override")
     ap.add_argument("--tensor-cores", type=int, choices=[0, 1, 2], default=None,
                     help="far-field coupling on the tensor cores in bf16 (1), TF32 (2), or FP32 SIMT (0)")
+    ap.add_argument("--expand-far", type=int, choices=[0, 1], default=None,
+                    help="override the expanded far table of the FP64-accurate apply")
     ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batch64", "serve"],
                     default="sphere5120_N256")
     ap.add_argument("--workers", type=int, default=6, help="server workers (batch64, serve)")

@@ -155,6 +155,12 @@ typedef struct cqm_setup_info {
   int64_t near_rank_entries;    /* sum over near blocks of rank * #r * #c */
   int32_t near_expanded;        /* 1 if the near field is held expanded per frequency */
   int32_t far_expanded;         /* 1 if the far couplings of the FP64-accurate apply are */
+  /* Kernel evaluations c exp(-s r) of the MACA (Alg. 2), near and far blocks:
+   * every slice evaluates all quadrature points of its block at one frequency
+   * (p^2 Chebyshev pairs for a far block), every fibre the points of its pivot
+   * pair at all Ls frequencies.  Slices are counted exactly (the ranks times
+   * the block's points); fibres with each block's mean points per pair. */
+  int64_t maca_slice_evals, maca_fibre_evals;
 } cqm_setup_info;
 
 /* Per-solve summary. */
@@ -166,6 +172,9 @@ typedef struct cqm_solve_info {
   double max_rel_residual;      /* max_l ||ghat_l - V_l qhat_l|| / ||ghat_l|| (true residual, FP64) */
   double max_imag;              /* max |Im q_n[i]| before taking the real part */
   double t_forward_ms, t_gmres_ms, t_inverse_ms;
+  /* Arnoldi work: sum over steps and active frequencies of the basis vectors
+   * the step orthogonalises against (j + 1 at step j), and of 1. */
+  int64_t arnoldi_vectors, arnoldi_freq_steps;
 } cqm_solve_info;
 
 typedef struct cqm_handle cqm_handle;
@@ -285,7 +294,7 @@ int cqm_bem_inverse_transform(cqm_handle* h, const double* qhat, double* q, int3
 #define CQM_K_GEOMETRY       0
 #define CQM_K_TREE           1
 #define CQM_K_PARTITION      2
-#define CQM_K_BASES          3    /* cluster bases, FP32 and float-float factor copies, expanded tables */
+#define CQM_K_BASES          3    /* cluster bases, FP32 and float-float factor copies */
 #define CQM_K_DENSE_ASSEMBLE 4
 #define CQM_K_ENTRIES        5
 #define CQM_K_MACA_SLICE     6
@@ -307,7 +316,9 @@ int cqm_bem_inverse_transform(cqm_handle* h, const double* qhat, double* q, int3
 #define CQM_K_PRECOND        22
 #define CQM_K_NEAR_EXACT     23   /* near field of the FP64-accurate apply (residuals) */
 #define CQM_K_FAR_EXACT      24   /* far coupling of the FP64-accurate apply (residuals) */
-#define CQM_K_COUNT          25
+#define CQM_K_EXPAND         25   /* expanded tables and tensor-core operand images (setup) */
+#define CQM_K_POINTS         26   /* near-field quadrature point cache and far kernel points (setup) */
+#define CQM_K_COUNT          27
 
 /* Turn per-launch event timing on (nonzero) or off; either way the counters
  * are reset.  Timing adds one event pair per launch on the handle's stream. */

@@ -34,7 +34,7 @@ EXPORTED = [
     "cqm_bem_estimate_bytes", "cqm_server_create", "cqm_bem_submit", "cqm_bem_poll",
     "cqm_server_load", "cqm_server_destroy",
 ]
-K_COUNT = 25
+K_COUNT = 27
 
 
 class cqm_mesh(C.Structure):
@@ -75,6 +75,7 @@ class cqm_setup_info(C.Structure):
         ("t_geometry_ms", C.c_double), ("t_tree_ms", C.c_double), ("t_bases_ms", C.c_double),
         ("t_assembly_ms", C.c_double), ("near_rank_entries", C.c_int64),
         ("near_expanded", C.c_int32), ("far_expanded", C.c_int32),
+        ("maca_slice_evals", C.c_int64), ("maca_fibre_evals", C.c_int64),
     ]
 
 
@@ -83,6 +84,7 @@ class cqm_solve_info(C.Structure):
         ("iterations", C.c_int32), ("restarts", C.c_int32), ("converged", C.c_int32),
         ("Ls", C.c_int32), ("max_rel_residual", C.c_double), ("max_imag", C.c_double),
         ("t_forward_ms", C.c_double), ("t_gmres_ms", C.c_double), ("t_inverse_ms", C.c_double),
+        ("arnoldi_vectors", C.c_int64), ("arnoldi_freq_steps", C.c_int64),
     ]
 
 

@@ -632,7 +632,7 @@ static const char* k_names[CQM_K_COUNT] = {
     "geometry", "tree", "partition", "bases", "dense_assemble", "entries", "maca_slice",
     "maca_pivot", "maca_fibre", "maca_finalize", "near_apply", "leaf_forward", "upsweep",
     "far_coupling", "downsweep", "leaf_backward", "dense_apply", "arnoldi", "gmres_other",
-    "forward_dft", "inverse_dft", "rhs", "precond", "near_exact", "far_exact"};
+    "forward_dft", "inverse_dft", "rhs", "precond", "near_exact", "far_exact", "expand", "points"};
 
 const char* cqm_bem_kernel_name(int32_t id) {
   return (id >= 0 && id < CQM_K_COUNT) ? k_names[id] : "";

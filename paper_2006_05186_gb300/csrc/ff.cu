@@ -338,7 +338,10 @@ __global__ void __launch_bounds__(256) k_far_expand_ff(int Ls, int p, int cap, c
                                                        const ffc* __restrict__ Cf, const double2* __restrict__ Df,
                                                        ffc* __restrict__ S) {
   __shared__ ffc Ds[64][FAR_NF];  // rank <= rank_cap <= 64
-  const int b = blockIdx.y, l0 = blockIdx.x * FAR_NF;
+  // one-dimensional grid, block-major: the frequency chunks of one block are
+  // consecutive blocks and share its factors in L2
+  const int nch = (Ls + FAR_NF - 1) / FAR_NF;
+  const int b = (int)(blockIdx.x / nch), l0 = (int)(blockIdx.x - (unsigned)b * nch) * FAR_NF;
   const int rk = rank[b], nf = min(FAR_NF, Ls - l0);
   for (int t = threadIdx.x; t < rk * FAR_NF; t += blockDim.x) {
     const int tt = t / FAR_NF, f = t - tt * FAR_NF;
@@ -421,8 +424,8 @@ int build_far_expanded(cqm_handle* h) {
     return CQM_OK;  // the allocation did not fit: stay factored
   }
   {
-    ProfScope ps_(h, CQM_K_BASES);
-    dim3 g((unsigned)((h->Ls + FAR_NF - 1) / FAR_NF), (unsigned)h->n_far);
+    ProfScope ps_(h, CQM_K_EXPAND);
+    const unsigned g = (unsigned)((h->Ls + FAR_NF - 1) / FAR_NF) * (unsigned)h->n_far;
     k_far_expand_ff<<<g, 256, 0, h->stream>>>(h->Ls, h->p, h->rank_cap, h->far_rank.p,
                                                (const ffc*)h->farC.p, h->farD.p, (ffc*)h->farS.p);
   }
@@ -460,7 +463,8 @@ __global__ void __launch_bounds__(256) k_near_expand_ff(int Ls, int cap, const i
                                                         const int64_t* __restrict__ voff,
                                                         ffc* __restrict__ V, float2* __restrict__ Vf) {
   __shared__ ffc Ds[64][FAR_NF];  // rank <= rank_cap <= 64
-  const int b = blockIdx.y, l0 = blockIdx.x * FAR_NF;
+  const int nch = (Ls + FAR_NF - 1) / FAR_NF;  // block-major one-dimensional grid
+  const int b = (int)(blockIdx.x / nch), l0 = (int)(blockIdx.x - (unsigned)b * nch) * FAR_NF;
   const int2 c2 = rc[b];
   const int nr = end[c2.x] - begin[c2.x], nc = end[c2.y] - begin[c2.y];
   const int rk = rank[b], nf = min(FAR_NF, Ls - l0);
@@ -544,8 +548,8 @@ int build_near_expanded_ff(cqm_handle* h) {
   CQM_CUDA_TRY(cudaMemcpyAsync(h->nearV_off.p, h->h_nearV_off.data(), sizeof(int64_t) * (nb + 1),
                                cudaMemcpyHostToDevice, h->stream));
   if (nb > 0) {
-    ProfScope ps_(h, CQM_K_BASES);
-    dim3 g((unsigned)((h->Ls + FAR_NF - 1) / FAR_NF), (unsigned)nb);
+    ProfScope ps_(h, CQM_K_EXPAND);
+    const unsigned g = (unsigned)((h->Ls + FAR_NF - 1) / FAR_NF) * (unsigned)nb;
     k_near_expand_ff<<<g, 256, 0, h->stream>>>(h->Ls, h->rank_cap, h->near_rc.p, h->node_begin.p,
                                                h->node_end.p, h->near_off.p, h->near_rank.p,
                                                (const ffc*)h->nearC.p, h->nearD.p, h->nearV_off.p,

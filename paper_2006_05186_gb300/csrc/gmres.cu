@@ -18,6 +18,7 @@ struct GmresWork {
   DArray<double2> Vb, r, H, sn, g, y, Z, p1, p2;  // p1, p2: partial dot products
   DArray<double> cs, bnorm, beta, thr, nrm;
   DArray<int> active, kdim, converged, counters;
+  DArray<unsigned long long> work;  // [0] basis vectors, [1] frequency steps of the Arnoldi steps
   int* h_counters = nullptr;  // pinned
 };
 
@@ -182,9 +183,13 @@ __global__ void __launch_bounds__(256) k_gs_finish(int M, int Ls, int m, int j, 
                                                    double* __restrict__ cs, double2* __restrict__ sn,
                                                    double2* __restrict__ g, const double* __restrict__ thr,
                                                    const double* __restrict__ nrm, int* active, int* kdim,
-                                                   int* counters) {
+                                                   int* counters, unsigned long long* work) {
   const int ch = blockIdx.x, l = blockIdx.y;
   if (!active[l]) return;
+  if (ch == 0 && threadIdx.x == 0) {
+    atomicAdd(&work[0], (unsigned long long)(j + 1));
+    atomicAdd(&work[1], 1ull);
+  }
   double s2 = 0.0;
   for (int c = 0; c < nch; ++c) s2 += nrm[(size_t)l * nch + c];
   const double hn = sqrt(s2);
@@ -291,7 +296,7 @@ int gmres_solve(cqm_handle* h, const double2* d_b, double2* d_x, cqm_solve_info*
     W.Vb.free(A); W.r.free(A); W.Z.free(A); W.H.free(A); W.sn.free(A); W.g.free(A); W.y.free(A);
     W.p1.free(A); W.p2.free(A); W.nrm.free(A);
     W.cs.free(A); W.bnorm.free(A); W.beta.free(A); W.thr.free(A); W.active.free(A); W.kdim.free(A);
-    W.converged.free(A); W.counters.free(A);
+    W.converged.free(A); W.counters.free(A); W.work.free(A);
     if (W.h_counters) cudaFreeHost(W.h_counters);
   };
 #define GM_TRY(e) do { st = (e); if (st != CQM_OK) { cleanup(); return st; } } while (0)
@@ -311,6 +316,7 @@ int gmres_solve(cqm_handle* h, const double2* d_b, double2* d_x, cqm_solve_info*
   GM_TRY(W.kdim.allocate(A, Ls));
   GM_TRY(W.converged.allocate(A, Ls));
   GM_TRY(W.counters.allocate(A, 4));
+  GM_TRY(W.work.allocate(A, 2));
   // row chunks per frequency for the Arnoldi kernels: about 4 blocks per SM in
   // all, at least 256 rows per chunk
   const int nch = std::max(1, std::min((M + 255) / 256, (4 * 152 + Ls - 1) / Ls));
@@ -333,6 +339,7 @@ int gmres_solve(cqm_handle* h, const double2* d_b, double2* d_x, cqm_solve_info*
     return CQM_OK;
   };
   GM_TRY(cu(cudaMemsetAsync(d_x, 0, sizeof(double2) * Ls * M, S)));
+  GM_TRY(cu(cudaMemsetAsync(W.work.p, 0, 2 * sizeof(unsigned long long), S)));
   GM_TRY(clear_wait_flag(h));
   GM_TRY(cu(cudaEventCreate(&e0)));
   GM_TRY(cu(cudaEventCreate(&e1)));
@@ -377,7 +384,7 @@ int gmres_solve(cqm_handle* h, const double2* d_b, double2* d_x, cqm_solve_info*
         k_gs_update<8><<<grid, 256, 0, S>>>(M, Ls, m, j, nch, 1, W.Vb.p, W.H.p, W.active.p, W.p2.p,
                                             W.p1.p, W.nrm.p);
         k_gs_finish<<<grid, 256, 0, S>>>(M, Ls, m, j, nch, W.Vb.p, W.H.p, W.cs.p, W.sn.p, W.g.p,
-                                         W.thr.p, W.nrm.p, W.active.p, W.kdim.p, W.counters.p);
+                                         W.thr.p, W.nrm.p, W.active.p, W.kdim.p, W.counters.p, W.work.p);
       }
       GM_TRY(cu(cudaGetLastError()));
       ++iters;
@@ -412,6 +419,8 @@ int gmres_solve(cqm_handle* h, const double2* d_b, double2* d_x, cqm_solve_info*
   // beta_l = ||ghat_l - V_l qhat_l|| at the returned solution
   std::vector<double> rel(Ls), bn(Ls);
   std::vector<int> conv(Ls);
+  unsigned long long work[2] = {0, 0};
+  GM_TRY(cu(cudaMemcpyAsync(work, W.work.p, sizeof(work), cudaMemcpyDeviceToHost, S)));
   GM_TRY(cu(cudaMemcpyAsync(rel.data(), W.beta.p, sizeof(double) * Ls, cudaMemcpyDeviceToHost, S)));
   GM_TRY(cu(cudaMemcpyAsync(bn.data(), W.bnorm.p, sizeof(double) * Ls, cudaMemcpyDeviceToHost, S)));
   GM_TRY(cu(cudaMemcpyAsync(conv.data(), W.converged.p, sizeof(int) * Ls, cudaMemcpyDeviceToHost, S)));
@@ -433,6 +442,8 @@ int gmres_solve(cqm_handle* h, const double2* d_b, double2* d_x, cqm_solve_info*
     info->converged = c;
     info->max_rel_residual = mx;
     info->t_gmres_ms = ms;
+    info->arnoldi_vectors = (int64_t)work[0];
+    info->arnoldi_freq_steps = (int64_t)work[1];
   }
   cleanup();
 #undef GM_TRY

@@ -66,6 +66,7 @@ struct cqm_handle {
   std::vector<int64_t> h_near_off;
   // near-field quadrature points cached for the MACA slices and fibres
   int64_t n_points = 0;
+  std::vector<int64_t> h_block_points;  // cached near points of each block (0 for lower blocks)
   cqm::DArray<int64_t> pt_off;
   cqm::DArray<int> pt_cnt;
   cqm::DArray<double> pt_r, pt_c;  // FP64 r and c; with maca_ff the same bytes hold

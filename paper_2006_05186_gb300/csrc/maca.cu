@@ -770,7 +770,7 @@ static int build_point_cache(cqm_handle* h, int64_t n_pairs) {
   if (st == CQM_OK) {
     const Geom g = geom_from(h);
     {
-      ProfScope ps_(h, CQM_K_MACA_SLICE);
+      ProfScope ps_(h, CQM_K_POINTS);
       k_pair_counts<<<nb, 1024, 0, h->stream>>>(h->near_rc.p, h->node_begin.p, h->node_end.p, h->perm.p,
                                                h->near_off.p, h->rank_cap, g, h->quad, h->pt_cnt.p,
                                                h->pt_off.p, tot.p);
@@ -778,6 +778,9 @@ static int build_point_cache(cqm_handle* h, int64_t n_pairs) {
     }
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(&npts, bbase.p + nb, sizeof(int64_t), cudaMemcpyDeviceToHost, h->stream);
+    h->h_block_points.assign(nb, 0);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(h->h_block_points.data(), tot.p, sizeof(int64_t) * nb, cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) {
       set_last_error(std::string("point cache: ") + cudaGetErrorString(e));
@@ -786,7 +789,7 @@ static int build_point_cache(cqm_handle* h, int64_t n_pairs) {
     if (st == CQM_OK) st = h->pt_r.allocate(h->alloc, std::max<int64_t>(npts, 1));
     if (st == CQM_OK) st = h->pt_c.allocate(h->alloc, std::max<int64_t>(npts, 1));
     if (st == CQM_OK) {
-      ProfScope ps_(h, CQM_K_MACA_SLICE);
+      ProfScope ps_(h, CQM_K_POINTS);
       const bool ffm = h->params.maca_ff != 0;
       if (ffm) st = h->pt_r0.allocate(h->alloc, std::max<int64_t>(n_pairs, 1));
       if (st == CQM_OK)
@@ -982,7 +985,7 @@ int build_maca(cqm_handle* h) {
     CQM_TRY(h->fpt_c.allocate(h->alloc, n));
     CQM_TRY(h->fpt_r0.allocate(h->alloc, h->n_far));
     {
-      ProfScope ps_(h, CQM_K_MACA_SLICE);
+      ProfScope ps_(h, CQM_K_POINTS);
       k_far_points<<<h->n_far, 256, 0, h->stream>>>(h->far_rc.p, h->cheb.p, h->m, h->p, h->fpt_d.p,
                                                     h->fpt_c.p, h->fpt_r0.p);
     }
@@ -1013,6 +1016,23 @@ int build_maca(cqm_handle* h) {
     I.rank_max = std::max(I.rank_max, h->h_far_rank[b]);
   }
   I.far_coupling = (int64_t)h->n_far * h->p * h->p;
+  // kernel evaluations of the MACA of the upper blocks (the lower ones are mirrored)
+  I.maca_slice_evals = I.maca_fibre_evals = 0;
+  const bool have_pts = (int)h->h_block_points.size() == h->n_near;
+  for (int b = 0; have_pts && b < h->n_near; ++b) {
+    const int2 rc = h->h_near[b];
+    if (rc.x > rc.y) continue;
+    const int64_t nr = h->h_end[rc.x] - h->h_begin[rc.x], nc = h->h_end[rc.y] - h->h_begin[rc.y];
+    const int64_t pairs = rc.x == rc.y ? nr * (nr + 1) / 2 : nr * nc;
+    const int64_t pts = h->h_block_points[b], rk = h->h_near_rank[b];
+    I.maca_slice_evals += rk * pts;
+    if (pairs > 0) I.maca_fibre_evals += rk * h->Ls * pts / pairs;
+  }
+  for (int b = 0; b < h->n_far; ++b) {
+    if (h->h_far[b].x > h->h_far[b].y) continue;
+    I.maca_slice_evals += (int64_t)h->h_far_rank[b] * h->p * h->p;
+    I.maca_fibre_evals += (int64_t)h->h_far_rank[b] * h->Ls;
+  }
   return CQM_OK;
 }
 

@@ -34,7 +34,8 @@ __global__ void __launch_bounds__(256) k_near_expand(int Ls, int cap, const int2
                                                      const int64_t* __restrict__ voff,
                                                      double2* __restrict__ V, float2* __restrict__ Vf) {
   __shared__ double2 Ds[64][EXP_NF];  // rank <= rank_cap <= 64
-  const int b = blockIdx.y, l0 = blockIdx.x * EXP_NF;
+  const int nch = (Ls + EXP_NF - 1) / EXP_NF;  // block-major one-dimensional grid
+  const int b = (int)(blockIdx.x / nch), l0 = (int)(blockIdx.x - (unsigned)b * nch) * EXP_NF;
   const int2 c2 = rc[b];
   const int nr = end[c2.x] - begin[c2.x], nc = end[c2.y] - begin[c2.y];
   const int rk = rank[b], nf = min(EXP_NF, Ls - l0);
@@ -123,8 +124,8 @@ int build_near_expanded(cqm_handle* h) {
   CQM_CUDA_TRY(cudaMemcpyAsync(h->nearV_off.p, h->h_nearV_off.data(), sizeof(int64_t) * (nb + 1),
                                cudaMemcpyHostToDevice, h->stream));
   if (nb > 0) {
-    ProfScope ps_(h, CQM_K_BASES);
-    dim3 g((unsigned)((h->Ls + EXP_NF - 1) / EXP_NF), (unsigned)nb);
+    ProfScope ps_(h, CQM_K_EXPAND);
+    const unsigned g = (unsigned)((h->Ls + EXP_NF - 1) / EXP_NF) * (unsigned)nb;
     k_near_expand<<<g, 256, 0, h->stream>>>(h->Ls, h->rank_cap, h->near_rc.p, h->node_begin.p,
                                             h->node_end.p, h->near_off.p, h->near_rank.p, h->nearC.p,
                                             h->nearD.p, h->nearV_off.p, h->nearV.p, h->nearV_f.p);

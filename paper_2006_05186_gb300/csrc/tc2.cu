@@ -85,12 +85,13 @@ __device__ __forceinline__ void split_bf16(float x, uint16_t& hi, uint16_t& lo) 
 
 // B images of every rank term: image (b, t) at (first[b] + t) * BIMG bytes,
 // element (mu, k) = Re C_t[mu][k] (k < 64) or Im C_t[mu][k - 64], split into
-// the hi and lo planes.  One block per (term, block).
-__global__ void __launch_bounds__(256) k_tc2_images(int cap, const int* __restrict__ rank,
+// the hi and lo planes.  One block per (term slot, block) on a one-dimensional
+// grid of nt slots per block.
+__global__ void __launch_bounds__(256) k_tc2_images(int cap, int nt, const int* __restrict__ rank,
                                                     const int64_t* __restrict__ first,
                                                     const double2* __restrict__ C,
                                                     unsigned char* __restrict__ img) {
-  const int b = blockIdx.y, t = blockIdx.x;
+  const int b = (int)(blockIdx.x / nt), t = (int)(blockIdx.x - (unsigned)b * nt);
   if (t >= rank[b]) return;
   const double2* Ct = C + ((size_t)b * cap + t) * TP * TP;
   unsigned char* dst = img + (size_t)(first[b] + t) * BIMG;
@@ -487,17 +488,17 @@ int build_tc2(cqm_handle* h) {
                                cudaMemcpyHostToDevice, h->stream));
   CQM_TRY(h->tc2_img.allocate(h->alloc, (size_t)std::max<int64_t>(1, first[h->n_far]) * BIMG));
   {
-    ProfScope ps_(h, CQM_K_BASES);
-    dim3 g((unsigned)std::max(1, h->info.rank_max), (unsigned)h->n_far);
-    k_tc2_images<<<g, 256, 0, h->stream>>>(h->rank_cap, h->far_rank.p, h->tc2_first.p, h->farC.p,
-                                          h->tc2_img.p);
+    ProfScope ps_(h, CQM_K_EXPAND);
+    const int nt = std::max(1, h->info.rank_max);
+    k_tc2_images<<<(unsigned)nt * (unsigned)h->n_far, 256, 0, h->stream>>>(
+        h->rank_cap, nt, h->far_rank.p, h->tc2_first.p, h->farC.p, h->tc2_img.p);
   }
   CQM_CHECK_LAUNCH();
   int nch, l_tail, ntail;
   tc2_split(h->Ls, nch, l_tail, ntail);
   if (ntail > 0) {
     CQM_TRY(h->tc2_tail.allocate(h->alloc, (size_t)h->n_far * ntail * TP * TP));
-    ProfScope ps_(h, CQM_K_BASES);
+    ProfScope ps_(h, CQM_K_EXPAND);
     k_tc2_tail_table<<<h->n_far, 256, 0, h->stream>>>(h->Ls, h->rank_cap, l_tail, ntail, h->far_rank.p,
                                                      h->farC.p, h->farD.p, h->tc2_tail.p);
     CQM_CHECK_LAUNCH();

@@ -63,3 +63,21 @@ def test_time_weighted_fraction(bench):
     tw = bench.time_weighted_frac(prof, models)
     assert tw["frac"] == pytest.approx((100.0 * fa + 300.0 * fb) / 400.0)
     assert tw["ms"] == pytest.approx(400.0) and tw["kernels"] == ["a", "b"]
+
+
+def test_maca_and_arnoldi_models(bench):
+    info = dict(INFO, near_expanded=1, far_expanded=1, nt=5120, maca_slice_evals=4.0e9,
+                maca_fibre_evals=1.0e9)
+    sinfo = dict(iterations=100, arnoldi_vectors=20000, arnoldi_freq_steps=1200)
+    lps = {"maca_slice": 16.0, "maca_fibre": 16.0}
+    m = bench.kernel_models(info, Ls=129, p=64, tensor_cores=1, sinfo=sinfo, launches_per_step=lps)
+    k = bench.MACA_FF_INSTR_PER_EVAL
+    assert m["maca_slice"]["bound"] == "alu" and m["maca_slice"]["work"] == 4.0e9 * k / 16.0
+    assert m["maca_fibre"]["work"] == 1.0e9 * k / 16.0
+    assert m["maca_slice"]["peak"] == pytest.approx(152 * 128 * 2.07e9 / 1e12)
+    # basis read four times and w eight times per active frequency and step
+    assert m["arnoldi"]["bound"] == "hbm"
+    assert m["arnoldi"]["work"] == (4.0 * 20000 + 8.0 * 1200) * 5120 * 16.0 / 100
+    # without counts the models are left out
+    m0 = bench.kernel_models(info, Ls=129, p=64, tensor_cores=1)
+    assert "maca_slice" not in m0 and "arnoldi" not in m0
