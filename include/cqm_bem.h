@@ -203,6 +203,32 @@ int cqm_bem_setup(const cqm_mesh* mesh, double dt, int32_t N, int32_t bdf_order,
 int cqm_bem_solve(cqm_handle* h, const double* rhs, double* density, int32_t mem,
                   cqm_solve_info* info);
 
+/* Solve the same problem by marching on in time, the paper's own time
+ * stepping (Sec. 3.2: sum_{k<=n} Vhat_{n-k} q_k = b_n, step by step), with the
+ * compressed weights: the MACA fibres are transformed to the CQM weights'
+ * time index (eq. fastdft), Vhat_n = Re sum_t C_t dhat_t[n] per block, and
+ * the history of each step is sum_t C_t (sum_{k<n} dhat_t[n-k] q_k) per block
+ * (eq. fastrhs; far blocks through their cluster bases).  Vhat_0 is
+ * assembled densely once and inverted once (FP64 blocked Gauss-Jordan; the
+ * paper factorises it once by LU); each step applies its inverse.  The result
+ * equals the decoupled solve of cqm_bem_solve up to O(R^L) and is exactly
+ * causal.  H2MACA mode only.  The first call builds the weights (held by the
+ * handle: (n_near + n_far) rank_cap L transformed fibres and M^2 doubles).
+ * rhs, density: (N+1) x nt float64 in `mem` memory.  info (may be NULL):
+ * iterations = N + 1 steps, t_gmres_ms = the march, t_forward_ms = the weight
+ * construction of this call (0 once built).  All FP64.
+ * Errors: CQM_EINVAL (NULL, dense mode), CQM_ENOMEM, CQM_ECUDA. */
+int cqm_bem_solve_mot(cqm_handle* h, const double* rhs, double* density, int32_t mem,
+                      cqm_solve_info* info);
+
+/* The CQM weight Vhat_n (eq. dft) of the compressed operator as a dense
+ * nt x nt float64 matrix in the caller's numbering (row-major), n = 0..N:
+ * Re sum_t C_t dhat_t[n] per near block, U_r (Re sum_t C_t dhat_t[n]) U_c^T
+ * per far block (eq. fastdft).  Inspection call of the marching-on-in-time
+ * path.  W in `mem` memory.  Errors: CQM_EINVAL (n out of range, dense
+ * mode), CQM_ENOMEM, CQM_ECUDA. */
+int cqm_bem_mot_weight(cqm_handle* h, int32_t n, double* W, int32_t mem);
+
 /* Galerkin data of the plane-wave pulse u(x,t) = exp(-((t - delay - d.x)/width)^2)
  * at t_n = n dt, n = 0..N, with Radon's 7-point rule per triangle.
  * dir: 3 doubles (host, normalised inside).  rhs: (N+1) x nt float64 in `mem`. */
@@ -318,7 +344,10 @@ int cqm_bem_inverse_transform(cqm_handle* h, const double* qhat, double* q, int3
 #define CQM_K_FAR_EXACT      24   /* far coupling of the FP64-accurate apply (residuals) */
 #define CQM_K_EXPAND         25   /* expanded tables and tensor-core operand images (setup) */
 #define CQM_K_POINTS         26   /* near-field quadrature point cache and far kernel points (setup) */
-#define CQM_K_COUNT          27
+#define CQM_K_MOT_WEIGHTS    27   /* marching on in time: transformed fibres, Vhat_0 and its inverse */
+#define CQM_K_MOT_HISTORY    28   /* marching on in time: history sum of each step (near and far) */
+#define CQM_K_MOT_STEP       29   /* marching on in time: step solve, H2 transforms of the new density */
+#define CQM_K_COUNT          30
 
 /* Turn per-launch event timing on (nonzero) or off; either way the counters
  * are reset.  Timing adds one event pair per launch on the handle's stream. */

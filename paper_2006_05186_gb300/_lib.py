@@ -32,9 +32,9 @@ EXPORTED = [
     "cqm_bem_profile", "cqm_bem_profile_read", "cqm_bem_kernel_name",
     "cqm_cluster_tree_noalloc", "cqm_bem_set_wait_limit",
     "cqm_bem_estimate_bytes", "cqm_server_create", "cqm_bem_submit", "cqm_bem_poll",
-    "cqm_server_load", "cqm_server_destroy",
+    "cqm_server_load", "cqm_server_destroy", "cqm_bem_solve_mot", "cqm_bem_mot_weight",
 ]
-K_COUNT = 27
+K_COUNT = 30
 
 
 class cqm_mesh(C.Structure):
@@ -146,6 +146,8 @@ def load(build_if_missing: bool = False):
         "cqm_bem_apply": (C.c_int, [vp, vp, vp, i32]),
         "cqm_bem_apply_inner": (C.c_int, [vp, vp, vp, i32]),
         "cqm_bem_solve_frequencies": (C.c_int, [vp, vp, vp, i32, C.POINTER(cqm_solve_info)]),
+        "cqm_bem_solve_mot": (C.c_int, [vp, vp, vp, i32, C.POINTER(cqm_solve_info)]),
+        "cqm_bem_mot_weight": (C.c_int, [vp, i32, vp, i32]),
         "cqm_bem_forward_transform": (C.c_int, [vp, vp, vp, i32]),
         "cqm_bem_inverse_transform": (C.c_int, [vp, vp, vp, i32]),
         "cqm_bem_profile": (C.c_int, [vp, i32]),
@@ -404,6 +406,25 @@ class CqmBem:
         _check(self._lib.cqm_bem_solve(self._h, pr, po, mem, C.byref(inf)), "solve",
                allow=(CQM_ENOCONV,) if allow_noconv else ())
         self.last_solve_info = _struct_dict(inf)
+        return out
+
+    def solve_mot(self, rhs, out=None):
+        """Densities q_n by marching on in time (cqm_bem_solve_mot)."""
+        if out is None:
+            out = _like(rhs, (self.L, self.M), complex_=False)
+        pr, mem = _ptr(rhs)
+        po, mem2 = _ptr(out)
+        if mem != mem2:
+            raise ValueError("rhs and density must both be host or both device")
+        inf = cqm_solve_info()
+        _check(self._lib.cqm_bem_solve_mot(self._h, pr, po, mem, C.byref(inf)), "solve_mot")
+        self.last_solve_info = _struct_dict(inf)
+        return out
+
+    def mot_weight(self, n):
+        """Dense CQM weight Vhat_n of the compressed operator (M x M, host)."""
+        out = np.zeros((self.M, self.M))
+        _check(self._lib.cqm_bem_mot_weight(self._h, int(n), out.ctypes.data, MEM_HOST), "mot_weight")
         return out
 
 

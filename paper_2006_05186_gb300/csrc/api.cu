@@ -124,12 +124,13 @@ int cqm_bem_destroy(cqm_handle* h) {
   h->nearC.free(A); h->nearD.free(A); h->farC.free(A); h->farD.free(A);
   h->xhat.free(A); h->yhat.free(A); h->d_leaves.free(A); h->d_far_rows.free(A);
   h->Pinv.free(A);
-  h->far_items.free(A); h->near_items.free(A); h->far_item_ptr.free(A); h->near_item_ptr.free(A);
+  h->far_items.free(A); h->near_items.free(A); h->far_order.free(A); h->far_item_ptr.free(A); h->near_item_ptr.free(A);
   h->part_f.free(A); h->part_d.free(A);
   h->pt_off.free(A); h->pt_cnt.free(A); h->pt_r.free(A); h->pt_c.free(A);
   h->nearC_f.free(A); h->nearD_f.free(A); h->farC_f.free(A); h->farD_f.free(A);
   h->nearV.free(A); h->nearV_f.free(A); h->nearV_off.free(A); h->farS.free(A);
   h->xhat_f.free(A); h->yhat_f.free(A); h->Uleaf_f.free(A); h->Etr_f.free(A);
+  mot_release(h);
   cudaStreamSynchronize(h->stream);
   prof_release(h);
   delete h;
@@ -438,6 +439,44 @@ int cqm_bem_solve_frequencies(cqm_handle* h, const double* ghat, double* qhat, i
   return st;
 }
 
+int cqm_bem_solve_mot(cqm_handle* h, const double* rhs, double* density, int32_t mem,
+                      cqm_solve_info* info) {
+  if (!h || !rhs || !density || (mem != CQM_MEM_HOST && mem != CQM_MEM_DEVICE)) return CQM_EINVAL;
+  set_last_error("");
+  const size_t nt = (size_t)h->L * h->M;
+  Scratch S(&h->alloc);
+  const double* db = rhs;
+  double* dq = density;
+  if (mem == CQM_MEM_HOST) {
+    double* t;
+    CQM_TRY(S.get(&t, nt));
+    CQM_CUDA_TRY(cudaMemcpyAsync(t, rhs, nt * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    db = t;
+    CQM_TRY(S.get(&dq, nt));
+  }
+  cqm_solve_info loc{};
+  CQM_TRY(mot_solve(h, db, dq, info ? info : &loc));
+  if (mem == CQM_MEM_HOST)
+    CQM_CUDA_TRY(cudaMemcpyAsync(density, dq, nt * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CQM_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  return CQM_OK;
+}
+
+int cqm_bem_mot_weight(cqm_handle* h, int32_t n, double* W, int32_t mem) {
+  if (!h || !W || (mem != CQM_MEM_HOST && mem != CQM_MEM_DEVICE)) return CQM_EINVAL;
+  set_last_error("");
+  const size_t nn = (size_t)h->M * h->M;
+  Scratch S(&h->alloc);
+  double* dw = W;
+  if (mem == CQM_MEM_HOST) CQM_TRY(S.get(&dw, nn));
+  CQM_TRY(mot_weight(h, n, dw));
+  if (mem == CQM_MEM_HOST) {
+    CQM_CUDA_TRY(cudaMemcpyAsync(W, dw, nn * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CQM_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  }
+  return CQM_OK;
+}
+
 int cqm_bem_solve(cqm_handle* h, const double* rhs, double* density, int32_t mem,
                   cqm_solve_info* info) {
   if (!h || !rhs || !density || (mem != CQM_MEM_HOST && mem != CQM_MEM_DEVICE)) return CQM_EINVAL;
@@ -632,7 +671,8 @@ static const char* k_names[CQM_K_COUNT] = {
     "geometry", "tree", "partition", "bases", "dense_assemble", "entries", "maca_slice",
     "maca_pivot", "maca_fibre", "maca_finalize", "near_apply", "leaf_forward", "upsweep",
     "far_coupling", "downsweep", "leaf_backward", "dense_apply", "arnoldi", "gmres_other",
-    "forward_dft", "inverse_dft", "rhs", "precond", "near_exact", "far_exact", "expand", "points"};
+    "forward_dft", "inverse_dft", "rhs", "precond", "near_exact", "far_exact", "expand", "points", "mot_weights", "mot_history",
+    "mot_step"};
 
 const char* cqm_bem_kernel_name(int32_t id) {
   return (id >= 0 && id < CQM_K_COUNT) ? k_names[id] : "";

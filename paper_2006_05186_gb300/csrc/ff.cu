@@ -277,12 +277,26 @@ __global__ void k_factors_to_ff(int64_t n, double2* __restrict__ a) {
   }
 }
 
+// The same for the far factors, slot by slot (block b, term t: one CTA);
+// the slots past a block's rank hold no factor and are skipped.
+__global__ void __launch_bounds__(256) k_far_factors_to_ff(int cap, int pp, const int* __restrict__ rank,
+                                                           double2* __restrict__ a) {
+  const int b = (int)(blockIdx.x / cap), t = (int)(blockIdx.x - (unsigned)b * cap);
+  if (t >= rank[b]) return;
+  double2* s = a + (size_t)blockIdx.x * pp;
+  for (int e = threadIdx.x; e < pp; e += blockDim.x) {
+    const double2 v = s[e];
+    ((ffc*)s)[e] = ffc_from(v);
+  }
+}
+
 int factors_to_ff(cqm_handle* h) {
   ProfScope ps_(h, CQM_K_BASES);
   if (h->nearC.n)
     k_factors_to_ff<<<grid_for((int64_t)h->nearC.n, 256), 256, 0, h->stream>>>((int64_t)h->nearC.n, h->nearC.p);
-  if (h->farC.n)
-    k_factors_to_ff<<<grid_for((int64_t)h->farC.n, 256), 256, 0, h->stream>>>((int64_t)h->farC.n, h->farC.p);
+  if (h->farC.n && h->n_far > 0)
+    k_far_factors_to_ff<<<(unsigned)h->n_far * (unsigned)h->rank_cap, 256, 0, h->stream>>>(
+        h->rank_cap, h->p * h->p, h->far_rank.p, h->farC.p);
   CQM_CHECK_LAUNCH();
   h->factors_ff = true;
   return CQM_OK;

@@ -85,6 +85,7 @@ struct cqm_handle {
   // with per-row item ranges; partial tiles are reduced per row in item order
   int n_far_items = 0, n_near_items = 0;
   cqm::DArray<int4> far_items, near_items;
+  cqm::DArray<int> far_order;  // far items by decreasing work (launch order of the coupling)
   cqm::DArray<int> far_item_ptr, near_item_ptr;
   cqm::DArray<float2> part_f;
   cqm::DArray<double2> part_d;
@@ -123,6 +124,17 @@ struct cqm_handle {
 
   // solver workspace
   cqm::DArray<double2> xhat, yhat;  // n_nodes x p x Ls (far field transforms)
+
+  // marching on in time (mot.cu), built on the first call that needs it:
+  // transformed MACA fibres dhat_t[n] (eq. fastdft), (b cap + t) L + n, of the
+  // near and far blocks; explicit cluster bases (rows of every node from
+  // Ue_off[r], p per row); the inverse of the dense step-0 weight Vhat_0 in
+  // tree order (M x M, row-major)
+  bool mot_ready = false;
+  cqm::DArray<double2> mot_dn, mot_df;
+  cqm::DArray<double> mot_Ue, mot_Ainv;
+  cqm::DArray<int64_t> mot_Ue_off;
+  double mot_setup_ms = 0.0;
 
   cqm_setup_info info{};
 
@@ -206,6 +218,12 @@ int apply_precond(cqm_handle* h, const double2* v, double2* z);
 
 // gmres.cu
 int gmres_solve(cqm_handle* h, const double2* d_b, double2* d_x, cqm_solve_info* info);
+
+// mot.cu (marching on in time with the compressed CQM weights)
+int mot_prepare(cqm_handle* h);
+int mot_weight(cqm_handle* h, int n, double* d_W);  // dense Vhat_n, original numbering
+int mot_solve(cqm_handle* h, const double* d_b, double* d_q, cqm_solve_info* info);
+void mot_release(cqm_handle* h);
 
 // Kernel timing scope: records an event pair around the launches it encloses.
 struct ProfScope {

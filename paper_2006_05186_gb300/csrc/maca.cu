@@ -1076,15 +1076,26 @@ int build_work_items(cqm_handle* h) {
   std::vector<int> fp, np;
   split(h->h_far_rows, h->h_far, h->h_far_rank, false, fi, fp);
   split(h->h_leaves, h->h_near, h->h_near_rank, true, ni, np);
+  // launch order of the far items: decreasing rank sum (longest first), ties by index
+  std::vector<int> forder(fi.size());
+  std::vector<int64_t> fw(fi.size(), 0);
+  for (size_t k = 0; k < fi.size(); ++k) {
+    forder[k] = (int)k;
+    for (int bi = fi[k].y; bi < fi[k].z; ++bi) fw[k] += std::max(1, h->h_far_rank[bi]);
+  }
+  std::stable_sort(forder.begin(), forder.end(), [&](int a, int b) { return fw[a] > fw[b]; });
   h->n_far_items = (int)fi.size();
   h->n_near_items = (int)ni.size();
   CQM_TRY(h->far_items.allocate(h->alloc, std::max<size_t>(1, fi.size())));
   CQM_TRY(h->near_items.allocate(h->alloc, std::max<size_t>(1, ni.size())));
+  CQM_TRY(h->far_order.allocate(h->alloc, std::max<size_t>(1, forder.size())));
   CQM_TRY(h->far_item_ptr.allocate(h->alloc, fp.size()));
   CQM_TRY(h->near_item_ptr.allocate(h->alloc, np.size()));
   cudaStream_t S = h->stream;
   if (!fi.empty()) CQM_CUDA_TRY(cudaMemcpyAsync(h->far_items.p, fi.data(), sizeof(int4) * fi.size(), cudaMemcpyHostToDevice, S));
   if (!ni.empty()) CQM_CUDA_TRY(cudaMemcpyAsync(h->near_items.p, ni.data(), sizeof(int4) * ni.size(), cudaMemcpyHostToDevice, S));
+  if (!forder.empty())
+    CQM_CUDA_TRY(cudaMemcpyAsync(h->far_order.p, forder.data(), sizeof(int) * forder.size(), cudaMemcpyHostToDevice, S));
   CQM_CUDA_TRY(cudaMemcpyAsync(h->far_item_ptr.p, fp.data(), sizeof(int) * fp.size(), cudaMemcpyHostToDevice, S));
   CQM_CUDA_TRY(cudaMemcpyAsync(h->near_item_ptr.p, np.data(), sizeof(int) * np.size(), cudaMemcpyHostToDevice, S));
   const size_t part = std::max((size_t)h->n_far_items * 64, (size_t)h->n_near_items * 32) * h->Ls;

@@ -34,8 +34,10 @@
 //     accumulator (one lane per frequency), multiply by d_t[l] (loaded three
 //     terms ahead) and keep the row's sum over all terms in registers, then
 //     write the item's partial tile, which the per-row reduction adds in item
-//     order.  CTA k takes items k, k + grid, ... (launched with one CTA per
-//     item, the hardware schedules the items as SMs free up).
+//     order.  CTA k takes the items at launch positions k, k + grid, ...
+//     (launched with one CTA per item, the hardware schedules the items as
+//     SMs free up); the launch order puts the largest items first, so that
+//     the small ones fill the end of the schedule.
 // Frequencies go in chunks of 128 lanes (the last one padded); when Ls mod 128
 // is 1 to TAIL_MAX the remaining frequencies are applied from an FP32 table of
 // the expanded couplings S_b(l) = sum_t d_t[l] C_t instead (k_far_tail_f32).
@@ -106,8 +108,9 @@ __global__ void __launch_bounds__(256) k_tc2_images(int cap, int nt, const int* 
   }
 }
 
-// Expanded couplings of the tail frequencies: S[(b * ntail + f) * 4096 + mu * 64 + nu]
-// = sum_t d_t[l0 + f] C_t[mu][nu] (FP32 from the FP64 factors).
+// Expanded couplings of the tail frequencies, nu-major:
+// S[(b * ntail + f) * 4096 + nu * 64 + mu] = sum_t d_t[l0 + f] C_t[mu][nu]
+// (FP32 from the FP64 factors).
 __global__ void __launch_bounds__(256) k_tc2_tail_table(int Ls, int cap, int l0, int ntail,
                                                         const int* __restrict__ rank,
                                                         const double2* __restrict__ C,
@@ -117,42 +120,56 @@ __global__ void __launch_bounds__(256) k_tc2_tail_table(int Ls, int cap, int l0,
   const int rk = rank[b];
   for (int e = threadIdx.x; e < TP * TP * ntail; e += blockDim.x) {
     const int f = e / (TP * TP), en = e - f * TP * TP;
+    const int nu = en / TP, mu = en - nu * TP;
     double2 acc = make_double2(0.0, 0.0);
     for (int t = 0; t < rk; ++t)
-      cfma(acc, C[((size_t)b * cap + t) * TP * TP + en], D[((size_t)b * cap + t) * Ls + l0 + f]);
+      cfma(acc, C[((size_t)b * cap + t) * TP * TP + mu * TP + nu], D[((size_t)b * cap + t) * Ls + l0 + f]);
     S[((size_t)b * ntail + f) * TP * TP + en] = make_float2((float)acc.x, (float)acc.y);
   }
 }
 
 // Tail frequencies: yhat_r(l)[mu] += sum over the far blocks (r, c) of row r of
-// sum_nu S_b(l)[mu][nu] xhat_c(l)[nu].  One warp per (far row, tail frequency),
-// lane owns mu = lane and lane + 32.
-__global__ void __launch_bounds__(256) k_far_tail_f32(int Ls, int l0, int ntail, int nrows,
+// sum_nu S_b(l)[mu][nu] xhat_c(l)[nu].  One CTA per (far row, tail
+// frequency); warp w takes the row's blocks w, w + 8, ... (lane owns mu = lane
+// and lane + 32, coalesced reads of the nu-major table); the warps' sums are
+// added in warp order.
+__global__ void __launch_bounds__(256) k_far_tail_f32(int Ls, int l0, int ntail,
                                                       const int* __restrict__ rows,
                                                       const int* __restrict__ rowptr,
                                                       const int2* __restrict__ rc,
                                                       const float2* __restrict__ S,
                                                       const float2* __restrict__ xhat,
                                                       float2* __restrict__ yhat) {
-  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  if (w >= nrows * ntail) return;
-  const int k = w / ntail, f = w - k * ntail, l = l0 + f;
+  __shared__ float2 red[8][TP];
+  const int k = blockIdx.x / ntail, f = blockIdx.x - k * ntail, l = l0 + f;
   const int r = rows[k];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
-  for (int bi = rowptr[r]; bi < rowptr[r + 1]; ++bi) {
+  for (int bi = rowptr[r] + w; bi < rowptr[r + 1]; bi += 8) {
     const float2* xc = xhat + (size_t)rc[bi].y * TP * Ls + l;
     const float2 x0 = xc[(size_t)lane * Ls], x1 = xc[(size_t)(lane + 32) * Ls];
     const float2* Sb = S + ((size_t)bi * ntail + f) * TP * TP;
+#pragma unroll 8
     for (int nu = 0; nu < TP; ++nu) {
       const float2 xv = make_float2(__shfl_sync(0xffffffffu, nu < 32 ? x0.x : x1.x, nu & 31),
                                     __shfl_sync(0xffffffffu, nu < 32 ? x0.y : x1.y, nu & 31));
-      cfma(a0, Sb[lane * TP + nu], xv);
-      cfma(a1, Sb[(lane + 32) * TP + nu], xv);
+      cfma(a0, Sb[nu * TP + lane], xv);
+      cfma(a1, Sb[nu * TP + lane + 32], xv);
     }
   }
-  float2* yr = yhat + (size_t)r * TP * Ls + l;
-  yr[(size_t)lane * Ls] = cadd(yr[(size_t)lane * Ls], a0);
-  yr[(size_t)(lane + 32) * Ls] = cadd(yr[(size_t)(lane + 32) * Ls], a1);
+  red[w][lane] = a0;
+  red[w][lane + 32] = a1;
+  __syncthreads();
+  if (w == 0) {
+    float2 s0 = red[0][lane], s1 = red[0][lane + 32];
+    for (int v = 1; v < 8; ++v) {
+      s0 = cadd(s0, red[v][lane]);
+      s1 = cadd(s1, red[v][lane + 32]);
+    }
+    float2* yr = yhat + (size_t)r * TP * Ls + l;
+    yr[(size_t)lane * Ls] = cadd(yr[(size_t)lane * Ls], s0);
+    yr[(size_t)(lane + 32) * Ls] = cadd(yr[(size_t)(lane + 32) * Ls], s1);
+  }
 }
 
 // Position in the sequence (item, chunk, block, term) of one CTA: items
@@ -163,9 +180,10 @@ struct Seq {
   int b0, b1;
   int n_items, stride, nch;
   const int4* items;
+  const int* order;  // launch position -> item (largest items first)
   const int* rank;
-  __device__ void start(const int4* items_, int n_items_, int nch_, const int* rank_) {
-    items = items_; n_items = n_items_; nch = nch_; rank = rank_;
+  __device__ void start(const int4* items_, const int* order_, int n_items_, int nch_, const int* rank_) {
+    items = items_; order = order_; n_items = n_items_; nch = nch_; rank = rank_;
     stride = gridDim.x;
     ii = blockIdx.x;
     t = 0;
@@ -175,7 +193,7 @@ struct Seq {
   __device__ void enter() {  // first block of item ii
     ch = 0;
     if (ii < n_items) {
-      const int4 it = items[ii];
+      const int4 it = items[order[ii]];
       b0 = it.y;
       b1 = it.z;
     } else {
@@ -217,7 +235,7 @@ __device__ __forceinline__ float2 term_d(const Seq& q, const float2* __restrict_
 
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_far_coupling_tc2(int Ls, int nch, int cap, int n_items, const int4* __restrict__ items,
-                       const int2* __restrict__ blocks, const int* __restrict__ rank,
+                       const int* __restrict__ order, const int2* __restrict__ blocks, const int* __restrict__ rank,
                        const int64_t* __restrict__ first, const unsigned char* __restrict__ img,
                        const float2* __restrict__ Df, const float2* __restrict__ xhat,
                        float2* __restrict__ part, int* __restrict__ err, uint64_t lim, int probe) {
@@ -264,7 +282,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     constexpr uint32_t ID_RE = idesc_bf16(128, 64, false);
     constexpr uint32_t ID_NEG = idesc_bf16(128, 64, true);
     Seq q;
-    q.start(items, n_items, nch, rank);
+    q.start(items, order, n_items, nch, rank);
     uint32_t ib = 0, ia = 0;
     bool first_term = true;
     while (!q.done()) {
@@ -309,7 +327,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     // ------------------------------------------------------------ B loader
     if (lane == 0) {
       Seq q;
-      q.start(items, n_items, nch, rank);
+      q.start(items, order, n_items, nch, rank);
       for (; !q.done(); q.next(), ++n_issued) {
         const int s = (int)(n_issued % NSTAGE);
         if (n_issued >= NSTAGE &&
@@ -325,7 +343,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int qd = warp & 3;
     const uint32_t trow = tmem + ((uint32_t)(32 * qd) << 16);
     Seq q;
-    q.start(items, n_items, nch, rank);
+    q.start(items, order, n_items, nch, rank);
     uint32_t ia = 0;
     while (!q.done()) {
       const int ab = (int)(ia & 1u);
@@ -378,7 +396,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
     for (int mu = 0; mu < MUE; ++mu) yr[mu] = yi[mu] = 0.f;
     Seq q, qp;
-    q.start(items, n_items, nch, rank);
+    q.start(items, order, n_items, nch, rank);
     qp = q;
     // d_t of the next three terms, loaded ahead of their accumulators
     float2 d0 = term_d(qp, Df, cap, Ls, qd, lane);
@@ -425,7 +443,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         // the item's partial tile of this chunk (zero for an item without terms)
         const int l = 128 * ch + 32 * qd + lane;
         if (l < Ls) {
-          float2* dst = part + ((size_t)ii * TP + mu0) * Ls + l;
+          float2* dst = part + ((size_t)order[ii] * TP + mu0) * Ls + l;
 #pragma unroll
           for (int mu = 0; mu < MUE; ++mu) dst[(size_t)mu * Ls] = make_float2(yr[mu], yi[mu]);
         }
@@ -515,7 +533,8 @@ int far_coupling_tc2(cqm_handle* h, int* l_tail_out) {
   ProfScope ps_(h, CQM_K_FAR_COUPLING);  // one timed unit: the chunks and the tail
   {
     k_far_coupling_tc2<<<h->n_far_items, NTHREADS, SMEM, h->stream>>>(
-        h->Ls, nch, h->rank_cap, h->n_far_items, h->far_items.p, h->far_rc.p, h->far_rank.p, h->tc2_first.p,
+        h->Ls, nch, h->rank_cap, h->n_far_items, h->far_items.p, h->far_order.p, h->far_rc.p, h->far_rank.p,
+        h->tc2_first.p,
         h->tc2_img.p, h->farD_f.p, h->xhat_f.p, h->part_f.p, h->flag.p + 1, h->wait_limit_ns,
         h->wait_probe ? 1 : 0);
     h->wait_probe = false;  // one-shot
@@ -523,9 +542,8 @@ int far_coupling_tc2(cqm_handle* h, int* l_tail_out) {
   CQM_CHECK_LAUNCH();
   if (ntail > 0) {
     const int nfr = (int)h->h_far_rows.size();
-    const int warps = nfr * ntail;
-    k_far_tail_f32<<<(unsigned)((warps + 7) / 8), 256, 0, h->stream>>>(
-        h->Ls, l_tail, ntail, nfr, h->d_far_rows.p, h->far_rowptr.p, h->far_rc.p, h->tc2_tail.p,
+    k_far_tail_f32<<<(unsigned)(nfr * ntail), 256, 0, h->stream>>>(
+        h->Ls, l_tail, ntail, h->d_far_rows.p, h->far_rowptr.p, h->far_rc.p, h->tc2_tail.p,
         h->xhat_f.p, h->yhat_f.p);
     CQM_CHECK_LAUNCH();
   }
