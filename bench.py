@@ -283,6 +283,39 @@ def kernel_models(info, Ls, p, tensor_cores, tf32=None, sinfo=None, launches_per
     return models
 
 
+def cqm_R(N):
+    """CQM radius (1e-10)^(1/(2L)), L = N + 1."""
+    return 1e-10 ** (1.0 / (2 * (N + 1)))
+
+
+def mot_models(info, N, launches_per_step):
+    """FP64 work of the marching-on-in-time kernels.  History of step n
+    (eq. fastrhs): the convolution sum_{k<n} dhat_t[n-k] q_k of every rank
+    term (complex times real: 4 flops per entry and lag; 64 entries for a far
+    term, the column cluster for a near one, taken as the mean leaf size) and
+    the real part of C_t z_t (4 flops per entry of C_t), summed over the
+    steps and divided by the launches.  Step: the dense inverse of Vhat_0
+    applied (2 M^2 flops) and the basis coefficients of the new density."""
+    M = info["nt"]
+    leaf = M / max(1, info["n_leaves"])
+    lags = N * (N + 1) / 2.0
+    per_lag = 4.0 * (info["rank_sum_far"] * 64 + info["rank_sum_near"] * leaf)
+    per_step = 4.0 * (info["rank_sum_far"] * 4096 + info["near_rank_entries"])
+    fp64 = dict(bound="alu", peak=FP64_PEAK_TFLOPS, unit="TFLOP/s",
+                peak_source="recipe nominal FP64 rate of a GB300 (1.25 TFLOP/s; a probe measured 1.19)")
+    lps = launches_per_step or {}
+    models = {}
+    if lps.get("mot_history"):
+        models["mot_history"] = dict(fp64, work=(per_lag * lags + per_step * N) / lps["mot_history"],
+                                     what="FP64 history sums of the march (eq. fastrhs)")
+    if lps.get("mot_step"):
+        models["mot_step"] = dict(bound="hbm", peak=_peaks()[0]["hbm_gbs"], unit="GB/s",
+                                  work=8.0 * M * M * (N + 1) / lps["mot_step"],
+                                  peak_source="measured STREAM-style copy, MEASURED_PEAKS.json hbm_gbs",
+                                  what="inverse of Vhat_0 streamed once per step (8 B per entry)")
+    return models
+
+
 def roofline_of(prof, models):
     """Roofline of the dominant modelled kernel (live CUDA-event timings)."""
     timed = [(k, v) for k, v in prof.items() if k in models and v[0]]
@@ -338,10 +371,15 @@ def run_ours(args):
     q = torch.empty((L, M), dtype=torch.float64, device="cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
+    mot = args.scheme == "mot"
+
     def step():
         op = CqmBem(m.xyz, m.tri, dt, N, W["bdf"], **params)
         op.rhs_plane_wave(pulse.direction, pulse.width, pulse.delay, out=rhs)
-        op.solve(rhs, out=q)
+        if mot:
+            op.solve_mot(rhs, out=q)
+        else:
+            op.solve(rhs, out=q)
         return op
 
     for _ in range(args.warmup):
@@ -383,7 +421,10 @@ def run_ours(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         op = CqmBem(m.xyz, m.tri, dt, N, W["bdf"], **params)
-        op.solve(rhs_host.numpy(), out=q_host.numpy())
+        if mot:
+            op.solve_mot(rhs_host.numpy(), out=q_host.numpy())
+        else:
+            op.solve(rhs_host.numpy(), out=q_host.numpy())
         op.close()
         torch.cuda.synchronize()
         e2e_times.append(time.perf_counter() - t0)
@@ -392,7 +433,7 @@ def run_ours(args):
 
     # the workload's per-frequency solution, for the oracle comparison (untimed)
     qhat_gpu = None
-    if rank == 0 and not args.no_cpu_baseline and world == 1:
+    if rank == 0 and not args.no_cpu_baseline and world == 1 and not mot:
         op = CqmBem(m.xyz, m.tri, dt, N, W["bdf"], **params)
         g = op.forward_transform(rhs)
         qhat_gpu = op.solve_frequencies(g)[0].cpu().numpy()
@@ -406,6 +447,8 @@ def run_ours(args):
     p = W["cheb_m"] ** 3
     lps = {k: v[0] / args.steps for k, v in prof.items()}
     models = kernel_models(inf, Ls, p, inf["tensor_cores"], tf32_measured, sinfos[-1], lps)
+    if mot:
+        models.update(mot_models(inf, N, lps))
     lat = sorted(times)
     clocks = clk.summary()
     line = {
@@ -451,7 +494,19 @@ def run_ours(args):
             line["step_error"] = {"error": str(e)}
     if args.dense_baseline:
         line["dense_fp64_gpu"] = dense_baseline(m, pulse, W, q)
-    if not args.no_cpu_baseline and world == 1:  # rank 0 at N = 1 only
+    if mot:
+        line["scheme"] = ("marching on in time (Sec. 3.2) with the compressed weights "
+                          "(eqs. fastdft, fastrhs), FP64")
+        line["dtype"] = "f64 (marching on in time); fp64 MACA pivots, float-float MACA kernel evaluations"
+        op = CqmBem(m.xyz, m.tri, dt, N, W["bdf"], **dict(params, profile=0))
+        qd = op.solve(rhs).cpu().numpy()
+        op.close()
+        a = q.cpu().numpy()
+        line["accuracy"]["mot_vs_decoupled"] = float(
+            np.max(np.linalg.norm(a - qd, axis=1)) / np.max(np.linalg.norm(qd, axis=1)))
+        line["accuracy"]["note"] = ("the march is exactly causal; the decoupled solve carries the "
+                                    f"O(R^L) = {cqm_R(N) ** (N + 1):.1e} aliasing of the CQM transform")
+    if not args.no_cpu_baseline and world == 1 and not mot:  # rank 0 at N = 1 only
         cb, qref = cpu_baseline()
         line["cpu_baseline"] = cb
         errs = {int(l): float(np.max(np.abs(qhat_gpu[l] - ref)) / np.max(np.abs(ref)))
@@ -709,6 +764,8 @@ def main():
     ap.add_argument("--N", type=int, default=None, help="time-step count override")
     ap.add_argument("--tensor-cores", type=int, choices=[0, 1, 2], default=None,
                     help="far-field coupling on the tensor cores in bf16 (1), TF32 (2), or FP32 SIMT (0)")
+    ap.add_argument("--scheme", choices=["decoupled", "mot"], default="decoupled",
+                    help="time stepping: the decoupled frequency-domain solve or marching on in time")
     ap.add_argument("--expand-far", type=int, choices=[0, 1], default=None,
                     help="override the expanded far table of the FP64-accurate apply")
     ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batch64", "serve"],

@@ -168,31 +168,49 @@ __global__ void __launch_bounds__(256) k_maca_slice(MacaBlocks B, Geom g, Quad q
     const int npair = diag ? nr * (nr + 1) / 2 : nr * nc;
     const float2* pd = (const float2*)B.pt_r;
     const float2* pc = (const float2*)B.pt_c;
-    for (int e2 = w; e2 < npair; e2 += nw) {
-      int i, j;
-      if (diag) {
-        i = 0;
-        int rem = e2;
-        while (rem >= nr - i) {
-          rem -= nr - i;
-          ++i;
+    // The warp's pairs e2 = w, w + nw, ... in groups of 32: lane kk keeps the
+    // sum of the group's pair kk, and the FP64 part (exp(-s r0), the product,
+    // the conversion) runs once per group with every lane busy, instead of on
+    // one lane per pair (an FP64 warp instruction costs the same pipe time
+    // with one active lane as with 32).
+    for (int g0 = w; g0 < npair; g0 += 32 * nw) {
+      ff mr = {0.f, 0.f}, mim = {0.f, 0.f};
+      int me = -1, mrow = 0, mcol = 0;
+      for (int kk = 0; kk < 32; ++kk) {
+        const int e2 = g0 + kk * nw;
+        if (e2 >= npair) break;
+        int i, j;
+        if (diag) {
+          i = 0;
+          int rem = e2;
+          while (rem >= nr - i) {
+            rem -= nr - i;
+            ++i;
+          }
+          j = i + rem;
+        } else {
+          i = e2 / nc;
+          j = e2 - i * nc;
         }
-        j = i + rem;
-      } else {
-        i = e2 / nc;
-        j = e2 - i * nc;
+        const int e = i * nc + j;
+        const int64_t o = B.pt_off[base + e];
+        ff ar = {0.f, 0.f}, ai = {0.f, 0.f};
+        lane_points_ff(pd + o, pc + o, B.pt_cnt[base + e], lane, sf, T, ar, ai);
+        ar = warp_sum_ff(ar);
+        ai = warp_sum_ff(ai);
+        if (lane == kk) {
+          mr = ar;
+          mim = ai;
+          me = e;
+          mrow = i;
+          mcol = j;
+        }
       }
-      const int e = i * nc + j;
-      const int64_t o = B.pt_off[base + e];
-      ff ar = {0.f, 0.f}, ai = {0.f, 0.f};
-      lane_points_ff(pd + o, pc + o, B.pt_cnt[base + e], lane, sf, T, ar, ai);
-      ar = warp_sum_ff(ar);
-      ai = warp_sum_ff(ai);
-      if (lane == 0) {
-        const double2 E0 = cexp_c(B.pt_r0[base + e], 1.0, sk, q);
-        const double2 v = cmul(make_double2(ff_to_double(ar), ff_to_double(ai)), E0);
-        out[e] = v;
-        if (diag) out[j * nc + i] = v;
+      if (me >= 0) {
+        const double2 E0 = cexp_c(B.pt_r0[base + me], 1.0, sk, q);
+        const double2 v = cmul(make_double2(ff_to_double(mr), ff_to_double(mim)), E0);
+        out[me] = v;
+        if (diag) out[mcol * nc + mrow] = v;
       }
     }
     return;
@@ -365,6 +383,10 @@ __global__ void __launch_bounds__(256) k_maca_fibre(MacaBlocks B, Geom g, Quad q
     const double r0 = B.pt_r0[k];
     const float2* pd = (const float2*)B.pt_r + o;
     const float2* pc = (const float2*)B.pt_c + o;
+    // lane gi NF + f keeps frequency f of the warp's group gi; the FP64 part
+    // (exp(-s r0), the product, the conversion) runs for 32 / NF groups at once
+    ff mr = {0.f, 0.f}, mim = {0.f, 0.f};
+    int mf = -1, gi = 0;
     for (int f0 = w * NF; f0 < B.Ls; f0 += nw * NF) {
       const int nf = min(NF, B.Ls - f0);
       ffs sv[NF];
@@ -399,13 +421,21 @@ __global__ void __launch_bounds__(256) k_maca_fibre(MacaBlocks B, Geom g, Quad q
         ar[f] = warp_sum_ff(ar[f]);
         ai[f] = warp_sum_ff(ai[f]);
       }
-      // lane f < nf scales frequency f by exp(-s_f r0)
 #pragma unroll
       for (int f = 0; f < NF; ++f)
-        if (lane == f && f < nf)
-          out[f0 + f] = cmul(make_double2(ff_to_double(ar[f]), ff_to_double(ai[f])),
-                             cexp_c(r0, 1.0, s[f0 + f], q));
+        if (lane == gi * NF + f && f < nf) {
+          mr = ar[f];
+          mim = ai[f];
+          mf = f0 + f;
+        }
+      if (++gi == 32 / NF) {
+        if (mf >= 0)  // frequency mf scaled by exp(-s r0)
+          out[mf] = cmul(make_double2(ff_to_double(mr), ff_to_double(mim)), cexp_c(r0, 1.0, s[mf], q));
+        mf = -1;
+        gi = 0;
+      }
     }
+    if (mf >= 0) out[mf] = cmul(make_double2(ff_to_double(mr), ff_to_double(mim)), cexp_c(r0, 1.0, s[mf], q));
     return;
   }
   if (B.pt_r) {

@@ -81,3 +81,16 @@ def test_maca_and_arnoldi_models(bench):
     # without counts the models are left out
     m0 = bench.kernel_models(info, Ls=129, p=64, tensor_cores=1)
     assert "maca_slice" not in m0 and "arnoldi" not in m0
+
+
+def test_mot_models(bench):
+    info = dict(nt=1280, n_leaves=64, rank_sum_far=100, rank_sum_near=50, near_rank_entries=40000)
+    N = 64
+    m = bench.mot_models(info, N, {"mot_history": 64.0, "mot_step": 65.0})
+    lags = N * (N + 1) / 2
+    per_lag = 4.0 * (100 * 64 + 50 * 20.0)
+    per_step = 4.0 * (100 * 4096 + 40000)
+    assert m["mot_history"]["work"] == pytest.approx((per_lag * lags + per_step * N) / 64.0)
+    assert m["mot_history"]["bound"] == "alu" and m["mot_history"]["unit"] == "TFLOP/s"
+    assert m["mot_step"]["work"] == pytest.approx(8.0 * 1280 * 1280 * 65 / 65.0)
+    assert abs(bench.cqm_R(N) ** (N + 1) - 1e-5) < 1e-12
