@@ -405,18 +405,32 @@ __global__ void __launch_bounds__(256) k_far_dense_ff(int Ls, int p, int nrows, 
     const ffc x0 = has0 ? ffc_from(xc[(size_t)lane * Ls]) : ffc_zero();
     const ffc x1 = has1 ? ffc_from(xc[(size_t)(lane + 32) * Ls]) : ffc_zero();
     const ffc* Sb = S + ((size_t)bi * Ls + l) * pp;
-    for (int nu = 0; nu < p; ++nu) {
-      const ffc src = nu < 32 ? x0 : x1;
-      ffc xv;
-      xv.rh = __shfl_sync(0xffffffffu, src.rh, nu & 31);
-      xv.ih = __shfl_sync(0xffffffffu, src.ih, nu & 31);
-      xv.rl = __shfl_sync(0xffffffffu, src.rl, nu & 31);
-      xv.il = __shfl_sync(0xffffffffu, src.il, nu & 31);
-      if (has0) ffc_mac(acc0, Sb[(size_t)nu * p + lane], xv);
-      if (has1) ffc_mac(acc1, Sb[(size_t)nu * p + lane + 32], xv);
-      if ((nu & 15) == 15) {
-        ffc_renorm(acc0);
-        ffc_renorm(acc1);
+    // nu in groups of 4: the group's loads are issued together
+    for (int n0 = 0; n0 < p; n0 += 4) {
+      ffc s0[4], s1[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int nu = n0 + u;
+        s0[u] = (has0 && nu < p) ? Sb[(size_t)nu * p + lane] : ffc_zero();
+        s1[u] = (has1 && nu < p) ? Sb[(size_t)nu * p + lane + 32] : ffc_zero();
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int nu = n0 + u;
+        if (nu < p) {
+          const ffc src = nu < 32 ? x0 : x1;
+          ffc xv;
+          xv.rh = __shfl_sync(0xffffffffu, src.rh, nu & 31);
+          xv.ih = __shfl_sync(0xffffffffu, src.ih, nu & 31);
+          xv.rl = __shfl_sync(0xffffffffu, src.rl, nu & 31);
+          xv.il = __shfl_sync(0xffffffffu, src.il, nu & 31);
+          if (has0) ffc_mac(acc0, s0[u], xv);
+          if (has1) ffc_mac(acc1, s1[u], xv);
+          if ((nu & 15) == 15) {
+            ffc_renorm(acc0);
+            ffc_renorm(acc1);
+          }
+        }
       }
     }
     ffc_renorm(acc0);
@@ -533,14 +547,25 @@ __global__ void __launch_bounds__(256) k_near_dense_ff(int M, int Ls, const int*
     const int cb = begin[c], nc = end[c] - cb;
     const ffc xj = lane < nc ? ffc_from(xl[perm[cb + lane]]) : ffc_zero();
     const ffc* Vb = V + voff[bi] + (size_t)l * nc * nr;
-    for (int j = 0; j < nc; ++j) {
-      ffc xv;
-      xv.rh = __shfl_sync(0xffffffffu, xj.rh, j);
-      xv.ih = __shfl_sync(0xffffffffu, xj.ih, j);
-      xv.rl = __shfl_sync(0xffffffffu, xj.rl, j);
-      xv.il = __shfl_sync(0xffffffffu, xj.il, j);
-      if (lane < nr) ffc_mac(acc, Vb[(size_t)j * nr + lane], xv);
-      if ((j & 15) == 15) ffc_renorm(acc);
+    // columns in groups of 8: the group's loads are issued together
+    for (int j0 = 0; j0 < nc; j0 += 8) {
+      ffc v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        v[u] = (lane < nr && j0 + u < nc) ? Vb[(size_t)(j0 + u) * nr + lane] : ffc_zero();
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int j = j0 + u;
+        if (j < nc) {
+          ffc xv;
+          xv.rh = __shfl_sync(0xffffffffu, xj.rh, j);
+          xv.ih = __shfl_sync(0xffffffffu, xj.ih, j);
+          xv.rl = __shfl_sync(0xffffffffu, xj.rl, j);
+          xv.il = __shfl_sync(0xffffffffu, xj.il, j);
+          if (lane < nr) ffc_mac(acc, v[u], xv);
+          if ((j & 15) == 15) ffc_renorm(acc);
+        }
+      }
     }
     ffc_renorm(acc);
   }

@@ -94,14 +94,19 @@ __global__ void __launch_bounds__(256) k_near_dense(int M, int Ls, const int* __
     const C xj = lane < nc ? to_c(xl[perm[cb + lane]], (C*)0) : cz<C>();
     const VT* Vb = V + voff[bi] + (size_t)l * nc * nr;
     C bacc = cz<C>();
-    for (int j = 0; j < nc; ++j) {
-      C xv;
-      xv.x = __shfl_sync(0xffffffffu, xj.x, j);
-      xv.y = __shfl_sync(0xffffffffu, xj.y, j);
-      if (lane < nr) {
-        const C v = Vb[(size_t)j * nr + lane];
-        bacc.x = fma(v.x, xv.x, fma(-v.y, xv.y, bacc.x));
-        bacc.y = fma(v.x, xv.y, fma(v.y, xv.x, bacc.y));
+    // columns in groups of 8: the group's loads are issued together
+    for (int j0 = 0; j0 < nc; j0 += 8) {
+      C v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        v[u] = (lane < nr && j0 + u < nc) ? Vb[(size_t)(j0 + u) * nr + lane] : cz<C>();
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        C xv;
+        xv.x = __shfl_sync(0xffffffffu, xj.x, (j0 + u) & 31);
+        xv.y = __shfl_sync(0xffffffffu, xj.y, (j0 + u) & 31);
+        bacc.x = fma(v[u].x, xv.x, fma(-v[u].y, xv.y, bacc.x));
+        bacc.y = fma(v[u].x, xv.y, fma(v[u].y, xv.x, bacc.y));
       }
     }
     acc = cadd(acc, to_d(bacc));
