@@ -26,7 +26,10 @@ based on Hierarchical Matrices and Adaptive Cross Approximation") step by step:
                     and the H^2-expanded matrices V_l.
 * ``maca``       -- multivariate adaptive cross approximation (Sec. 5.1, Alg. 2).
 * ``mot``        -- marching on in time with the CQM weights (Sec. 3.2, eq. dft),
-                    the paper's own time stepping (not on the GPU path yet).
+                    the paper's own time stepping.
+* ``dlayer``     -- the P0 Galerkin double layer (Sec. 2.2), its H^2 column
+                    basis, and the direct formulation of the Dirichlet problem
+                    (Sec. 7.2, eq. cqmdir) decoupled in frequency.
 
 Parity pins: every module is checked in ``tests/test_oracle_*.py`` against
 closed forms, invariants or brute force.  The conventions the paper leaves
