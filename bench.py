@@ -372,12 +372,20 @@ def run_ours(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     mot = args.scheme == "mot"
+    dirichlet = args.scheme == "dirichlet"
+    # Dirichlet data of sound-soft scattering: g = -u_inc on the boundary, as
+    # P0 coefficients (the Galerkin data divided by the element areas)
+    P = m.xyz[m.tri]
+    area = torch.from_numpy(0.5 * np.linalg.norm(np.cross(P[:, 1] - P[:, 0], P[:, 2] - P[:, 0]), axis=1)).cuda()
 
     def step():
         op = CqmBem(m.xyz, m.tri, dt, N, W["bdf"], **params)
         op.rhs_plane_wave(pulse.direction, pulse.width, pulse.delay, out=rhs)
         if mot:
             op.solve_mot(rhs, out=q)
+        elif dirichlet:
+            rhs.div_(area).neg_()
+            op.solve_dirichlet(rhs, out=q)
         else:
             op.solve(rhs, out=q)
         return op
@@ -423,6 +431,8 @@ def run_ours(args):
         op = CqmBem(m.xyz, m.tri, dt, N, W["bdf"], **params)
         if mot:
             op.solve_mot(rhs_host.numpy(), out=q_host.numpy())
+        elif dirichlet:
+            op.solve_dirichlet(rhs_host.numpy(), out=q_host.numpy())
         else:
             op.solve(rhs_host.numpy(), out=q_host.numpy())
         op.close()
@@ -433,7 +443,7 @@ def run_ours(args):
 
     # the workload's per-frequency solution, for the oracle comparison (untimed)
     qhat_gpu = None
-    if rank == 0 and not args.no_cpu_baseline and world == 1 and not mot:
+    if rank == 0 and not args.no_cpu_baseline and world == 1 and not mot and not dirichlet:
         op = CqmBem(m.xyz, m.tri, dt, N, W["bdf"], **params)
         g = op.forward_transform(rhs)
         qhat_gpu = op.solve_frequencies(g)[0].cpu().numpy()
@@ -506,7 +516,10 @@ def run_ours(args):
             np.max(np.linalg.norm(a - qd, axis=1)) / np.max(np.linalg.norm(qd, axis=1)))
         line["accuracy"]["note"] = ("the march is exactly causal; the decoupled solve carries the "
                                     f"O(R^L) = {cqm_R(N) ** (N + 1):.1e} aliasing of the CQM transform")
-    if not args.no_cpu_baseline and world == 1 and not mot:  # rank 0 at N = 1 only
+    if dirichlet:
+        line["scheme"] = ("direct formulation of sound-soft scattering (Sec. 7.2, eq. cqmdir) decoupled "
+                          "in frequency: V qhat = (-1/2 M + K) ghat, g = -u_inc")
+    if not args.no_cpu_baseline and world == 1 and not mot and not dirichlet:  # rank 0 at N = 1 only
         cb, qref = cpu_baseline()
         line["cpu_baseline"] = cb
         errs = {int(l): float(np.max(np.abs(qhat_gpu[l] - ref)) / np.max(np.abs(ref)))
@@ -764,8 +777,9 @@ def main():
     ap.add_argument("--N", type=int, default=None, help="time-step count override")
     ap.add_argument("--tensor-cores", type=int, choices=[0, 1, 2], default=None,
                     help="far-field coupling on the tensor cores in bf16 (1), TF32 (2), or FP32 SIMT (0)")
-    ap.add_argument("--scheme", choices=["decoupled", "mot"], default="decoupled",
-                    help="time stepping: the decoupled frequency-domain solve or marching on in time")
+    ap.add_argument("--scheme", choices=["decoupled", "mot", "dirichlet"], default="decoupled",
+                    help="the decoupled single-layer solve, marching on in time, or the direct "
+                         "Dirichlet formulation with the double layer")
     ap.add_argument("--expand-far", type=int, choices=[0, 1], default=None,
                     help="override the expanded far table of the FP64-accurate apply")
     ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batch64", "serve"],

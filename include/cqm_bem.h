@@ -98,7 +98,8 @@ typedef struct cqm_params {
   int32_t rank_cap;       /* rank slots reserved per block (1..64)         [32]  */
   int32_t gmres_restart;  /* Krylov dimension per cycle                    [50]  */
   int32_t gmres_max_iter; /* total Arnoldi steps cap                       [3000] */
-  double gmres_tol;       /* relative residual target ||r_l|| <= tol ||ghat_l|| [1e-13] */
+  double gmres_tol;       /* residual target ||r_l|| <= tol max(||ghat_l||, 1e-6 max_k ||ghat_k||):
+                             every frequency weighs the same in the time steps [1e-13] */
   int32_t profile;        /* nonzero: time every kernel launch with CUDA events [0] */
   int32_t precond;        /* H2MACA: right-precondition GMRES with the inverses of the
                              leaf diagonal near blocks, per frequency     [1]   */
@@ -169,7 +170,8 @@ typedef struct cqm_solve_info {
   int32_t restarts;
   int32_t converged;            /* frequencies meeting gmres_tol */
   int32_t Ls;
-  double max_rel_residual;      /* max_l ||ghat_l - V_l qhat_l|| / ||ghat_l|| (true residual, FP64) */
+  double max_rel_residual;      /* max_l ||ghat_l - V_l qhat_l|| / n_l (true residual, FP64), with
+                                   n_l = max(||ghat_l||, 1e-6 max_k ||ghat_k||) */
   double max_imag;              /* max |Im q_n[i]| before taking the real part */
   double t_forward_ms, t_gmres_ms, t_inverse_ms;
   /* Arnoldi work: sum over steps and active frequencies of the basis vectors
@@ -228,6 +230,27 @@ int cqm_bem_solve_mot(cqm_handle* h, const double* rhs, double* density, int32_t
  * path.  W in `mem` memory.  Errors: CQM_EINVAL (n out of range, dense
  * mode), CQM_ENOMEM, CQM_ECUDA. */
 int cqm_bem_mot_weight(cqm_handle* h, int32_t n, double* W, int32_t mem);
+
+/* The direct formulation of the sound-soft (Dirichlet) problem (Sec. 7.2,
+ * eq. cqmdir; Sec. 2.2 for the double layer K), decoupled in frequency as in
+ * the Remark of Sec. 6.2: V_l qhat_l = (-1/2 M + K_l) ghat_l with M the P0
+ * mass matrix diag |tau_i|, then the inverse transform.  g: (N+1) x nt float64,
+ * row n = the P0 (L^2-projection) coefficients of the Dirichlet data at t_n;
+ * q: (N+1) x nt float64, the Neumann data (normal derivative along the outward
+ * normal).  Both in `mem` memory.  K_l has the single layer's quadrature rules
+ * (test i, trial j, no symmetrisation; identical pairs vanish on flat
+ * triangles); its near field is evaluated once per solved frequency (held by
+ * the handle after the first call: near entries x Ls complex), its far field
+ * is U_r S_b W_c^T with the single layer's compressed couplings and the column
+ * basis W_c = int n . grad L_c.  The solve is the single layer's batched GMRES
+ * (info as for cqm_bem_solve).  H2MACA mode only.
+ * Errors: CQM_EINVAL, CQM_ENOMEM, CQM_ENOCONV (results written), CQM_ECUDA. */
+int cqm_bem_solve_dirichlet(cqm_handle* h, const double* g, double* q, int32_t mem,
+                            cqm_solve_info* info);
+
+/* y_l = K_l x_l for the Ls solved frequencies (the double layer of
+ * cqm_bem_solve_dirichlet).  x, y: Ls x nt complex in `mem` memory. */
+int cqm_bem_apply_double_layer(cqm_handle* h, const double* x, double* y, int32_t mem);
 
 /* Galerkin data of the plane-wave pulse u(x,t) = exp(-((t - delay - d.x)/width)^2)
  * at t_n = n dt, n = 0..N, with Radon's 7-point rule per triangle.
@@ -347,7 +370,9 @@ int cqm_bem_inverse_transform(cqm_handle* h, const double* qhat, double* q, int3
 #define CQM_K_MOT_WEIGHTS    27   /* marching on in time: transformed fibres, Vhat_0 and its inverse */
 #define CQM_K_MOT_HISTORY    28   /* marching on in time: history sum of each step (near and far) */
 #define CQM_K_MOT_STEP       29   /* marching on in time: step solve, H2 transforms of the new density */
-#define CQM_K_COUNT          30
+#define CQM_K_DL_SETUP       30   /* double layer: near-field table and leaf column basis */
+#define CQM_K_DL_APPLY       31   /* double layer: near field of an apply (the far field counts as H2 steps) */
+#define CQM_K_COUNT          32
 
 /* Turn per-launch event timing on (nonzero) or off; either way the counters
  * are reset.  Timing adds one event pair per launch on the handle's stream. */

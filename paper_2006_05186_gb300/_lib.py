@@ -33,8 +33,9 @@ EXPORTED = [
     "cqm_cluster_tree_noalloc", "cqm_bem_set_wait_limit",
     "cqm_bem_estimate_bytes", "cqm_server_create", "cqm_bem_submit", "cqm_bem_poll",
     "cqm_server_load", "cqm_server_destroy", "cqm_bem_solve_mot", "cqm_bem_mot_weight",
+    "cqm_bem_solve_dirichlet", "cqm_bem_apply_double_layer",
 ]
-K_COUNT = 30
+K_COUNT = 32
 
 
 class cqm_mesh(C.Structure):
@@ -148,6 +149,8 @@ def load(build_if_missing: bool = False):
         "cqm_bem_solve_frequencies": (C.c_int, [vp, vp, vp, i32, C.POINTER(cqm_solve_info)]),
         "cqm_bem_solve_mot": (C.c_int, [vp, vp, vp, i32, C.POINTER(cqm_solve_info)]),
         "cqm_bem_mot_weight": (C.c_int, [vp, i32, vp, i32]),
+        "cqm_bem_solve_dirichlet": (C.c_int, [vp, vp, vp, i32, C.POINTER(cqm_solve_info)]),
+        "cqm_bem_apply_double_layer": (C.c_int, [vp, vp, vp, i32]),
         "cqm_bem_forward_transform": (C.c_int, [vp, vp, vp, i32]),
         "cqm_bem_inverse_transform": (C.c_int, [vp, vp, vp, i32]),
         "cqm_bem_profile": (C.c_int, [vp, i32]),
@@ -419,6 +422,28 @@ class CqmBem:
         inf = cqm_solve_info()
         _check(self._lib.cqm_bem_solve_mot(self._h, pr, po, mem, C.byref(inf)), "solve_mot")
         self.last_solve_info = _struct_dict(inf)
+        return out
+
+    def solve_dirichlet(self, g, out=None, allow_noconv=False):
+        """Neumann data of the Dirichlet problem with P0 data g (cqm_bem_solve_dirichlet)."""
+        if out is None:
+            out = _like(g, (self.L, self.M), complex_=False)
+        pg, mem = _ptr(g)
+        po, mem2 = _ptr(out)
+        if mem != mem2:
+            raise ValueError("g and the Neumann data must both be host or both device")
+        inf = cqm_solve_info()
+        _check(self._lib.cqm_bem_solve_dirichlet(self._h, pg, po, mem, C.byref(inf)), "solve_dirichlet",
+               allow=(CQM_ENOCONV,) if allow_noconv else ())
+        self.last_solve_info = _struct_dict(inf)
+        return out
+
+    def apply_double_layer(self, x):
+        """y_l = K_l x_l for the solved frequencies."""
+        out = _like(x, (self.Ls, self.M), complex_=True)
+        px, mem = _ptr(x)
+        po, _ = _ptr(out)
+        _check(self._lib.cqm_bem_apply_double_layer(self._h, px, po, mem), "apply_double_layer")
         return out
 
     def mot_weight(self, n):

@@ -131,6 +131,7 @@ int cqm_bem_destroy(cqm_handle* h) {
   h->nearV.free(A); h->nearV_f.free(A); h->nearV_off.free(A); h->farS.free(A);
   h->xhat_f.free(A); h->yhat_f.free(A); h->Uleaf_f.free(A); h->Etr_f.free(A);
   mot_release(h);
+  dl_release(h);
   cudaStreamSynchronize(h->stream);
   prof_release(h);
   delete h;
@@ -462,6 +463,50 @@ int cqm_bem_solve_mot(cqm_handle* h, const double* rhs, double* density, int32_t
   return CQM_OK;
 }
 
+int cqm_bem_apply_double_layer(cqm_handle* h, const double* x, double* y, int32_t mem) {
+  if (!h || !x || !y || (mem != CQM_MEM_HOST && mem != CQM_MEM_DEVICE)) return CQM_EINVAL;
+  set_last_error("");
+  const size_t n = (size_t)h->Ls * h->M;
+  Scratch S(&h->alloc);
+  const double2* dx = (const double2*)x;
+  double2* dy = (double2*)y;
+  if (mem == CQM_MEM_HOST) {
+    double2* t;
+    CQM_TRY(S.get(&t, n));
+    CQM_CUDA_TRY(cudaMemcpyAsync(t, x, n * sizeof(double2), cudaMemcpyHostToDevice, h->stream));
+    dx = t;
+    CQM_TRY(S.get(&dy, n));
+  }
+  CQM_TRY(dl_apply(h, dx, dy));
+  if (mem == CQM_MEM_HOST)
+    CQM_CUDA_TRY(cudaMemcpyAsync(y, dy, n * sizeof(double2), cudaMemcpyDeviceToHost, h->stream));
+  CQM_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  return CQM_OK;
+}
+
+int cqm_bem_solve_dirichlet(cqm_handle* h, const double* g, double* q, int32_t mem, cqm_solve_info* info) {
+  if (!h || !g || !q || (mem != CQM_MEM_HOST && mem != CQM_MEM_DEVICE)) return CQM_EINVAL;
+  set_last_error("");
+  const size_t nt = (size_t)h->L * h->M;
+  Scratch S(&h->alloc);
+  const double* dg = g;
+  double* dq = q;
+  if (mem == CQM_MEM_HOST) {
+    double* t;
+    CQM_TRY(S.get(&t, nt));
+    CQM_CUDA_TRY(cudaMemcpyAsync(t, g, nt * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    dg = t;
+    CQM_TRY(S.get(&dq, nt));
+  }
+  cqm_solve_info loc{};
+  const int st = dl_solve(h, dg, dq, info ? info : &loc);
+  if (st != CQM_OK && st != CQM_ENOCONV) return st;
+  if (mem == CQM_MEM_HOST)
+    CQM_CUDA_TRY(cudaMemcpyAsync(q, dq, nt * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CQM_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  return st;
+}
+
 int cqm_bem_mot_weight(cqm_handle* h, int32_t n, double* W, int32_t mem) {
   if (!h || !W || (mem != CQM_MEM_HOST && mem != CQM_MEM_DEVICE)) return CQM_EINVAL;
   set_last_error("");
@@ -672,7 +717,7 @@ static const char* k_names[CQM_K_COUNT] = {
     "maca_pivot", "maca_fibre", "maca_finalize", "near_apply", "leaf_forward", "upsweep",
     "far_coupling", "downsweep", "leaf_backward", "dense_apply", "arnoldi", "gmres_other",
     "forward_dft", "inverse_dft", "rhs", "precond", "near_exact", "far_exact", "expand", "points", "mot_weights", "mot_history",
-    "mot_step"};
+    "mot_step", "dl_setup", "dl_apply"};
 
 const char* cqm_bem_kernel_name(int32_t id) {
   return (id >= 0 && id < CQM_K_COUNT) ? k_names[id] : "";

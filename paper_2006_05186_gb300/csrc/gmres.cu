@@ -67,6 +67,28 @@ __global__ void k_restart(int M, int m, const double2* __restrict__ b, const dou
   for (int i = threadIdx.x; i < M; i += blockDim.x) v0[i] = cscale(rl[i], inv);
 }
 
+// Reference norms of the convergence test: bnorm_l <- max(bnorm_l, floor *
+// max_k bnorm_k).  Every frequency enters the time steps with the same weight
+// (inverse transform), so a frequency whose data lie far below the largest
+// (the rounding floor of smooth data at high l) needs only that absolute
+// accuracy; its own relative target could sit below what FP64 residuals
+// resolve.  One CTA.
+__global__ void k_bnorm_floor(int Ls, double* bnorm, double floor_rel) {
+  __shared__ double sh[32];
+  double mx = 0.0;
+  for (int l = threadIdx.x; l < Ls; l += blockDim.x) mx = fmax(mx, bnorm[l]);
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) mx = fmax(mx, sh[w]);
+    sh[0] = mx;
+  }
+  __syncthreads();
+  mx = sh[0];
+  for (int l = threadIdx.x; l < Ls; l += blockDim.x) bnorm[l] = fmax(bnorm[l], floor_rel * mx);
+}
+
 // One Arnoldi step j for every active frequency: w = basis slot j+1 (already
 // holds V v_j) is orthogonalised against v_0..v_j by classical Gram-Schmidt
 // applied twice (CGS2), normalised, and the new Hessenberg column is reduced
@@ -357,6 +379,7 @@ int gmres_solve(cqm_handle* h, const double2* d_b, double2* d_x, cqm_solve_info*
       k_restart<<<Ls, 256, 0, S>>>(M, m, d_b, first ? nullptr : Ax, W.r.p, W.Vb.p, W.bnorm.p,
                                    W.beta.p, W.active.p, W.converged.p, W.g.p, tol, rtol, W.thr.p,
                                    first ? 1 : 0, W.counters.p);
+      if (first) k_bnorm_floor<<<1, 256, 0, S>>>(Ls, W.bnorm.p, 1e-6);
     }
     GM_TRY(cu(cudaGetLastError()));
     GM_TRY(cu(cudaMemsetAsync(W.kdim.p, 0, sizeof(int) * Ls, S)));

@@ -508,15 +508,19 @@ struct OpView {
   const C *nearC, *nearD, *farC, *farD;
   const R *U, *Etr;
   C *xhat, *yhat;
+  const R* Ucol = nullptr;  // column basis of the leaf forward transform (U when null)
 };
 
 template <class R>
-static int apply_t(cqm_handle* h, const OpView<R>& V, const double2* x, double2* y, bool ff = false) {
+static int apply_t(cqm_handle* h, const OpView<R>& V, const double2* x, double2* y, bool ff = false,
+                   bool far_only = false) {
   using C = typename Cplx<R>::type;
   const int nleaf = (int)h->h_leaves.size(), nfr = (int)h->h_far_rows.size();
   const int M = h->M, Ls = h->Ls, p = h->p, m = h->m;
   cudaStream_t S = h->stream;
-  if (ff) {
+  if (far_only) {
+    // the caller has written y
+  } else if (ff) {
     CQM_TRY(near_apply_ff(h, x, y));
   } else if (std::is_same<R, float>::value) {
     CQM_TRY(near_apply_f32(h, x, y));
@@ -530,7 +534,8 @@ static int apply_t(cqm_handle* h, const OpView<R>& V, const double2* x, double2*
     {
       ProfScope ps_(h, CQM_K_LEAF_FORWARD);
       k_leaf_forward<R><<<(unsigned)nleaf, 256, 0, S>>>(M, Ls, p, h->d_leaves.p, h->node_begin.p,
-                                                        h->node_end.p, h->perm.p, V.U, x, V.xhat);
+                                                        h->node_end.p, h->perm.p, V.Ucol ? V.Ucol : V.U,
+                                                        x, V.xhat);
     }
     for (int lv = h->depth - 1; lv >= 0; --lv) {
       const int n0 = h->level_begin[lv], n1 = h->level_begin[lv + 1];
@@ -584,6 +589,14 @@ int apply_compressed(cqm_handle* h, const double2* x, double2* y) {
   OpView<double> V{h->nearC.p, h->nearD.p, h->farC.p, h->farD.p, h->Uleaf.p, h->Etr.p,
                    h->xhat.p, h->yhat.p};
   return apply_t<double>(h, V, x, y, h->params.exact_ff != 0);
+}
+
+// y += U (S_b) W^T x over the far blocks, the FP64-accurate couplings of the
+// handle with the column basis W in place of U (the double layer's far field).
+int apply_far_columns(cqm_handle* h, const double* Wleaf, const double2* x, double2* y) {
+  OpView<double> V{h->nearC.p, h->nearD.p, h->farC.p, h->farD.p, h->Uleaf.p, h->Etr.p,
+                   h->xhat.p, h->yhat.p, Wleaf};
+  return apply_t<double>(h, V, x, y, h->params.exact_ff != 0 && h->factors_ff, true);
 }
 
 int apply_compressed_f32(cqm_handle* h, const double2* x, double2* y) {

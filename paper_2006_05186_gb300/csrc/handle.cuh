@@ -136,6 +136,14 @@ struct cqm_handle {
   cqm::DArray<int64_t> mot_Ue_off;
   double mot_setup_ms = 0.0;
 
+  // double layer (dlayer.cu), built on the first call that needs it: the
+  // near-field table (the expanded near-field layout, FP64) and the leaf
+  // column basis W (M x p, tree order)
+  bool dl_ready = false;
+  cqm::DArray<double2> dl_table;
+  cqm::DArray<int64_t> dl_off;
+  cqm::DArray<double> dl_W;
+
   cqm_setup_info info{};
 
   // per-launch kernel timing (cqm_bem_profile)
@@ -224,6 +232,14 @@ int mot_prepare(cqm_handle* h);
 int mot_weight(cqm_handle* h, int n, double* d_W);  // dense Vhat_n, original numbering
 int mot_solve(cqm_handle* h, const double* d_b, double* d_q, cqm_solve_info* info);
 void mot_release(cqm_handle* h);
+
+// dlayer.cu (double layer, direct Dirichlet formulation)
+int dl_apply(cqm_handle* h, const double2* x, double2* y);  // y_l = K_l x_l, l < Ls
+int dl_solve(cqm_handle* h, const double* d_g, double* d_q, cqm_solve_info* info);
+void dl_release(cqm_handle* h);
+// near_dense.cu / h2.cu pieces the double layer shares
+int near_apply_table(cqm_handle* h, const double2* T, const int64_t* off, const double2* x, double2* y);
+int apply_far_columns(cqm_handle* h, const double* Wleaf, const double2* x, double2* y);
 
 // Kernel timing scope: records an event pair around the launches it encloses.
 struct ProfScope {

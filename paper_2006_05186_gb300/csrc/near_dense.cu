@@ -140,6 +140,19 @@ int build_near_expanded(cqm_handle* h) {
   return CQM_OK;
 }
 
+// y = (table) x over the near field for a table of the layout above (the
+// double layer's near field), FP64.
+int near_apply_table(cqm_handle* h, const double2* T, const int64_t* off, const double2* x, double2* y) {
+  const int nleaf = (int)h->h_leaves.size();
+  if (nleaf == 0) return CQM_OK;
+  dim3 g((unsigned)((h->Ls + 7) / 8), (unsigned)nleaf);
+  k_near_dense<double2><<<g, 256, 0, h->stream>>>(h->M, h->Ls, h->d_leaves.p, h->near_rowptr.p,
+                                                  h->near_rc.p, h->node_begin.p, h->node_end.p,
+                                                  h->perm.p, off, T, x, y);
+  CQM_CHECK_LAUNCH();
+  return CQM_OK;
+}
+
 int near_apply_expanded(cqm_handle* h, const double2* x, double2* y, bool fp64) {
   const int nleaf = (int)h->h_leaves.size();
   if (nleaf == 0) return CQM_OK;
