@@ -21,6 +21,7 @@
 #include <algorithm>
 #include <vector>
 
+#include "ffexp.cuh"
 #include "handle.cuh"
 
 namespace cqm {
@@ -36,79 +37,114 @@ __device__ __forceinline__ void tri_normal(const double* P, double* n) {
   n[2] = c2 * inv;
 }
 
-// Visit this lane's share of the quadrature points of pair (i, j) (test i,
-// trial j; no swap): f(r, c) with c = weight (x - y).n_j / (4 pi r^3).  Rules
-// and singular vertex orders as for the single layer; identical pairs have no
-// points (the integrand vanishes on a flat triangle).
-template <class F>
-__device__ __forceinline__ void dl_pair_points(const Geom& g, const Quad& q, int i, int j, int cse,
-                                               int lane, int nlanes, F&& f) {
-  if (cse == CASE_IDENT) return;
+// Radius of the ball about the centroid that holds triangle t.
+__device__ __forceinline__ double dl_tri_radius(const Geom& g, int t) {
+  const double* P = g.P + 9 * t;
+  const double* c = g.cen + 3 * t;
+  double r2 = 0.0;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const double dx = P[3 * k] - c[0], dy = P[3 * k + 1] - c[1], dz = P[3 * k + 2] - c[2];
+    r2 = fmax(r2, dx * dx + dy * dy + dz * dz);
+  }
+  return sqrt(r2) * (1.0 + 1e-12);
+}
+
+// One quadrature point of pair (i, j) (test i, trial j): r = |x - y| and
+// c = weight (x - y).n_j / (4 pi r^3); the pair's rule data prepared once.
+struct DlPair {
+  int cse, npts, nq;
+  double aa;
+  double X[9], Y[9];  // rule-ordered vertices (singular) or the triangles' own
+  double n[3];
+};
+__device__ __forceinline__ void dl_pair_prepare(const Geom& g, const Quad& q, int i, int j, int cse, DlPair& P) {
+  P.cse = cse;
   const double* Pi = g.P + 9 * i;
   const double* Pj = g.P + 9 * j;
-  double nj[3];
-  tri_normal(Pj, nj);
+  tri_normal(Pj, P.n);
   if (cse == CASE_REGULAR || cse == CASE_NEAR) {
-    const int nq = (cse == CASE_REGULAR) ? 7 : q.n_near;
-    const double aa = g.area[i] * g.area[j];
-    for (int p = lane; p < nq * nq; p += nlanes) {
-      const int qa = p / nq, qb = p - qa * nq;
-      double a0, a1, a2, wa, b0, b1, b2, wb;
-      if (cse == CASE_REGULAR) {
-        radon7(qa, a0, a1, a2, wa);
-        radon7(qb, b0, b1, b2, wb);
-      } else {
-        const double4 A = q.near_pt[qa], B = q.near_pt[qb];
-        a0 = A.x; a1 = A.y; a2 = A.z; wa = A.w;
-        b0 = B.x; b1 = B.y; b2 = B.z; wb = B.w;
-      }
-      const double d0 = (a0 * Pi[0] + a1 * Pi[3] + a2 * Pi[6]) - (b0 * Pj[0] + b1 * Pj[3] + b2 * Pj[6]);
-      const double d1 = (a0 * Pi[1] + a1 * Pi[4] + a2 * Pi[7]) - (b0 * Pj[1] + b1 * Pj[4] + b2 * Pj[7]);
-      const double d2 = (a0 * Pi[2] + a1 * Pi[5] + a2 * Pi[8]) - (b0 * Pj[2] + b1 * Pj[5] + b2 * Pj[8]);
-      const double r = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
-      f(r, (wa * wb * aa) * (d0 * nj[0] + d1 * nj[1] + d2 * nj[2]) / (CQM_FOUR_PI * r * r * r));
+    P.nq = (cse == CASE_REGULAR) ? 7 : q.n_near;
+    P.npts = P.nq * P.nq;
+    P.aa = g.area[i] * g.area[j];
+    for (int k = 0; k < 9; ++k) {
+      P.X[k] = Pi[k];
+      P.Y[k] = Pj[k];
     }
     return;
   }
+  P.nq = 0;
+  P.npts = cse == CASE_IDENT ? 0 : q.ss_n[cse - CASE_VERT];
+  P.aa = 4.0 * g.area[i] * g.area[j];
   int vx[3], vy[3];
   singular_vertices(g.tri, i, j, cse, vx, vy);
-  double X[9], Y[9];
   for (int k = 0; k < 3; ++k) {
     const int tx = (vx[k] == g.tri[3 * i]) ? 0 : (vx[k] == g.tri[3 * i + 1] ? 1 : 2);
     const int ty = (vy[k] == g.tri[3 * j]) ? 0 : (vy[k] == g.tri[3 * j + 1] ? 1 : 2);
     for (int d = 0; d < 3; ++d) {
-      X[3 * k + d] = Pi[3 * tx + d];
-      Y[3 * k + d] = Pj[3 * ty + d];
+      P.X[3 * k + d] = Pi[3 * tx + d];
+      P.Y[3 * k + d] = Pj[3 * ty + d];
     }
   }
-  const int t = cse - CASE_VERT;
-  const double4* pt = q.ss_pt[t];
-  const double* wt = q.ss_w[t];
-  const int n = q.ss_n[t];
-  const double aa = 4.0 * g.area[i] * g.area[j];
-  for (int p = lane; p < n; p += nlanes) {
-    const double4 z = pt[p];
-    const double a0 = 1.0 - z.x, a1 = z.x - z.y, a2 = z.y;
-    const double b0 = 1.0 - z.z, b1 = z.z - z.w, b2 = z.w;
-    const double d0 = (a0 * X[0] + a1 * X[3] + a2 * X[6]) - (b0 * Y[0] + b1 * Y[3] + b2 * Y[6]);
-    const double d1 = (a0 * X[1] + a1 * X[4] + a2 * X[7]) - (b0 * Y[1] + b1 * Y[4] + b2 * Y[7]);
-    const double d2 = (a0 * X[2] + a1 * X[5] + a2 * X[8]) - (b0 * Y[2] + b1 * Y[5] + b2 * Y[8]);
-    const double r = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
-    f(r, (wt[p] * aa) * (d0 * nj[0] + d1 * nj[1] + d2 * nj[2]) / (CQM_FOUR_PI * r * r * r));
+}
+__device__ __forceinline__ void dl_point(const Quad& q, const DlPair& P, int p, double& r, double& c) {
+  double a0, a1, a2, b0, b1, b2, w;
+  if (P.cse == CASE_REGULAR || P.cse == CASE_NEAR) {
+    const int qa = p / P.nq, qb = p - qa * P.nq;
+    double wa, wb;
+    if (P.cse == CASE_REGULAR) {
+      radon7(qa, a0, a1, a2, wa);
+      radon7(qb, b0, b1, b2, wb);
+    } else {
+      const double4 A = q.near_pt[qa], B = q.near_pt[qb];
+      a0 = A.x; a1 = A.y; a2 = A.z; wa = A.w;
+      b0 = B.x; b1 = B.y; b2 = B.z; wb = B.w;
+    }
+    w = wa * wb * P.aa;
+  } else {
+    const int t = P.cse - CASE_VERT;
+    const double4 z = q.ss_pt[t][p];
+    a0 = 1.0 - z.x; a1 = z.x - z.y; a2 = z.y;
+    b0 = 1.0 - z.z; b1 = z.z - z.w; b2 = z.w;
+    w = q.ss_w[t][p] * P.aa;
   }
+  const double* X = P.X;
+  const double* Y = P.Y;
+  const double d0 = (a0 * X[0] + a1 * X[3] + a2 * X[6]) - (b0 * Y[0] + b1 * Y[3] + b2 * Y[6]);
+  const double d1 = (a0 * X[1] + a1 * X[4] + a2 * X[7]) - (b0 * Y[1] + b1 * Y[4] + b2 * Y[7]);
+  const double d2 = (a0 * X[2] + a1 * X[5] + a2 * X[8]) - (b0 * Y[2] + b1 * Y[5] + b2 * Y[8]);
+  r = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+  c = w * (d0 * P.n[0] + d1 * P.n[1] + d2 * P.n[2]) / (CQM_FOUR_PI * r * r * r);
 }
 
-// Near-field table of K: one CTA per near block, a warp per pair, the lanes
-// over the pair's points, NF frequencies per pass (lane f of the warp writes
-// frequency f of the pass).
+// Near-field table of K: one CTA per near block, a warp per pair.  With r0 a
+// lower bound of the pair's distances (0 for pairs sharing a vertex) and
+// d = r - r0 >= 0,
+//   K_l[i][j] = e^{-s_l r0} (A_l + s_l B_l),  A_l = sum c e^{-s_l d},  B_l = sum c r e^{-s_l d}.
+// The lanes take the frequencies (lane + 32 u of a group of 32 UG); the pair's
+// points come in batches of 32, whose geometry one lane each forms in FP64
+// (d, c, c r as float-float pairs in shared memory), and every lane then sums
+// e^{-s d} for its frequencies in float-float on the FP32 pipes (Tang's table
+// method, ffexp.cuh).  The FP64 part (e^{-s r0}, the combination) runs once
+// per pair and frequency with every lane busy.
 __global__ void __launch_bounds__(256) k_dl_near_table(int Ls, Geom g, Quad q, const double2* __restrict__ s,
                                                        const int2* __restrict__ rc,
                                                        const int* __restrict__ begin,
                                                        const int* __restrict__ end,
                                                        const int* __restrict__ perm,
                                                        const int64_t* __restrict__ off,
+                                                       const float2* __restrict__ t2ff,
+                                                       const float4* __restrict__ csff,
                                                        double2* __restrict__ T) {
-  constexpr int NF = 8;
+  constexpr int UG = 4;  // frequencies per lane and group
+  __shared__ float2 t2s[1024];
+  __shared__ float4 css[1024];
+  __shared__ float2 pd[8][32], pc[8][32], pcr[8][32];
+  for (int k = threadIdx.x; k < 1024; k += blockDim.x) {
+    t2s[k] = t2ff[k];
+    css[k] = csff[k];
+  }
+  __syncthreads();
   const int b = blockIdx.x;
   const int2 c2 = rc[b];
   const int rb = begin[c2.x], nr = end[c2.x] - rb, cb = begin[c2.y], nc = end[c2.y] - cb;
@@ -118,32 +154,72 @@ __global__ void __launch_bounds__(256) k_dl_near_table(int Ls, Geom g, Quad q, c
     const int i = e / nc, j = e - i * nc;
     const int I = perm[rb + i], J = perm[cb + j];
     const int cse = pair_case(g, q, I, J);
-    for (int f0 = 0; f0 < Ls; f0 += NF) {
-      const int nf = min(NF, Ls - f0);
-      double2 sv[NF], acc[NF];
+    DlPair P;
+    dl_pair_prepare(g, q, I, J, cse, P);
+    double r0 = 0.0;
+    if (cse == CASE_REGULAR || cse == CASE_NEAR) {
+      const double* ci = g.cen + 3 * I;
+      const double* cj = g.cen + 3 * J;
+      const double dx = ci[0] - cj[0], dy = ci[1] - cj[1], dz = ci[2] - cj[2];
+      r0 = fmax(0.0, sqrt(dx * dx + dy * dy + dz * dz) * (1.0 - 1e-12) - dl_tri_radius(g, I) -
+                         dl_tri_radius(g, J));
+    }
+    for (int fg = 0; fg < Ls; fg += 32 * UG) {
+      ffs sf[UG];
+      ff A[UG][2], B[UG][2];
 #pragma unroll
-      for (int f = 0; f < NF; ++f) {
-        sv[f] = f < nf ? s[f0 + f] : make_double2(0.0, 0.0);
-        acc[f] = make_double2(0.0, 0.0);
+      for (int u = 0; u < UG; ++u) {
+        const int l = fg + lane + 32 * u;
+        sf[u] = ffs_of(l < Ls ? s[l] : make_double2(0.0, 0.0));
+        A[u][0] = A[u][1] = B[u][0] = B[u][1] = ff{0.f, 0.f};
       }
-      dl_pair_points(g, q, I, J, cse, lane, 32, [&](double r, double c) {
+      int cnt = 0;
+      for (int p0 = 0; p0 < P.npts; p0 += 32) {
+        const int np = min(32, P.npts - p0);
+        __syncwarp();
+        if (lane < np) {
+          double r, c;
+          dl_point(q, P, p0 + lane, r, c);
+          const ff dd = ff_of(fmax(r - r0, 0.0)), cc = ff_of(c), cr = ff_of(c * r);
+          pd[w][lane] = make_float2(dd.h, dd.l);
+          pc[w][lane] = make_float2(cc.h, cc.l);
+          pcr[w][lane] = make_float2(cr.h, cr.l);
+        }
+        __syncwarp();
+        for (int k = 0; k < np; ++k) {
+          const float2 dk = pd[w][k], ck = pc[w][k], crk = pcr[w][k];
+          const ff cf = {ck.x, ck.y}, crf = {crk.x, crk.y};
 #pragma unroll
-        for (int f = 0; f < NF; ++f) {
-          if (f < nf) {
-            // c (1 + s r) e^{-s r}
-            const double2 v = cexp_c(r, c, sv[f], q);
-            const double2 o = make_double2(1.0 + sv[f].x * r, sv[f].y * r);
-            const double2 t = cmul(v, o);
-            acc[f].x += t.x;
-            acc[f].y += t.y;
+          for (int u = 0; u < UG; ++u) {
+            ff er, ei;  // e^{-s d}
+            cexp_ff(ff{dk.x, dk.y}, ff{1.f, 0.f}, sf[u], t2s, css, er, ei);
+            ff_acc(A[u][0], ff_mul(cf, er));
+            ff_acc(A[u][1], ff_mul(cf, ei));
+            ff_acc(B[u][0], ff_mul(crf, er));
+            ff_acc(B[u][1], ff_mul(crf, ei));
+          }
+          if ((++cnt & 15) == 0) {
+#pragma unroll
+            for (int u = 0; u < UG; ++u) {
+              ff_norm(A[u][0]);
+              ff_norm(A[u][1]);
+              ff_norm(B[u][0]);
+              ff_norm(B[u][1]);
+            }
           }
         }
-      });
+      }
 #pragma unroll
-      for (int f = 0; f < NF; ++f) acc[f] = warp_sum2(acc[f]);
-#pragma unroll
-      for (int f = 0; f < NF; ++f)
-        if (lane == f && f < nf) Tb[((size_t)(f0 + f) * nc + j) * nr + i] = acc[f];
+      for (int u = 0; u < UG; ++u) {
+        const int l = fg + lane + 32 * u;
+        if (l < Ls) {
+          const double2 sl = s[l];
+          const double2 a = make_double2(ff_to_double(A[u][0]), ff_to_double(A[u][1]));
+          const double2 bb = make_double2(ff_to_double(B[u][0]), ff_to_double(B[u][1]));
+          const double2 v = cadd(a, cmul(sl, bb));
+          Tb[((size_t)l * nc + j) * nr + i] = cmul(v, cexp_c(r0, 1.0, sl, q));
+        }
+      }
     }
   }
 }
@@ -261,7 +337,8 @@ static int dl_prepare(cqm_handle* h) {
       if (nb > 0)
         k_dl_near_table<<<nb, 256, 0, h->stream>>>(h->Ls, geom_of(h), h->quad, h->s.p, h->near_rc.p,
                                                    h->node_begin.p, h->node_end.p, h->perm.p,
-                                                   h->dl_off.p, h->dl_table.p);
+                                                   h->dl_off.p, h->exp_t2_ff.p, h->exp_cs_ff.p,
+                                                   h->dl_table.p);
       k_dl_leaf_of<<<h->n_nodes, 128, 0, h->stream>>>(h->node_son0.p, h->node_begin.p, h->node_end.p,
                                                        leaf_of.p);
       k_dl_leaf_basis<<<grid_for((int64_t)M * p, 256), 256, 0, h->stream>>>(
