@@ -288,26 +288,35 @@ def cqm_R(N):
     return 1e-10 ** (1.0 / (2 * (N + 1)))
 
 
+# FP32 instructions of one float-float multiply-add of the march's history
+# sums (a complex value times a real one, or the real part of a complex
+# product): two products (two_prod + two cross FMAs + fast_two_sum, 6 each)
+# and two TwoSum accumulations (8 each), counted from the source.
+MOT_FF_INSTR_PER_MAC = 28
+
+
 def mot_models(info, N, launches_per_step):
-    """FP64 work of the marching-on-in-time kernels.  History of step n
-    (eq. fastrhs): the convolution sum_{k<n} dhat_t[n-k] q_k of every rank
-    term (complex times real: 4 flops per entry and lag; 64 entries for a far
-    term, the column cluster for a near one, taken as the mean leaf size) and
-    the real part of C_t z_t (4 flops per entry of C_t), summed over the
-    steps and divided by the launches.  Step: the dense inverse of Vhat_0
-    applied (2 M^2 flops) and the basis coefficients of the new density."""
+    """Work of the marching-on-in-time kernels.  History of step n (eq.
+    fastrhs), in float-float on the FP32 pipes: the convolution
+    sum_{k<n} dhat_t[n-k] q_k of every rank term (64 entries for a far term,
+    the column cluster for a near one, taken as the mean leaf size) and the
+    real part of C_t z_t (one multiply-add per entry of C_t), summed over
+    the steps and divided by the launches, each multiply-add
+    MOT_FF_INSTR_PER_MAC FP32 instructions.  Step: the dense inverse of
+    Vhat_0 applied (8 B per entry, streamed)."""
     M = info["nt"]
     leaf = M / max(1, info["n_leaves"])
     lags = N * (N + 1) / 2.0
-    per_lag = 4.0 * (info["rank_sum_far"] * 64 + info["rank_sum_near"] * leaf)
-    per_step = 4.0 * (info["rank_sum_far"] * 4096 + info["near_rank_entries"])
-    fp64 = dict(bound="alu", peak=FP64_PEAK_TFLOPS, unit="TFLOP/s",
-                peak_source="recipe nominal FP64 rate of a GB300 (1.25 TFLOP/s; a probe measured 1.19)")
+    per_lag = info["rank_sum_far"] * 64 + info["rank_sum_near"] * leaf
+    per_step = info["rank_sum_far"] * 4096 + info["near_rank_entries"]
     lps = launches_per_step or {}
     models = {}
     if lps.get("mot_history"):
-        models["mot_history"] = dict(fp64, work=(per_lag * lags + per_step * N) / lps["mot_history"],
-                                     what="FP64 history sums of the march (eq. fastrhs)")
+        models["mot_history"] = dict(
+            bound="alu", peak=FP32_ISSUE_PEAK_T, unit="Tinst/s",
+            peak_source="FP32 issue: unit counts x max SM clock (152 SMs x 128 lanes x 2.07 GHz)",
+            work=MOT_FF_INSTR_PER_MAC * (per_lag * lags + per_step * N) / lps["mot_history"],
+            what="float-float history sums of the march (eq. fastrhs), FP32 instructions")
     if lps.get("mot_step"):
         models["mot_step"] = dict(bound="hbm", peak=_peaks()[0]["hbm_gbs"], unit="GB/s",
                                   work=8.0 * M * M * (N + 1) / lps["mot_step"],
@@ -506,8 +515,9 @@ def run_ours(args):
         line["dense_fp64_gpu"] = dense_baseline(m, pulse, W, q)
     if mot:
         line["scheme"] = ("marching on in time (Sec. 3.2) with the compressed weights "
-                          "(eqs. fastdft, fastrhs), FP64")
-        line["dtype"] = "f64 (marching on in time); fp64 MACA pivots, float-float MACA kernel evaluations"
+                          "(eqs. fastdft, fastrhs)")
+        line["dtype"] = ("fp64 weights, Vhat_0 inverse and step solve; float-float (~48-bit) history sums "
+                         "and MACA kernel evaluations; fp64 MACA pivots")
         op = CqmBem(m.xyz, m.tri, dt, N, W["bdf"], **dict(params, profile=0))
         qd = op.solve(rhs).cpu().numpy()
         op.close()

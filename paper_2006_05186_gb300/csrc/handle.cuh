@@ -132,6 +132,7 @@ struct cqm_handle {
   // tree order (M x M, row-major)
   bool mot_ready = false;
   cqm::DArray<double2> mot_dn, mot_df;
+  cqm::DArray<float4> mot_dn_ff, mot_df_ff;  // the same as float-float pairs (history sums)
   cqm::DArray<double> mot_Ue, mot_Ainv;
   cqm::DArray<int64_t> mot_Ue_off;
   double mot_setup_ms = 0.0;

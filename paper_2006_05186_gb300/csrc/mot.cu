@@ -20,10 +20,14 @@
 // down-sweep and the leaf bases.  Vhat_0 is real symmetric positive definite;
 // it is assembled densely once (tree order), inverted once by blocked
 // Gauss-Jordan elimination, and each step applies the inverse (one GEMV).
-// Everything here is FP64: the weights carry R^-n ~ 1e5 at the last steps.
+// The weights, the inverse and the step solve are FP64 (the weights carry
+// R^-n ~ 1e5 at the last steps); the history sums, the bulk of the work, run
+// in float-float (~48 bits) on the FP32 pipes when the factors are held as
+// float-float pairs, and in FP64 otherwise.
 #include <algorithm>
 #include <vector>
 
+#include "ffexp.cuh"
 #include "handle.cuh"
 
 namespace cqm {
@@ -411,6 +415,172 @@ __global__ void __launch_bounds__(256) k_mot_hist_far(int n, int L, int cap, int
   }
 }
 
+// ---- the same history sums in float-float on the FP32 pipes ---------------
+// (used when the C factors are held as float-float pairs).  The transformed
+// fibres, the densities and the basis coefficients come as float-float
+// copies (dhat: (re hi, im hi, re lo, im lo); reals: (hi, lo)); the sums
+// carry about 48 bits, renormalised every 16 terms.
+__device__ __forceinline__ ff ffv(float2 v) { return ff{v.x, v.y}; }
+
+__global__ void __launch_bounds__(256) k_mot_hist_near_ff(int n, int L, int cap, int M,
+                                                          const int2* __restrict__ rc,
+                                                          const int* __restrict__ begin,
+                                                          const int* __restrict__ end,
+                                                          const int64_t* __restrict__ off,
+                                                          const int* __restrict__ rank,
+                                                          const float4* __restrict__ C,
+                                                          const float4* __restrict__ Dh,
+                                                          const float2* __restrict__ qt,
+                                                          double* __restrict__ part) {
+  __shared__ float4 zs[64][32];
+  const int b = blockIdx.x;
+  const int2 c2 = rc[b];
+  const int rb = begin[c2.x], nr = end[c2.x] - rb, cb = begin[c2.y], nc = end[c2.y] - cb;
+  const int rk = rank[b];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  {
+    ff ar[8], ai[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) ar[u] = ai[u] = ff{0.f, 0.f};
+    const float4* dh = Dh + (size_t)b * cap * L + n;  // dhat_t[n - k] at dh[t L - k]
+    for (int k = 0; k < n; ++k) {
+      const ff x = lane < nc ? ffv(qt[(size_t)k * M + cb + lane]) : ff{0.f, 0.f};
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int t = w + 8 * u;
+        if (t < rk) {
+          const float4 d = dh[(ptrdiff_t)t * L - k];
+          ff_acc(ar[u], ff_mul(ff{d.x, d.z}, x));
+          ff_acc(ai[u], ff_mul(ff{d.y, d.w}, x));
+        }
+      }
+      if ((k & 15) == 15) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          ff_norm(ar[u]);
+          ff_norm(ai[u]);
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      ff_norm(ar[u]);
+      ff_norm(ai[u]);
+      if (w + 8 * u < rk) zs[w + 8 * u][lane] = make_float4(ar[u].h, ai[u].h, ar[u].l, ai[u].l);
+    }
+  }
+  __syncthreads();
+  for (int i = w; i < nr; i += 8) {
+    ff v = {0.f, 0.f};
+    if (lane < nc)
+      for (int t = 0; t < rk; ++t) {
+        const float4 c = C[(size_t)off[b] + (size_t)t * nr * nc + (size_t)i * nc + lane];
+        const float4 z = zs[t][lane];
+        ff_acc(v, ff_mul(ff{c.x, c.z}, ff{z.x, z.z}));
+        const ff q2 = ff_mul(ff{c.y, c.w}, ff{z.y, z.w});
+        ff_acc(v, ff{-q2.h, -q2.l});
+        if ((t & 15) == 15) ff_norm(v);
+      }
+    ff_norm(v);
+    const double vd = warp_sum(ff_to_double(v));
+    if (lane == 0) part[(size_t)b * 32 + i] = vd;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_mot_hist_far_ff(int n, int L, int cap, int p,
+                                                         const int2* __restrict__ rc,
+                                                         const int* __restrict__ rank,
+                                                         const float4* __restrict__ C,
+                                                         const float4* __restrict__ Dh,
+                                                         const float2* __restrict__ Xh,
+                                                         double* __restrict__ part) {
+  __shared__ float4 zs[32][TP];
+  const int b = blockIdx.x;
+  const int c = rc[b].y;
+  const int rk = rank[b], pp = p * p;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int nu = threadIdx.x & 63, g = threadIdx.x >> 6;
+  ff out[8];
+#pragma unroll
+  for (int v = 0; v < 8; ++v) out[v] = ff{0.f, 0.f};
+  const float2* xc = Xh + (size_t)c * L * p;
+  for (int t0 = 0; t0 < rk; t0 += 32) {
+    ff ar[8], ai[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) ar[u] = ai[u] = ff{0.f, 0.f};
+    const float4* dh = Dh + (size_t)b * cap * L + n;
+    for (int k = 0; k < n; ++k) {
+      const ff x = nu < p ? ffv(xc[(size_t)k * p + nu]) : ff{0.f, 0.f};
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int t = t0 + g + 4 * u;
+        if (t < rk) {
+          const float4 d = dh[(ptrdiff_t)t * L - k];
+          ff_acc(ar[u], ff_mul(ff{d.x, d.z}, x));
+          ff_acc(ai[u], ff_mul(ff{d.y, d.w}, x));
+        }
+      }
+      if ((k & 15) == 15) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          ff_norm(ar[u]);
+          ff_norm(ai[u]);
+        }
+      }
+    }
+    __syncthreads();  // the previous pass has read zs
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      ff_norm(ar[u]);
+      ff_norm(ai[u]);
+      zs[g + 4 * u][nu] = make_float4(ar[u].h, ai[u].h, ar[u].l, ai[u].l);
+    }
+    __syncthreads();
+    const int nt = min(32, rk - t0);
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+      const int mu = w + 8 * v;
+      if (mu < p) {
+        for (int t = 0; t < nt; ++t) {
+          const size_t base = ((size_t)b * cap + t0 + t) * pp + (size_t)mu * p;
+#pragma unroll
+          for (int hh = 0; hh < 2; ++hh) {
+            const int nv = lane + 32 * hh;
+            if (nv < p) {
+              const float4 cv = C[base + nv], z = zs[t][nv];
+              ff_acc(out[v], ff_mul(ff{cv.x, cv.z}, ff{z.x, z.z}));
+              const ff q2 = ff_mul(ff{cv.y, cv.w}, ff{z.y, z.w});
+              ff_acc(out[v], ff{-q2.h, -q2.l});
+            }
+          }
+          if ((t & 7) == 7) ff_norm(out[v]);
+        }
+        ff_norm(out[v]);
+      }
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < 8; ++v) {
+    const double sd = warp_sum(ff_to_double(out[v]));
+    if (lane == 0 && w + 8 * v < p) part[(size_t)b * TP + w + 8 * v] = sd;
+  }
+}
+
+// float-float copies: dhat (complex) and reals
+__global__ void k_mot_to_ffc(int64_t n, const double2* __restrict__ a, float4* __restrict__ b) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double2 v = a[i];
+  const ff re = ff_of(v.x), im = ff_of(v.y);
+  b[i] = make_float4(re.h, im.h, re.l, im.l);
+}
+__global__ void k_mot_to_ffr(int64_t n, const double* __restrict__ a, float2* __restrict__ b) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const ff v = ff_of(a[i]);
+  b[i] = make_float2(v.h, v.l);
+}
+
 // yh[r][mu] = sum of the far blocks of row cluster r in stored order (0 if none).
 __global__ void k_mot_reduce_far(int p, const int* __restrict__ rowptr, const double* __restrict__ part,
                                  double* __restrict__ yh) {
@@ -450,14 +620,21 @@ __global__ void k_mot_rhs(int n, int M, int p, int hist, const int* __restrict__
 
 // qt[n][a] = sum_b Ainv[a][b] f[b]: a warp per row.
 __global__ void __launch_bounds__(256) k_mot_gemv(int M, const double* __restrict__ Ainv,
-                                                  const double* __restrict__ f, double* __restrict__ q) {
+                                                  const double* __restrict__ f, double* __restrict__ q,
+                                                  float2* __restrict__ qff) {
   const int a = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (a >= M) return;
   const double* row = Ainv + (size_t)a * M;
   double v = 0.0;
   for (int j = lane; j < M; j += 32) v = fma(row[j], f[j], v);
   v = warp_sum(v);
-  if (lane == 0) q[a] = v;
+  if (lane == 0) {
+    q[a] = v;
+    if (qff) {
+      const ff vf = ff_of(v);
+      qff[a] = make_float2(vf.h, vf.l);
+    }
+  }
 }
 
 // xhat_r(n)[mu] = sum_i Ue_r[i][mu] q_n[begin_r + i] for every node r; one CTA
@@ -465,7 +642,8 @@ __global__ void __launch_bounds__(256) k_mot_gemv(int M, const double* __restric
 __global__ void __launch_bounds__(256) k_mot_forward(int n, int L, int p, const int* __restrict__ begin,
                                                      const int* __restrict__ end, const double* __restrict__ Ue,
                                                      const int64_t* __restrict__ uoff,
-                                                     const double* __restrict__ q, double* __restrict__ Xh) {
+                                                     const double* __restrict__ q, double* __restrict__ Xh,
+                                                     float2* __restrict__ Xff) {
   __shared__ double red[4][TP];
   const int r = blockIdx.x;
   const int rb = begin[r], nr = end[r] - rb;
@@ -476,8 +654,14 @@ __global__ void __launch_bounds__(256) k_mot_forward(int n, int L, int p, const 
     for (int i = g; i < nr; i += 4) v = fma(u[(size_t)i * p + mu], q[rb + i], v);
   red[g][mu] = v;
   __syncthreads();
-  if (g == 0 && mu < p)
-    Xh[((size_t)r * L + n) * p + mu] = (red[0][mu] + red[1][mu]) + (red[2][mu] + red[3][mu]);
+  if (g == 0 && mu < p) {
+    const double x = (red[0][mu] + red[1][mu]) + (red[2][mu] + red[3][mu]);
+    Xh[((size_t)r * L + n) * p + mu] = x;
+    if (Xff) {
+      const ff xf = ff_of(x);
+      Xff[((size_t)r * L + n) * p + mu] = make_float2(xf.h, xf.l);
+    }
+  }
 }
 
 // q[n][perm[pos]] = qt[n][pos]
@@ -505,6 +689,8 @@ void mot_release(cqm_handle* h) {
   h->mot_Ue.free(A);
   h->mot_Ainv.free(A);
   h->mot_Ue_off.free(A);
+  h->mot_dn_ff.free(A);
+  h->mot_df_ff.free(A);
   h->mot_ready = false;
 }
 
@@ -558,6 +744,14 @@ int mot_prepare(cqm_handle* h) {
       k_mot_fastdft<<<h->n_near, 256, sh, S>>>(L, Ls, cap, h->R, h->near_rank.p, h->nearD.p, tw.p, h->mot_dn.p);
     if (h->n_far > 0)
       k_mot_fastdft<<<h->n_far, 256, sh, S>>>(L, Ls, cap, h->R, h->far_rank.p, h->farD.p, tw.p, h->mot_df.p);
+    if (h->factors_ff) {  // float-float copies for the history sums
+      if ((st = h->mot_dn_ff.allocate(A, h->mot_dn.n)) != CQM_OK) break;
+      if ((st = h->mot_df_ff.allocate(A, h->mot_df.n)) != CQM_OK) break;
+      k_mot_to_ffc<<<grid_for((int64_t)h->mot_dn.n, 256), 256, 0, S>>>((int64_t)h->mot_dn.n, h->mot_dn.p,
+                                                                        h->mot_dn_ff.p);
+      k_mot_to_ffc<<<grid_for((int64_t)h->mot_df.n, 256), 256, 0, S>>>((int64_t)h->mot_df.n, h->mot_df.p,
+                                                                        h->mot_df_ff.p);
+    }
     // explicit bases, deepest level first
     std::vector<int64_t> off(h->n_nodes + 1, 0);
     for (int r = 0; r < h->n_nodes; ++r) off[r + 1] = off[r] + (int64_t)(h->h_end[r] - h->h_begin[r]) * p;
@@ -641,9 +835,12 @@ int mot_solve(cqm_handle* h, const double* d_b, double* d_q, cqm_solve_info* inf
   const int ff = h->factors_ff ? 1 : 0;
   cudaStream_t S = h->stream;
   DArray<double> qt, Xh, pn, pf, yh, f;
+  DArray<float2> qff, Xff;
   DArray<int> leaf_of;
+  const bool ffh = h->factors_ff && h->mot_dn_ff.p != nullptr;  // float-float history sums
   auto release = [&]() {
     qt.free(A); Xh.free(A); pn.free(A); pf.free(A); yh.free(A); f.free(A); leaf_of.free(A);
+    qff.free(A); Xff.free(A);
   };
   int st = CQM_OK;
 #define MOT_TRY(e) do { if ((st = (e)) != CQM_OK) { release(); return st; } } while (0)
@@ -654,6 +851,10 @@ int mot_solve(cqm_handle* h, const double* d_b, double* d_q, cqm_solve_info* inf
   MOT_TRY(yh.allocate(A, (size_t)nn * p));
   MOT_TRY(f.allocate(A, M));
   MOT_TRY(leaf_of.allocate(A, M));
+  if (ffh) {
+    MOT_TRY(qff.allocate(A, (size_t)L * M));
+    MOT_TRY(Xff.allocate(A, (size_t)nn * L * p));
+  }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
     if (e0) cudaEventDestroy(e0);
@@ -668,13 +869,23 @@ int mot_solve(cqm_handle* h, const double* d_b, double* d_q, cqm_solve_info* inf
     const int hist = n > 0 ? 1 : 0;
     {
       ProfScope ps_(h, CQM_K_MOT_HISTORY);
-      if (hist && h->n_near > 0)
-        k_mot_hist_near<<<h->n_near, 256, 0, S>>>(n, L, cap, M, h->near_rc.p, h->node_begin.p,
-                                                  h->node_end.p, h->near_off.p, h->near_rank.p,
-                                                  h->nearC.p, ff, h->mot_dn.p, qt.p, pn.p);
+      if (hist && h->n_near > 0) {
+        if (ffh)
+          k_mot_hist_near_ff<<<h->n_near, 256, 0, S>>>(n, L, cap, M, h->near_rc.p, h->node_begin.p,
+                                                       h->node_end.p, h->near_off.p, h->near_rank.p,
+                                                       (const float4*)h->nearC.p, h->mot_dn_ff.p, qff.p, pn.p);
+        else
+          k_mot_hist_near<<<h->n_near, 256, 0, S>>>(n, L, cap, M, h->near_rc.p, h->node_begin.p,
+                                                    h->node_end.p, h->near_off.p, h->near_rank.p,
+                                                    h->nearC.p, ff, h->mot_dn.p, qt.p, pn.p);
+      }
       if (hist && h->n_far > 0) {
-        k_mot_hist_far<<<h->n_far, 256, 0, S>>>(n, L, cap, p, h->far_rc.p, h->far_rank.p, h->farC.p, ff,
-                                                h->mot_df.p, Xh.p, pf.p);
+        if (ffh)
+          k_mot_hist_far_ff<<<h->n_far, 256, 0, S>>>(n, L, cap, p, h->far_rc.p, h->far_rank.p,
+                                                     (const float4*)h->farC.p, h->mot_df_ff.p, Xff.p, pf.p);
+        else
+          k_mot_hist_far<<<h->n_far, 256, 0, S>>>(n, L, cap, p, h->far_rc.p, h->far_rank.p, h->farC.p, ff,
+                                                  h->mot_df.p, Xh.p, pf.p);
         k_mot_reduce_far<<<nn, TP, 0, S>>>(p, h->far_rowptr.p, pf.p, yh.p);
       }
       k_mot_rhs<<<grid_for(M, 256), 256, 0, S>>>(n, M, p, hist, h->perm.p, leaf_of.p, h->node_parent.p,
@@ -683,10 +894,12 @@ int mot_solve(cqm_handle* h, const double* d_b, double* d_q, cqm_solve_info* inf
     }
     {
       ProfScope ps_(h, CQM_K_MOT_STEP);
-      k_mot_gemv<<<grid_for(M, 8), 256, 0, S>>>(M, h->mot_Ainv.p, f.p, qt.p + (size_t)n * M);
+      k_mot_gemv<<<grid_for(M, 8), 256, 0, S>>>(M, h->mot_Ainv.p, f.p, qt.p + (size_t)n * M,
+                                                 ffh ? qff.p + (size_t)n * M : nullptr);
       if (n + 1 < L)
         k_mot_forward<<<nn, 256, 0, S>>>(n, L, p, h->node_begin.p, h->node_end.p, h->mot_Ue.p,
-                                         h->mot_Ue_off.p, qt.p + (size_t)n * M, Xh.p);
+                                         h->mot_Ue_off.p, qt.p + (size_t)n * M, Xh.p,
+                                         ffh ? Xff.p : nullptr);
     }
     if (cudaGetLastError() != cudaSuccess) {
       set_last_error("marching on in time: step launch failed");

@@ -88,9 +88,10 @@ def test_mot_models(bench):
     N = 64
     m = bench.mot_models(info, N, {"mot_history": 64.0, "mot_step": 65.0})
     lags = N * (N + 1) / 2
-    per_lag = 4.0 * (100 * 64 + 50 * 20.0)
-    per_step = 4.0 * (100 * 4096 + 40000)
-    assert m["mot_history"]["work"] == pytest.approx((per_lag * lags + per_step * N) / 64.0)
-    assert m["mot_history"]["bound"] == "alu" and m["mot_history"]["unit"] == "TFLOP/s"
+    per_lag = 100 * 64 + 50 * 20.0
+    per_step = 100 * 4096 + 40000
+    k = bench.MOT_FF_INSTR_PER_MAC
+    assert m["mot_history"]["work"] == pytest.approx(k * (per_lag * lags + per_step * N) / 64.0)
+    assert m["mot_history"]["bound"] == "alu" and m["mot_history"]["unit"] == "Tinst/s"
     assert m["mot_step"]["work"] == pytest.approx(8.0 * 1280 * 1280 * 65 / 65.0)
     assert abs(bench.cqm_R(N) ** (N + 1) - 1e-5) < 1e-12
