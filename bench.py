@@ -91,12 +91,15 @@ MACA_FF_INSTR_PER_EVAL = 160
 
 
 # DRAM bytes (read + write) of one launch of the bf16 tensor-core coupling per
-# far rank term, from an ncu capture of that kernel; None until one is taken
-# of the current kernel.  The traffic is the 32 KB bf16 image of each rank
-# term read once plus the small d_t, xhat and partial-tile terms, so it grows
-# with the rank terms and the bench scales it to the workload's count.
-TC2_DRAM_BYTES_PER_RANK_TERM = None
-TC2_DRAM_SOURCE = "ncu dram__bytes_read.sum + dram__bytes_write.sum of k_far_coupling_tc2, scaled by far rank terms"
+# far rank term, from an ncu capture of that kernel: 461.1 MB + 23.2 MB over
+# the 13,284 far rank terms of the 1280-triangle sphere at N = 256 (one
+# full capture of the kernel on that case).  The traffic is the 32 KB
+# bf16 image of each rank term read once plus the small d_t, xhat and
+# partial-tile terms, so it grows with the rank terms and the bench scales it
+# to the workload's count.
+TC2_DRAM_BYTES_PER_RANK_TERM = (461.124352e6 + 23.230976e6) / 13284
+TC2_DRAM_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of k_far_coupling_tc2 (1280-triangle "
+                   "sphere, N = 256), per far rank term, scaled to this workload's terms")
 
 
 def tf32_peak():
@@ -498,7 +501,7 @@ def run_ours(args):
                                            "rank_max", "t_tree_ms", "t_bases_ms", "t_assembly_ms",
                                            "near_expanded", "far_expanded")},
                       total_ms=inf["t_geometry_ms"] + inf["t_tree_ms"] + inf["t_bases_ms"] + inf["t_assembly_ms"]),
-        "solve": dict({k: sinfos[-1][k] for k in ("iterations", "restarts", "t_gmres_ms")},
+        "solve": dict({k: sinfos[-1][k] for k in ("iterations", "restarts", "t_gmres_ms", "arnoldi_freq_steps")},
                       total_ms=sinfos[-1]["t_forward_ms"] + sinfos[-1]["t_gmres_ms"] + sinfos[-1]["t_inverse_ms"]),
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(L * M * 8 + m.xyz.nbytes + m.tri.nbytes),
