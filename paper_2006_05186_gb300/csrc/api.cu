@@ -129,7 +129,7 @@ int cqm_bem_destroy(cqm_handle* h) {
   h->pt_off.free(A); h->pt_cnt.free(A); h->pt_r.free(A); h->pt_c.free(A);
   h->nearC_f.free(A); h->nearD_f.free(A); h->farC_f.free(A); h->farD_f.free(A);
   h->nearV.free(A); h->nearV_f.free(A); h->nearV_off.free(A); h->farS.free(A);
-  h->xhat_f.free(A); h->yhat_f.free(A); h->Uleaf_f.free(A); h->Etr_f.free(A);
+  h->xhat_f.free(A); h->yhat_f.free(A); h->Uleaf_f.free(A); h->Etr_f.free(A); h->x32.free(A);
   mot_release(h);
   dl_release(h);
   cudaStreamSynchronize(h->stream);

@@ -113,6 +113,7 @@ struct cqm_handle {
   bool far_expanded = false;
   cqm::DArray<double2> farS;
   cqm::DArray<float2> nearC_f, nearD_f, farC_f, farD_f, xhat_f, yhat_f;
+  cqm::DArray<float2> x32;  // FP32 copy of the inner apply's input (expanded near field)
   // bf16 images of the far factors for the tensor-core coupling (32 KB per rank
   // term, term t of block b at tc2_first[b] + t) and the FP32 expanded
   // couplings of its tail frequencies

@@ -64,10 +64,9 @@ __global__ void __launch_bounds__(256) k_near_expand(int Ls, int cap, const int2
 
 // y_l[perm[rb + i]] = sum over the near blocks (r, c) of leaf row r of
 // sum_j V_l[i][j] x_l[perm[cb + j]]: one warp per (leaf row, frequency), lanes
-// over the rows i, blocks in their stored order.  Each block's sum (at most
-// 32 terms) is formed in the storage precision and added to an FP64 total, so
-// the FP32 form does not lose accuracy over the whole row.  Overwrites y on
-// the rows.
+// over the rows i, blocks in their stored order, each block's sum added to an
+// FP64 total (the FP64 table; the double layer's table).  Overwrites y on the
+// rows.
 template <class VT>
 __global__ void __launch_bounds__(256) k_near_dense(int M, int Ls, const int* __restrict__ leaves,
                                                     const int* __restrict__ rowptr,
@@ -114,6 +113,67 @@ __global__ void __launch_bounds__(256) k_near_dense(int M, int Ls, const int* __
   if (lane < nr) y[(size_t)l * M + perm[rb + lane]] = acc;
 }
 
+// The same for the FP32 table with an FP32 copy of x (converted once per
+// apply, not once per block that reads it): each block's sum in FP32, the
+// row's total over the blocks in compensated FP32 (TwoSum, ~48 bits, the
+// accuracy of the FP64 total of the kernel above without its FP64
+// instructions).  Overwrites y on the rows.
+__global__ void __launch_bounds__(256) k_near_dense_f32x(int M, int Ls, const int* __restrict__ leaves,
+                                                         const int* __restrict__ rowptr,
+                                                         const int2* __restrict__ rc,
+                                                         const int* __restrict__ begin,
+                                                         const int* __restrict__ end,
+                                                         const int* __restrict__ perm,
+                                                         const int64_t* __restrict__ voff,
+                                                         const float2* __restrict__ V,
+                                                         const float2* __restrict__ x,
+                                                         double2* __restrict__ y) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int l = blockIdx.x * 8 + w;
+  if (l >= Ls) return;
+  const int r = leaves[blockIdx.y];
+  const int rb = begin[r], nr = end[r] - rb;
+  const float2* xl = x + (size_t)l * M;
+  float hr = 0.f, lr = 0.f, hi = 0.f, li = 0.f;  // compensated totals (re, im)
+  for (int bi = rowptr[r]; bi < rowptr[r + 1]; ++bi) {
+    const int c = rc[bi].y;
+    const int cb = begin[c], nc = end[c] - cb;
+    const float2 xj = lane < nc ? xl[perm[cb + lane]] : make_float2(0.f, 0.f);
+    const float2* Vb = V + voff[bi] + (size_t)l * nc * nr;
+    float2 bacc = make_float2(0.f, 0.f);
+    for (int j0 = 0; j0 < nc; j0 += 8) {
+      float2 v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        v[u] = (lane < nr && j0 + u < nc) ? Vb[(size_t)(j0 + u) * nr + lane] : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        float2 xv;
+        xv.x = __shfl_sync(0xffffffffu, xj.x, (j0 + u) & 31);
+        xv.y = __shfl_sync(0xffffffffu, xj.y, (j0 + u) & 31);
+        bacc.x = fmaf(v[u].x, xv.x, fmaf(-v[u].y, xv.y, bacc.x));
+        bacc.y = fmaf(v[u].x, xv.y, fmaf(v[u].y, xv.x, bacc.y));
+      }
+    }
+    float s, e;
+    s = __fadd_rn(hr, bacc.x);  // TwoSum
+    e = __fadd_rn(__fsub_rn(hr, __fsub_rn(s, __fsub_rn(s, hr))), __fsub_rn(bacc.x, __fsub_rn(s, hr)));
+    hr = s;
+    lr = __fadd_rn(lr, e);
+    s = __fadd_rn(hi, bacc.y);
+    e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, __fsub_rn(s, hi))), __fsub_rn(bacc.y, __fsub_rn(s, hi)));
+    hi = s;
+    li = __fadd_rn(li, e);
+  }
+  if (lane < nr)
+    y[(size_t)l * M + perm[rb + lane]] = make_double2((double)hr + (double)lr, (double)hi + (double)li);
+}
+
+__global__ void k_x_to_f32(int64_t n, const double2* __restrict__ a, float2* __restrict__ b) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = make_float2((float)a[i].x, (float)a[i].y);
+}
+
 int build_near_expanded(cqm_handle* h) {
   const int nb = h->n_near;
   h->h_nearV_off.assign(nb + 1, 0);
@@ -157,14 +217,19 @@ int near_apply_expanded(cqm_handle* h, const double2* x, double2* y, bool fp64) 
   const int nleaf = (int)h->h_leaves.size();
   if (nleaf == 0) return CQM_OK;
   dim3 g((unsigned)((h->Ls + 7) / 8), (unsigned)nleaf);
-  if (fp64)
-    k_near_dense<double2><<<g, 256, 0, h->stream>>>(h->M, h->Ls, h->d_leaves.p, h->near_rowptr.p,
-                                                    h->near_rc.p, h->node_begin.p, h->node_end.p,
-                                                    h->perm.p, h->nearV_off.p, h->nearV.p, x, y);
-  else
-    k_near_dense<float2><<<g, 256, 0, h->stream>>>(h->M, h->Ls, h->d_leaves.p, h->near_rowptr.p,
-                                                   h->near_rc.p, h->node_begin.p, h->node_end.p,
-                                                   h->perm.p, h->nearV_off.p, h->nearV_f.p, x, y);
+  if (!fp64) {
+    const int64_t n = (int64_t)h->Ls * h->M;
+    if (h->x32.n < (size_t)n) CQM_TRY(h->x32.allocate(h->alloc, (size_t)n));
+    k_x_to_f32<<<grid_for(n, 256), 256, 0, h->stream>>>(n, x, h->x32.p);
+    k_near_dense_f32x<<<g, 256, 0, h->stream>>>(h->M, h->Ls, h->d_leaves.p, h->near_rowptr.p, h->near_rc.p,
+                                                h->node_begin.p, h->node_end.p, h->perm.p, h->nearV_off.p,
+                                                h->nearV_f.p, h->x32.p, y);
+    CQM_CHECK_LAUNCH();
+    return CQM_OK;
+  }
+  k_near_dense<double2><<<g, 256, 0, h->stream>>>(h->M, h->Ls, h->d_leaves.p, h->near_rowptr.p,
+                                                  h->near_rc.p, h->node_begin.p, h->node_end.p,
+                                                  h->perm.p, h->nearV_off.p, h->nearV.p, x, y);
   CQM_CHECK_LAUNCH();
   return CQM_OK;
 }
