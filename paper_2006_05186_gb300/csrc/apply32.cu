@@ -88,12 +88,13 @@ __global__ void __launch_bounds__(256) k_far_coupling_f32(int Ls, int cap,
 // yhat_r[mu][l] += sum of the partial tiles of row r's items, in item order.
 __global__ void k_far_reduce_f32(int Ls, int lmax, const int* __restrict__ rows,
                                  const int* __restrict__ item_ptr, const float2* __restrict__ part,
-                                 float2* __restrict__ yhat) {
+                                 float2* __restrict__ yhat, const int* __restrict__ act) {
   constexpr int P = 64;
   const int k = blockIdx.x;  // index into the list of far rows
   const int r = rows[k];
   for (int e = threadIdx.x; e < P * Ls; e += blockDim.x) {
     if (e % Ls >= lmax) continue;  // frequencies the partial tiles do not hold
+    if (act && !act[e % Ls]) continue;  // converged frequencies (act may be null)
     float2 a = make_float2(0.f, 0.f);
     for (int it = item_ptr[k]; it < item_ptr[k + 1]; ++it) a = cadd(a, part[(size_t)it * P * Ls + e]);
     float2* o = yhat + (size_t)r * P * Ls + e;
@@ -208,14 +209,16 @@ int far_coupling_f32(cqm_handle* h) {
     int l_tail = h->Ls;
     CQM_TRY(far_coupling_tc2(h, &l_tail));
     k_far_reduce_f32<<<(unsigned)h->h_far_rows.size(), 256, 0, h->stream>>>(
-        h->Ls, l_tail, h->d_far_rows.p, h->far_item_ptr.p, h->part_f.p, h->yhat_f.p);
+        h->Ls, l_tail, h->d_far_rows.p, h->far_item_ptr.p, h->part_f.p, h->yhat_f.p,
+        h->inner_active);
     CQM_CHECK_LAUNCH();
     return CQM_OK;
   }
   if (h->params.tensor_cores == 2 && h->p == 64) {
     CQM_TRY(far_coupling_tc(h));
     k_far_reduce_f32<<<(unsigned)h->h_far_rows.size(), 256, 0, h->stream>>>(
-        h->Ls, h->Ls, h->d_far_rows.p, h->far_item_ptr.p, h->part_f.p, h->yhat_f.p);
+        h->Ls, h->Ls, h->d_far_rows.p, h->far_item_ptr.p, h->part_f.p, h->yhat_f.p,
+        h->inner_active);
     CQM_CHECK_LAUNCH();
     return CQM_OK;
   }
@@ -233,7 +236,8 @@ int far_coupling_f32(cqm_handle* h) {
   }
 #undef LAUNCH_NLT
   k_far_reduce_f32<<<(unsigned)h->h_far_rows.size(), 256, 0, h->stream>>>(
-      h->Ls, h->Ls, h->d_far_rows.p, h->far_item_ptr.p, h->part_f.p, h->yhat_f.p);
+      h->Ls, h->Ls, h->d_far_rows.p, h->far_item_ptr.p, h->part_f.p, h->yhat_f.p,
+        h->inner_active);
   CQM_CHECK_LAUNCH();
   return CQM_OK;
 }

@@ -392,12 +392,18 @@ int gmres_solve(cqm_handle* h, const double2* d_b, double2* d_x, cqm_solve_info*
       break;
     }
     for (int j = 0; j < m && iters < maxit; ++j) {
+      // the converged frequencies' new basis vectors are never read: the
+      // inner apply and the preconditioner skip them
+      h->inner_active = W.active.p;
+      int ast;
       if (pre) {
-        GM_TRY(apply_precond(h, W.Vb.p + (size_t)j * Ls * M, W.Z.p));
-        GM_TRY(apply_operator_inner(h, W.Z.p, W.Vb.p + (size_t)(j + 1) * Ls * M));
+        ast = apply_precond(h, W.Vb.p + (size_t)j * Ls * M, W.Z.p, W.active.p);
+        if (ast == CQM_OK) ast = apply_operator_inner(h, W.Z.p, W.Vb.p + (size_t)(j + 1) * Ls * M);
       } else {
-        GM_TRY(apply_operator_inner(h, W.Vb.p + (size_t)j * Ls * M, W.Vb.p + (size_t)(j + 1) * Ls * M));
+        ast = apply_operator_inner(h, W.Vb.p + (size_t)j * Ls * M, W.Vb.p + (size_t)(j + 1) * Ls * M);
       }
+      h->inner_active = nullptr;
+      GM_TRY(ast);
       {
         ProfScope ps_(h, CQM_K_ARNOLDI);
         const dim3 grid((unsigned)nch, (unsigned)Ls);

@@ -144,6 +144,14 @@ int build_bases(cqm_handle* h) {
 // inner GMRES iterations).  Input and output vectors are always FP64.
 constexpr int LC = 32;  // frequencies per chunk (one warp width)
 
+// Whether any frequency of the chunk [l0, l0 + LC) is still iterating (act
+// may be null: all are); a barrier, called by every thread of the block.
+__device__ __forceinline__ bool chunk_active(const int* __restrict__ act, int l0, int Ls) {
+  if (!act) return true;
+  return __syncthreads_or(threadIdx.x < LC && l0 + (int)threadIdx.x < Ls && act[l0 + threadIdx.x]) != 0;
+}
+
+
 // Near field: one block per leaf row cluster r; y_r = sum over near blocks.
 template <class R>
 __global__ void __launch_bounds__(256) k_near_apply(
@@ -209,7 +217,8 @@ __global__ void __launch_bounds__(256) k_leaf_forward(int M, int Ls, int p,
                                                       const int* __restrict__ perm,
                                                       const R* __restrict__ U,
                                                       const double2* __restrict__ X,
-                                                      typename Cplx<R>::type* __restrict__ xhat) {
+                                                      typename Cplx<R>::type* __restrict__ xhat,
+                                                      const int* __restrict__ act) {
   using C = typename Cplx<R>::type;
   __shared__ C Xs[32][LC];
   __shared__ R Us[32 * MAXP];
@@ -218,6 +227,7 @@ __global__ void __launch_bounds__(256) k_leaf_forward(int M, int Ls, int p,
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int t = threadIdx.x; t < nc * p; t += blockDim.x) Us[t] = U[(size_t)cb * p + t];
   for (int l0 = 0; l0 < Ls; l0 += LC) {
+    if (!chunk_active(act, l0, Ls)) continue;
     __syncthreads();
     for (int t = threadIdx.x; t < nc * LC; t += blockDim.x) {
       const int j = t / LC, l = t - j * LC;
@@ -258,13 +268,15 @@ __global__ void __launch_bounds__(256) k_upsweep(int node0, int Ls, int m, int p
                                                  const int* __restrict__ son0,
                                                  const int* __restrict__ son1,
                                                  const R* __restrict__ Etr,
-                                                 typename Cplx<R>::type* __restrict__ xhat) {
+                                                 typename Cplx<R>::type* __restrict__ xhat,
+                                                 const int* __restrict__ act) {
   using C = typename Cplx<R>::type;
   extern __shared__ __align__(16) unsigned char smraw[];
   R* E = (R*)smraw;                        // 2 x p x p
   C* Xs = (C*)(E + 2 * MAXP * MAXP);       // p x LC
   const int r = node0 + blockIdx.x;
   if (son0[r] < 0) return;
+  if (!chunk_active(act, blockIdx.y * LC, Ls)) return;
   const int sons[2] = {son0[r], son1[r]};
   expand_transfer<R>(Etr, sons[0], m, p, E);
   expand_transfer<R>(Etr, sons[1], m, p, E + MAXP * MAXP);
@@ -374,7 +386,8 @@ template <class R>
 __global__ void __launch_bounds__(256) k_downsweep(int node0, int Ls, int m, int p,
                                                    const int* __restrict__ parent,
                                                    const R* __restrict__ Etr,
-                                                   typename Cplx<R>::type* __restrict__ yhat) {
+                                                   typename Cplx<R>::type* __restrict__ yhat,
+                                                   const int* __restrict__ act) {
   using C = typename Cplx<R>::type;
   extern __shared__ __align__(16) unsigned char smraw[];
   R* E = (R*)smraw;                  // p x p
@@ -382,6 +395,7 @@ __global__ void __launch_bounds__(256) k_downsweep(int node0, int Ls, int m, int
   const int s = node0 + blockIdx.x;
   const int r = parent[s];
   if (r < 0) return;
+  if (!chunk_active(act, blockIdx.y * LC, Ls)) return;
   expand_transfer<R>(Etr, s, m, p, E);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const C* yr = yhat + (size_t)r * p * Ls;
@@ -418,7 +432,8 @@ __global__ void __launch_bounds__(256) k_leaf_backward(int M, int Ls, int p,
                                                        const int* __restrict__ perm,
                                                        const R* __restrict__ U,
                                                        const typename Cplx<R>::type* __restrict__ yhat,
-                                                       double2* __restrict__ Y) {
+                                                       double2* __restrict__ Y,
+                                                       const int* __restrict__ act) {
   using C = typename Cplx<R>::type;
   extern __shared__ __align__(16) unsigned char smraw[];
   R* Us = (R*)smraw;                 // 32 x p
@@ -429,6 +444,7 @@ __global__ void __launch_bounds__(256) k_leaf_backward(int M, int Ls, int p,
   for (int t = threadIdx.x; t < nr * p; t += blockDim.x) Us[t] = U[(size_t)rb * p + t];
   const C* yr = yhat + (size_t)r * p * Ls;
   for (int l0 = 0; l0 < Ls; l0 += LC) {
+    if (!chunk_active(act, l0, Ls)) continue;
     __syncthreads();
     for (int t = threadIdx.x; t < p * LC; t += blockDim.x) {
       const int mu = t / LC, l = t - mu * LC;
@@ -518,6 +534,8 @@ static int apply_t(cqm_handle* h, const OpView<R>& V, const double2* x, double2*
   const int nleaf = (int)h->h_leaves.size(), nfr = (int)h->h_far_rows.size();
   const int M = h->M, Ls = h->Ls, p = h->p, m = h->m;
   cudaStream_t S = h->stream;
+  // the inner (FP32) apply inside GMRES skips converged frequencies
+  const int* act = std::is_same<R, float>::value ? h->inner_active : nullptr;
   if (far_only) {
     // the caller has written y
   } else if (ff) {
@@ -535,13 +553,13 @@ static int apply_t(cqm_handle* h, const OpView<R>& V, const double2* x, double2*
       ProfScope ps_(h, CQM_K_LEAF_FORWARD);
       k_leaf_forward<R><<<(unsigned)nleaf, 256, 0, S>>>(M, Ls, p, h->d_leaves.p, h->node_begin.p,
                                                         h->node_end.p, h->perm.p, V.Ucol ? V.Ucol : V.U,
-                                                        x, V.xhat);
+                                                        x, V.xhat, act);
     }
     for (int lv = h->depth - 1; lv >= 0; --lv) {
       const int n0 = h->level_begin[lv], n1 = h->level_begin[lv + 1];
       if (n1 > n0) {
         ProfScope ps_(h, CQM_K_UPSWEEP);
-        k_upsweep<R><<<dim3((unsigned)(n1 - n0), (unsigned)((Ls + LC - 1) / LC)), 256, upsweep_smem<R>(), S>>>(n0, Ls, m, p, h->node_son0.p, h->node_son1.p, V.Etr, V.xhat);
+        k_upsweep<R><<<dim3((unsigned)(n1 - n0), (unsigned)((Ls + LC - 1) / LC)), 256, upsweep_smem<R>(), S>>>(n0, Ls, m, p, h->node_son0.p, h->node_son1.p, V.Etr, V.xhat, act);
       }
     }
     cudaMemsetAsync(V.yhat, 0, sizeof(C) * (size_t)h->n_nodes * p * Ls, S);
@@ -559,13 +577,13 @@ static int apply_t(cqm_handle* h, const OpView<R>& V, const double2* x, double2*
       const int n0 = h->level_begin[lv], n1 = h->level_begin[lv + 1];
       if (n1 > n0) {
         ProfScope ps_(h, CQM_K_DOWNSWEEP);
-        k_downsweep<R><<<dim3((unsigned)(n1 - n0), (unsigned)((Ls + LC - 1) / LC)), 256, downsweep_smem<R>(), S>>>(n0, Ls, m, p, h->node_parent.p, V.Etr, V.yhat);
+        k_downsweep<R><<<dim3((unsigned)(n1 - n0), (unsigned)((Ls + LC - 1) / LC)), 256, downsweep_smem<R>(), S>>>(n0, Ls, m, p, h->node_parent.p, V.Etr, V.yhat, act);
       }
     }
     {
       ProfScope ps_(h, CQM_K_LEAF_BACKWARD);
       k_leaf_backward<R><<<(unsigned)nleaf, 256, leaf_backward_smem<R>(), S>>>(M, Ls, p, h->d_leaves.p, h->node_begin.p,
-                                                         h->node_end.p, h->perm.p, V.U, V.yhat, y);
+                                                         h->node_end.p, h->perm.p, V.U, V.yhat, y, act);
     }
   }
   cudaError_t e = cudaGetLastError();

@@ -114,6 +114,10 @@ struct cqm_handle {
   cqm::DArray<double2> farS;
   cqm::DArray<float2> nearC_f, nearD_f, farC_f, farD_f, xhat_f, yhat_f;
   cqm::DArray<float2> x32;  // FP32 copy of the inner apply's input (expanded near field)
+  // frequencies still iterating while GMRES applies the inner operator (null
+  // otherwise): the kernels of the inner apply that work per frequency or per
+  // chunk of 32 skip the others, whose results GMRES does not read
+  const int* inner_active = nullptr;
   // bf16 images of the far factors for the tensor-core coupling (32 KB per rank
   // term, term t of block b at tc2_first[b] + t) and the FP32 expanded
   // couplings of its tail frequencies
@@ -224,7 +228,8 @@ int build_work_items(cqm_handle* h);
 
 // precond.cu
 int build_precond(cqm_handle* h);
-int apply_precond(cqm_handle* h, const double2* v, double2* z);
+// act (may be null): frequencies to compute (the others are left untouched)
+int apply_precond(cqm_handle* h, const double2* v, double2* z, const int* act = nullptr);
 
 // gmres.cu
 int gmres_solve(cqm_handle* h, const double2* d_b, double2* d_x, cqm_solve_info* info);

@@ -127,10 +127,11 @@ __global__ void __launch_bounds__(256) k_near_dense_f32x(int M, int Ls, const in
                                                          const int64_t* __restrict__ voff,
                                                          const float2* __restrict__ V,
                                                          const float2* __restrict__ x,
-                                                         double2* __restrict__ y) {
+                                                         double2* __restrict__ y,
+                                                         const int* __restrict__ act) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int l = blockIdx.x * 8 + w;
-  if (l >= Ls) return;
+  if (l >= Ls || (act && !act[l])) return;  // act: frequencies still iterating (may be null)
   const int r = leaves[blockIdx.y];
   const int rb = begin[r], nr = end[r] - rb;
   const float2* xl = x + (size_t)l * M;
@@ -223,7 +224,7 @@ int near_apply_expanded(cqm_handle* h, const double2* x, double2* y, bool fp64) 
     k_x_to_f32<<<grid_for(n, 256), 256, 0, h->stream>>>(n, x, h->x32.p);
     k_near_dense_f32x<<<g, 256, 0, h->stream>>>(h->M, h->Ls, h->d_leaves.p, h->near_rowptr.p, h->near_rc.p,
                                                 h->node_begin.p, h->node_end.p, h->perm.p, h->nearV_off.p,
-                                                h->nearV_f.p, h->x32.p, y);
+                                                h->nearV_f.p, h->x32.p, y, h->inner_active);
     CQM_CHECK_LAUNCH();
     return CQM_OK;
   }

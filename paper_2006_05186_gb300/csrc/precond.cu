@@ -99,16 +99,20 @@ __global__ void __launch_bounds__(256) k_precond_apply(int M, int Ls, const int*
                                                        const int* __restrict__ perm,
                                                        const double2* __restrict__ P,
                                                        const double2* __restrict__ v,
-                                                       double2* __restrict__ z) {
+                                                       double2* __restrict__ z,
+                                                       const int* __restrict__ act) {
   __shared__ double2 vs[PB][32];
   const int k = blockIdx.x;
   const int r = leaves[k];
   const int rb = begin[r], n = end[r] - rb;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int l = blockIdx.y * 32 + lane;
-  for (int j = w; j < n; j += 8) vs[j][lane] = l < Ls ? v[(size_t)l * M + perm[rb + j]] : make_double2(0.0, 0.0);
+  // act (may be null): frequencies still iterating; the others are skipped
+  const bool on = l < Ls && (!act || act[l]);
+  if (!__syncthreads_or(on)) return;
+  for (int j = w; j < n; j += 8) vs[j][lane] = on ? v[(size_t)l * M + perm[rb + j]] : make_double2(0.0, 0.0);
   __syncthreads();
-  if (l >= Ls) return;
+  if (!on) return;
   for (int i = w; i < n; i += 8) {
     double2 acc = make_double2(0.0, 0.0);
     const double2* Pi = P + ((size_t)k * PB + i) * PB * Ls + l;
@@ -157,12 +161,12 @@ int build_precond(cqm_handle* h) {
   return CQM_OK;
 }
 
-int apply_precond(cqm_handle* h, const double2* v, double2* z) {
+int apply_precond(cqm_handle* h, const double2* v, double2* z, const int* act) {
   const int nl = (int)h->h_leaves.size();
   {
     ProfScope ps_(h, CQM_K_PRECOND);
     k_precond_apply<<<dim3(nl, (h->Ls + 31) / 32), 256, 0, h->stream>>>(
-        h->M, h->Ls, h->d_leaves.p, h->node_begin.p, h->node_end.p, h->perm.p, h->Pinv.p, v, z);
+        h->M, h->Ls, h->d_leaves.p, h->node_begin.p, h->node_end.p, h->perm.p, h->Pinv.p, v, z, act);
   }
   CQM_CHECK_LAUNCH();
   return CQM_OK;

@@ -139,9 +139,11 @@ __global__ void __launch_bounds__(256) k_far_tail_f32(int Ls, int l0, int ntail,
                                                       const int2* __restrict__ rc,
                                                       const float2* __restrict__ S,
                                                       const float2* __restrict__ xhat,
-                                                      float2* __restrict__ yhat) {
+                                                      float2* __restrict__ yhat,
+                                                      const int* __restrict__ act) {
   __shared__ float2 red[8][TP];
   const int k = blockIdx.x / ntail, f = blockIdx.x - k * ntail, l = l0 + f;
+  if (act && !act[l]) return;  // a converged frequency (act may be null)
   const int r = rows[k];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
@@ -544,7 +546,7 @@ int far_coupling_tc2(cqm_handle* h, int* l_tail_out) {
     const int nfr = (int)h->h_far_rows.size();
     k_far_tail_f32<<<(unsigned)(nfr * ntail), 256, 0, h->stream>>>(
         h->Ls, l_tail, ntail, h->d_far_rows.p, h->far_rowptr.p, h->far_rc.p, h->tc2_tail.p,
-        h->xhat_f.p, h->yhat_f.p);
+        h->xhat_f.p, h->yhat_f.p, h->inner_active);
     CQM_CHECK_LAUNCH();
   }
   *l_tail_out = l_tail;
