@@ -391,10 +391,11 @@ __global__ void __launch_bounds__(256) k_far_dense_ff(int Ls, int p, int nrows, 
                                                       const int2* __restrict__ rc,
                                                       const ffc* __restrict__ S,
                                                       const double2* __restrict__ xhat,
-                                                      double2* __restrict__ yhat) {
+                                                      double2* __restrict__ yhat,
+                                                      const int* __restrict__ act) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int l = blockIdx.x * 8 + w;
-  if (l >= Ls) return;
+  if (l >= Ls || (act && !act[l])) return;  // act: frequencies to compute (may be null)
   const int r = rows[blockIdx.y];
   const int pp = p * p;
   ffc acc0 = ffc_zero(), acc1 = ffc_zero();
@@ -467,7 +468,8 @@ int far_apply_expanded_ff(cqm_handle* h) {
   if (nfr == 0) return CQM_OK;
   dim3 g((unsigned)((h->Ls + 7) / 8), (unsigned)nfr);
   k_far_dense_ff<<<g, 256, 0, h->stream>>>(h->Ls, h->p, nfr, h->d_far_rows.p, h->far_rowptr.p,
-                                            h->far_rc.p, (const ffc*)h->farS.p, h->xhat.p, h->yhat.p);
+                                            h->far_rc.p, (const ffc*)h->farS.p, h->xhat.p, h->yhat.p,
+                                            h->exact_active);
   CQM_CHECK_LAUNCH();
   return CQM_OK;
 }
@@ -534,10 +536,11 @@ __global__ void __launch_bounds__(256) k_near_dense_ff(int M, int Ls, const int*
                                                        const int64_t* __restrict__ voff,
                                                        const ffc* __restrict__ V,
                                                        const double2* __restrict__ x,
-                                                       double2* __restrict__ y) {
+                                                       double2* __restrict__ y,
+                                                       const int* __restrict__ act) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int l = blockIdx.x * 8 + w;
-  if (l >= Ls) return;
+  if (l >= Ls || (act && !act[l])) return;  // act: frequencies to compute (may be null)
   const int r = leaves[blockIdx.y];
   const int rb = begin[r], nr = end[r] - rb;
   const double2* xl = x + (size_t)l * M;
@@ -606,7 +609,7 @@ int near_apply_expanded_ff(cqm_handle* h, const double2* x, double2* y) {
   dim3 g((unsigned)((h->Ls + 7) / 8), (unsigned)nleaf);
   k_near_dense_ff<<<g, 256, 0, h->stream>>>(h->M, h->Ls, h->d_leaves.p, h->near_rowptr.p, h->near_rc.p,
                                             h->node_begin.p, h->node_end.p, h->perm.p, h->nearV_off.p,
-                                            (const ffc*)h->nearV.p, x, y);
+                                            (const ffc*)h->nearV.p, x, y, h->exact_active);
   CQM_CHECK_LAUNCH();
   return CQM_OK;
 }

@@ -17,7 +17,7 @@ struct GmresWork {
   int m = 0;
   DArray<double2> Vb, r, H, sn, g, y, Z, p1, p2;  // p1, p2: partial dot products
   DArray<double> cs, bnorm, beta, thr, nrm;
-  DArray<int> active, kdim, converged, counters;
+  DArray<int> active, kdim, converged, counters, need;
   DArray<unsigned long long> work;  // [0] basis vectors, [1] frequency steps of the Arnoldi steps
   int* h_counters = nullptr;  // pinned
 };
@@ -31,6 +31,15 @@ __global__ void k_restart(int M, int m, const double2* __restrict__ b, const dou
                           double rtol, double* thr, int first, int* counters) {
   __shared__ double sh[32];
   const int l = blockIdx.x;
+  // converged at an earlier restart: the solution has not changed since, and
+  // y (not computed for it) is not read; the residual and state stay
+  if (!first && converged[l]) {
+    if (threadIdx.x == 0) {
+      active[l] = 0;
+      for (int k = 0; k <= m; ++k) g[(size_t)l * (m + 1) + k] = make_double2(0.0, 0.0);
+    }
+    return;
+  }
   const double2* bl = b + (size_t)l * M;
   double2* rl = r + (size_t)l * M;
   double s = 0.0, sb = 0.0;
@@ -65,6 +74,12 @@ __global__ void k_restart(int M, int m, const double2* __restrict__ b, const dou
   const double inv = 1.0 / bt;
   double2* v0 = V0 + (size_t)l * M;
   for (int i = threadIdx.x; i < M; i += blockDim.x) v0[i] = cscale(rl[i], inv);
+}
+
+// need[l] = !converged[l]
+__global__ void k_not(int n, const int* __restrict__ a, int* __restrict__ b) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = a[i] ? 0 : 1;
 }
 
 // Reference norms of the convergence test: bnorm_l <- max(bnorm_l, floor *
@@ -318,7 +333,7 @@ int gmres_solve(cqm_handle* h, const double2* d_b, double2* d_x, cqm_solve_info*
     W.Vb.free(A); W.r.free(A); W.Z.free(A); W.H.free(A); W.sn.free(A); W.g.free(A); W.y.free(A);
     W.p1.free(A); W.p2.free(A); W.nrm.free(A);
     W.cs.free(A); W.bnorm.free(A); W.beta.free(A); W.thr.free(A); W.active.free(A); W.kdim.free(A);
-    W.converged.free(A); W.counters.free(A); W.work.free(A);
+    W.converged.free(A); W.counters.free(A); W.work.free(A); W.need.free(A);
     if (W.h_counters) cudaFreeHost(W.h_counters);
   };
 #define GM_TRY(e) do { st = (e); if (st != CQM_OK) { cleanup(); return st; } } while (0)
@@ -339,6 +354,7 @@ int gmres_solve(cqm_handle* h, const double2* d_b, double2* d_x, cqm_solve_info*
   GM_TRY(W.converged.allocate(A, Ls));
   GM_TRY(W.counters.allocate(A, 4));
   GM_TRY(W.work.allocate(A, 2));
+  GM_TRY(W.need.allocate(A, Ls));
   // row chunks per frequency for the Arnoldi kernels: about 4 blocks per SM in
   // all, at least 256 rows per chunk
   const int nch = std::max(1, std::min((M + 255) / 256, (4 * 152 + Ls - 1) / Ls));
@@ -372,7 +388,14 @@ int gmres_solve(cqm_handle* h, const double2* d_b, double2* d_x, cqm_solve_info*
   int status = CQM_OK;
   while (true) {
     double2* Ax = W.Vb.p + (size_t)1 * Ls * M;  // scratch: basis slot 1
-    if (!first) GM_TRY(apply_operator(h, d_x, Ax));
+    if (!first) {
+      // the residual only of the frequencies not converged at an earlier restart
+      k_not<<<grid_for(Ls, 256), 256, 0, S>>>(Ls, W.converged.p, W.need.p);
+      h->exact_active = W.need.p;
+      const int ast = apply_operator(h, d_x, Ax);
+      h->exact_active = nullptr;
+      GM_TRY(ast);
+    }
     GM_TRY(cu(cudaMemsetAsync(W.counters.p, 0, 4 * sizeof(int), S)));
     {
       ProfScope ps_(h, CQM_K_GMRES_OTHER);

@@ -534,8 +534,9 @@ static int apply_t(cqm_handle* h, const OpView<R>& V, const double2* x, double2*
   const int nleaf = (int)h->h_leaves.size(), nfr = (int)h->h_far_rows.size();
   const int M = h->M, Ls = h->Ls, p = h->p, m = h->m;
   cudaStream_t S = h->stream;
-  // the inner (FP32) apply inside GMRES skips converged frequencies
-  const int* act = std::is_same<R, float>::value ? h->inner_active : nullptr;
+  // inside GMRES the inner (FP32) apply skips converged frequencies, and the
+  // restart's FP64-accurate apply those whose residual is already final
+  const int* act = std::is_same<R, float>::value ? h->inner_active : h->exact_active;
   if (far_only) {
     // the caller has written y
   } else if (ff) {

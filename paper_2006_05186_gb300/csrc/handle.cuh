@@ -118,6 +118,10 @@ struct cqm_handle {
   // otherwise): the kernels of the inner apply that work per frequency or per
   // chunk of 32 skip the others, whose results GMRES does not read
   const int* inner_active = nullptr;
+  // frequencies whose residual a GMRES restart recomputes (null otherwise):
+  // the FP64-accurate apply's expanded streams and sweeps skip the others
+  // (converged at an earlier restart: their solution has not changed since)
+  const int* exact_active = nullptr;
   // bf16 images of the far factors for the tensor-core coupling (32 KB per rank
   // term, term t of block b at tc2_first[b] + t) and the FP32 expanded
   // couplings of its tail frequencies
