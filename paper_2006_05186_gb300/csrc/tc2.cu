@@ -8,36 +8,43 @@
 // and the rank terms of the block stream past it; d_t[l] scales row l of Z^T,
 // which is one value per TMEM lane, in the epilogue.  In real arithmetic, with
 // A = [Re xhat_c^T | Im xhat_c^T] (128 frequencies x K = 128) and
-// B = [Re C_t | Im C_t] (N = 64 x K = 128):
+// B = [Re C_t | Im C_t] (64 rows x K = 128):
 //   Re Z^T = A[:, :64] Re C^T - A[:, 64:] Im C^T   (B's second K half negated),
-//   Im Z^T = A[:, :64] Im C^T + A[:, 64:] Re C^T   (B's K halves swapped),
-// two GEMMs of M = 128, N = 64, K = 128 per rank term.  Operands are split
-// as hi + lo in bf16 and the products hi*hi + hi*lo + lo*hi are accumulated
-// in fp32 (about 2^-17 per product; the inner operator only steers GMRES,
-// whose restarts recompute the residual in float-float).
+//   Im Z^T = A[:, :64] Im C^T + A[:, 64:] Re C^T   (B's K halves swapped).
+// Two consecutive rank terms t, t + 1 of a block share A, so their B operands
+// are stacked into one of N = 128 rows: per pair of terms, two GEMMs of
+// M = 128, N = 128, K = 128 (the tensor pipe takes about as long for an MMA of
+// N = 64 as for one of N = 128).  The last term of a block of odd rank runs
+// alone with N = 64.  Operands are split as hi + lo in bf16 and the products
+// hi*hi + hi*lo + lo*hi are accumulated in fp32 (about 2^-17 per product; the
+// inner operator only steers GMRES, whose restarts recompute the residual in
+// float-float).
 //
 // Layout and roles (one CTA per work item: a row cluster and a run of its far
 // blocks; 1 CTA per SM, which owns the 512 TMEM columns):
 //   TMEM columns [0, 256): A, two buffers of 128 (bf16 hi 64 + lo 64; lane l
 //     holds frequency l0 + l, two bf16 per column, lower K in the low half);
-//   TMEM columns [256, 512): accumulators, two buffers of 128 (Re Z^T 64 +
-//     Im Z^T 64 columns, one per mu).
-//   shared memory: a ring of NSTAGE B images of 32 KB, copied whole from the
-//     precomputed images in HBM by one bulk copy each (warp 13); an image holds
-//     the hi and lo planes of [Re C_t | Im C_t] in the canonical K-major
-//     layout without swizzle (core matrices of 8 rows x 16 bytes, K-adjacent
-//     ones 128 bytes apart, 8-row groups 2048 bytes apart).
+//   TMEM columns [256, 512): accumulators, slot 0 for Re Z^T and slot 1 for
+//     Im Z^T of one pair (128 columns each: mu of term t, then mu of t + 1).
+//   shared memory: a ring of NSTAGE stages of 64 KB, [hi t | hi t+1 | lo t |
+//     lo t+1], each plane (16 KB) bulk-copied from the term's precomputed
+//     32 KB image in HBM (warp 13); a plane is 64 rows x 128 bf16 of
+//     [Re C_t | Im C_t] in the canonical K-major layout without swizzle (core
+//     matrices of 8 rows x 16 bytes, K-adjacent ones 128 bytes apart, 8-row
+//     groups 2048 bytes apart), so the two hi (lo) planes of a stage are one
+//     operand of 128 rows.
 //   warps 8-11 build A for each block from xhat_c (one lane per frequency);
-//   warp 12 (one thread) issues 48 MMAs per rank term and frees each B stage,
-//     accumulator and A buffer with tcgen05.commit;
-//   warps 0-7 (two per TMEM lane quadrant, 32 mu each) read each term's
-//     accumulator (one lane per frequency), multiply by d_t[l] (loaded three
-//     terms ahead) and keep the row's sum over all terms in registers, then
-//     write the item's partial tile, which the per-row reduction adds in item
-//     order.  CTA k takes the items at launch positions k, k + grid, ...
-//     (launched with one CTA per item, the hardware schedules the items as
-//     SMs free up); the launch order puts the largest items first, so that
-//     the small ones fill the end of the schedule.
+//   warp 12 (one thread) issues 24 MMAs into slot 0 and 24 into slot 1 per
+//     pair and frees each B stage, accumulator slot and A buffer with
+//     tcgen05.commit;
+//   warps 0-7 (two per TMEM lane quadrant, 32 mu each) read each slot (one
+//     lane per frequency), multiply by d_t[l] and d_{t+1}[l] (loaded two pairs
+//     ahead) and keep the row's sum over all terms in registers, then write
+//     the item's partial tile, which the per-row reduction adds in item order.
+//     CTA k takes the items at launch positions k, k + grid, ... (launched with
+//     one CTA per item, the hardware schedules the items as SMs free up); the
+//     launch order puts the largest items first, so that the small ones fill
+//     the end of the schedule.
 // Frequencies go in chunks of 128 lanes (the last one padded); when Ls mod 128
 // is 1 to TAIL_MAX the remaining frequencies are applied from an FP32 table of
 // the expanded couplings S_b(l) = sum_t d_t[l] C_t instead (k_far_tail_f32).
@@ -56,9 +63,10 @@ namespace cqm {
 
 namespace {
 constexpr int TP = 64;                 // Chebyshev points per cluster (m = 4)
-constexpr int NSTAGE = 6;              // B stages
-constexpr uint32_t BIMG = 32768;       // bytes of one B image (hi + lo planes)
+constexpr int NSTAGE = 3;              // B stages
+constexpr uint32_t BIMG = 32768;       // bytes of one term's B image in HBM (hi + lo planes)
 constexpr uint32_t BPLANE = 16384;     // one plane: 64 rows x 128 bf16
+constexpr uint32_t BSTAGE = 65536;     // one stage: the planes of a pair of terms
 constexpr uint32_t B_SBO = 2048;       // 8-row groups
 constexpr uint32_t B_LBO = 128;        // K-adjacent core matrices
 constexpr int NTHREADS = 448;          // warps 0-7 epilogue, 8-11 A, 12 MMA, 13 loader
@@ -68,7 +76,7 @@ constexpr int MUE = TP / 2;            // mu columns per epilogue warp
 constexpr uint32_t TCOLS = 512;
 constexpr uint32_t ACC0 = 256;         // first accumulator column
 constexpr int ERR_TIMEOUT = 1;
-constexpr size_t SMEM = (size_t)NSTAGE * BIMG + 1024;
+constexpr size_t SMEM = (size_t)NSTAGE * BSTAGE + 1024;
 }  // namespace
 
 constexpr int TC2_TAIL_MAX = 4;
@@ -174,9 +182,9 @@ __global__ void __launch_bounds__(256) k_far_tail_f32(int Ls, int l0, int ntail,
   }
 }
 
-// Position in the sequence (item, chunk, block, term) of one CTA: items
-// blockIdx.x, blockIdx.x + gridDim.x, ...; blocks of rank 0 skipped; done()
-// once the items are exhausted.
+// Position in the sequence (item, chunk, block, pair of terms t, t + 1) of
+// one CTA: items blockIdx.x, blockIdx.x + gridDim.x, ...; blocks of rank 0
+// skipped; done() once the items are exhausted.
 struct Seq {
   int ii, ch, bi, t;
   int b0, b1;
@@ -216,9 +224,12 @@ struct Seq {
     }
   }
   __device__ bool done() const { return ii >= n_items; }
-  // advance by one term; returns true if the block (or chunk, or item) changed
+  // the unit holds terms t and t + 1 (false: t is a block's last, odd term)
+  __device__ bool two() const { return t + 1 < rank[bi]; }
+  // advance by one pair; returns true if the block (or chunk, or item) changed
   __device__ bool next() {
-    if (++t < rank[bi]) return false;
+    t += 2;
+    if (t < rank[bi]) return false;
     t = 0;
     ++bi;
     skip();
@@ -227,12 +238,13 @@ struct Seq {
   __device__ bool same_block(const Seq& o) const { return ii == o.ii && ch == o.ch && bi == o.bi; }
 };
 
-// d_t[l] of the term at q for this lane's frequency of q's chunk (0 past the end)
-__device__ __forceinline__ float2 term_d(const Seq& q, const float2* __restrict__ Df, int cap, int Ls,
+// d_{t+j}[l] (j = 0, 1) of the pair at q for this lane's frequency of q's
+// chunk (0 past the end and for the missing second term)
+__device__ __forceinline__ float2 term_d(const Seq& q, int j, const float2* __restrict__ Df, int cap, int Ls,
                                          int qd, int lane) {
-  if (q.done()) return make_float2(0.f, 0.f);
+  if (q.done() || (j && !q.two())) return make_float2(0.f, 0.f);
   const int l = 128 * q.ch + 32 * qd + lane;
-  return l < Ls ? __ldg(Df + ((size_t)q.bi * cap + q.t) * Ls + l) : make_float2(0.f, 0.f);
+  return l < Ls ? __ldg(Df + ((size_t)q.bi * cap + q.t + j) * Ls + l) : make_float2(0.f, 0.f);
 }
 
 __global__ void __launch_bounds__(NTHREADS, 1)
@@ -281,49 +293,60 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   uint32_t n_issued = 0;  // loader: images copied
   if (warp == W_MMA) {
     // -------------------------------------------------------------- MMA issue
-    constexpr uint32_t ID_RE = idesc_bf16(128, 64, false);
-    constexpr uint32_t ID_NEG = idesc_bf16(128, 64, true);
+    constexpr uint32_t ID2 = idesc_bf16(128, 128, false), ID2N = idesc_bf16(128, 128, true);
+    constexpr uint32_t ID1 = idesc_bf16(128, 64, false), ID1N = idesc_bf16(128, 64, true);
     Seq q;
     q.start(items, order, n_items, nch, rank);
-    uint32_t ib = 0, ia = 0;
-    bool first_term = true;
+    uint32_t ib = 0, ia = 0;  // pairs issued, blocks entered
+    bool first_pair = true;
     while (!q.done()) {
-      const int s = (int)(ib % NSTAGE), cb = (int)(ib & 1u), ab = (int)(ia & 1u);
+      const int s = (int)(ib % NSTAGE), ab = (int)(ia & 1u);
+      const bool two = q.two(), last_pair = q.t + 2 >= rank[q.bi];
+      const uint32_t id = two ? ID2 : ID1, idn = two ? ID2N : ID1N;
+      const uint32_t a_hi = tmem + 128u * ab, a_lo = a_hi + 64u;
+      const uint32_t bh = smem_u32(ring + (size_t)s * BSTAGE), bl = bh + 2u * BPLANE;
       bool ok = mbar_wait(&b_full[s], (ib / NSTAGE) & 1u, &abort_sh, err, ERR_TIMEOUT, lim);
-      if (first_term) ok = mbar_wait(&a_full[ab], (ia >> 1) & 1u, &abort_sh, err, ERR_TIMEOUT, lim) && ok;
-      if (ib >= 2) ok = mbar_wait(&c_empty[cb], ((ib >> 1) - 1) & 1u, &abort_sh, err, ERR_TIMEOUT, lim) && ok;
-      ok = __all_sync(0xffffffffu, ok);
-      tc_fence_after();
-      const bool last_term = q.t + 1 == rank[q.bi];
-      if (lane == 0) {
-        if (ok) {
-          const uint32_t a_hi = tmem + 128u * ab, a_lo = a_hi + 64u;
-          const uint32_t zr = tmem + ACC0 + 128u * cb, zi = zr + 64u;
-          const uint32_t bh = smem_u32(ring + (size_t)s * BIMG), bl = bh + BPLANE;
-          // products hi*hi, hi*lo, lo*hi over K = 128 in 8 steps of 16
+      if (first_pair) ok = mbar_wait(&a_full[ab], (ia >> 1) & 1u, &abort_sh, err, ERR_TIMEOUT, lim) && ok;
+      // slot 0 (Re Z^T), then slot 1 (Im Z^T); each is free once the epilogue
+      // has read the previous pair's
 #pragma unroll
-          for (int pr = 0; pr < 3; ++pr) {
-            const uint32_t aa = pr == 2 ? a_lo : a_hi;
-            const uint32_t bb = pr == 1 ? bl : bh;
+      for (int sl = 0; sl < 2; ++sl) {
+        if (ib >= 1) ok = mbar_wait(&c_empty[sl], (ib - 1) & 1u, &abort_sh, err, ERR_TIMEOUT, lim) && ok;
+        ok = __all_sync(0xffffffffu, ok);
+        tc_fence_after();
+        if (lane == 0) {
+          if (ok) {
+            const uint32_t z = tmem + ACC0 + 128u * sl;
+            // products hi*hi, hi*lo, lo*hi over K = 128 in 8 steps of 16
 #pragma unroll
-            for (int ks = 0; ks < 8; ++ks) {
-              const uint32_t acc = (pr == 0 && ks == 0) ? 0u : 1u;
-              mma_bf16_ts(zr, aa + 8u * ks, sdesc_lbo_sbo(bb + 256u * ks, B_LBO, B_SBO),
-                          ks < 4 ? ID_RE : ID_NEG, acc);
-              mma_bf16_ts(zi, aa + 8u * ks, sdesc_lbo_sbo(bb + 256u * ((ks + 4) & 7), B_LBO, B_SBO),
-                          ID_RE, acc);
+            for (int pr = 0; pr < 3; ++pr) {
+              const uint32_t aa = pr == 2 ? a_lo : a_hi;
+              const uint32_t bb = pr == 1 ? bl : bh;
+#pragma unroll
+              for (int ks = 0; ks < 8; ++ks) {
+                const uint32_t acc = (pr == 0 && ks == 0) ? 0u : 1u;
+                if (sl == 0)
+                  mma_bf16_ts(z, aa + 8u * ks, sdesc_lbo_sbo(bb + 256u * ks, B_LBO, B_SBO), ks < 4 ? id : idn,
+                              acc);
+                else
+                  mma_bf16_ts(z, aa + 8u * ks, sdesc_lbo_sbo(bb + 256u * ((ks + 4) & 7), B_LBO, B_SBO), id,
+                              acc);
+              }
             }
           }
+          mma_commit(&c_full[sl]);
         }
+        __syncwarp();
+      }
+      if (lane == 0) {
         mma_commit(&b_empty[s]);
-        mma_commit(&c_full[cb]);
-        if (last_term) mma_commit(&a_empty[ab]);
+        if (last_pair) mma_commit(&a_empty[ab]);
       }
       __syncwarp();
       ++ib;
       const bool newblock = q.next();
       if (newblock) ++ia;
-      first_term = newblock;
+      first_pair = newblock;
     }
   } else if (warp == W_LOAD) {
     // ------------------------------------------------------------ B loader
@@ -335,8 +358,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         if (n_issued >= NSTAGE &&
             !mbar_wait(&b_empty[s], (n_issued / NSTAGE - 1) & 1u, &abort_sh, err, ERR_TIMEOUT, lim))
           break;
-        mbar_arrive_expect_tx(&b_full[s], BIMG);
-        bulk_g2s(ring + (size_t)s * BIMG, img + (size_t)(first[q.bi] + q.t) * BIMG, BIMG, &b_full[s]);
+        const bool two = q.two();
+        unsigned char* st = ring + (size_t)s * BSTAGE;
+        const unsigned char* src = img + (size_t)(first[q.bi] + q.t) * BIMG;  // [hi t | lo t | hi t+1 | lo t+1]
+        mbar_arrive_expect_tx(&b_full[s], two ? 4u * BPLANE : 2u * BPLANE);
+        bulk_g2s(st, src, BPLANE, &b_full[s]);
+        bulk_g2s(st + 2u * BPLANE, src + BPLANE, BPLANE, &b_full[s]);
+        if (two) {
+          bulk_g2s(st + BPLANE, src + 2u * BPLANE, BPLANE, &b_full[s]);
+          bulk_g2s(st + 3u * BPLANE, src + 3u * BPLANE, BPLANE, &b_full[s]);
+        }
       }
     }
     __syncwarp();
@@ -400,45 +431,58 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     Seq q, qp;
     q.start(items, order, n_items, nch, rank);
     qp = q;
-    // d_t of the next three terms, loaded ahead of their accumulators
-    float2 d0 = term_d(qp, Df, cap, Ls, qd, lane);
+    // d_t, d_{t+1} of the next two pairs, loaded ahead of their accumulators
+    float2 da0 = term_d(qp, 0, Df, cap, Ls, qd, lane), db0 = term_d(qp, 1, Df, cap, Ls, qd, lane);
     if (!qp.done()) qp.next();
-    float2 d1 = term_d(qp, Df, cap, Ls, qd, lane);
+    float2 da1 = term_d(qp, 0, Df, cap, Ls, qd, lane), db1 = term_d(qp, 1, Df, cap, Ls, qd, lane);
     if (!qp.done()) qp.next();
-    float2 d2 = term_d(qp, Df, cap, Ls, qd, lane);
-    if (!qp.done()) qp.next();
-    uint32_t ic = 0;
+    uint32_t ic = 0;  // pairs consumed
     for (int ii = blockIdx.x; ii < n_items; ii += gridDim.x) {
       for (int ch = 0; ch < nch; ++ch) {
         while (!q.done() && q.ii == ii && q.ch == ch) {
-          const int cb = (int)(ic & 1u);
-          const float2 d = d0;
-          d0 = d1;
-          d1 = d2;
-          d2 = term_d(qp, Df, cap, Ls, qd, lane);
+          const bool two = q.two();
+          const float2 da = da0, db = db0;
+          da0 = da1;
+          db0 = db1;
+          da1 = term_d(qp, 0, Df, cap, Ls, qd, lane);
+          db1 = term_d(qp, 1, Df, cap, Ls, qd, lane);
           if (!qp.done()) qp.next();
-          bool ok = mbar_wait(&c_full[cb], (ic >> 1) & 1u, &abort_sh, err, ERR_TIMEOUT, lim);
-          ok = __all_sync(0xffffffffu, ok);
-          tc_fence_after();
-          if (ok) {
-            const uint32_t zr = trow + ACC0 + 128u * cb + (uint32_t)mu0, zi = zr + 64u;
 #pragma unroll
-            for (int m0 = 0; m0 < MUE; m0 += 16) {
-              uint32_t vr[16], vi[16];
-              tmem_ld16(zr + (uint32_t)m0, vr);
-              tmem_ld16(zi + (uint32_t)m0, vi);
-              tmem_wait_ld();
+          for (int sl = 0; sl < 2; ++sl) {
+            bool ok = mbar_wait(&c_full[sl], ic & 1u, &abort_sh, err, ERR_TIMEOUT, lim);
+            ok = __all_sync(0xffffffffu, ok);
+            tc_fence_after();
+            if (ok) {
+              // slot 0 holds Re Z^T: y += d Re z; slot 1 holds Im Z^T: y += i d Im z
+              const float war = sl ? -da.y : da.x, wai = sl ? da.x : da.y;
+              const float wbr = sl ? -db.y : db.x, wbi = sl ? db.x : db.y;
+              const uint32_t z = trow + ACC0 + 128u * sl + (uint32_t)mu0;
 #pragma unroll
-              for (int j = 0; j < 16; ++j) {
-                const float a = __uint_as_float(vr[j]), bq = __uint_as_float(vi[j]);
-                yr[m0 + j] = fmaf(d.x, a, fmaf(-d.y, bq, yr[m0 + j]));
-                yi[m0 + j] = fmaf(d.x, bq, fmaf(d.y, a, yi[m0 + j]));
+              for (int m0 = 0; m0 < MUE; m0 += 16) {
+                uint32_t va[16], vb[16];
+                tmem_ld16(z + (uint32_t)m0, va);
+                if (two) tmem_ld16(z + 64u + (uint32_t)m0, vb);
+                tmem_wait_ld();
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                  const float a = __uint_as_float(va[j]);
+                  yr[m0 + j] = fmaf(war, a, yr[m0 + j]);
+                  yi[m0 + j] = fmaf(wai, a, yi[m0 + j]);
+                }
+                if (two) {
+#pragma unroll
+                  for (int j = 0; j < 16; ++j) {
+                    const float bq = __uint_as_float(vb[j]);
+                    yr[m0 + j] = fmaf(wbr, bq, yr[m0 + j]);
+                    yi[m0 + j] = fmaf(wbi, bq, yi[m0 + j]);
+                  }
+                }
               }
             }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&c_empty[sl]);
           }
-          tc_fence_before();
-          __syncwarp();
-          if (lane == 0) mbar_arrive(&c_empty[cb]);
           ++ic;
           q.next();
         }
