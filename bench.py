@@ -90,16 +90,32 @@ FP32_ISSUE_PEAK_T = 152 * 128 * 2.07e9 / 1e12
 MACA_FF_INSTR_PER_EVAL = 160
 
 
-# DRAM bytes (read + write) of one launch of the bf16 tensor-core coupling per
-# far rank term, from an ncu capture of that kernel: 461.1 MB + 23.2 MB over
-# the 13,284 far rank terms of the 1280-triangle sphere at N = 256 (one
-# full capture of the kernel on that case).  The traffic is the 32 KB
-# bf16 image of each rank term read once plus the small d_t, xhat and
-# partial-tile terms, so it grows with the rank terms and the bench scales it
-# to the workload's count.
-TC2_DRAM_BYTES_PER_RANK_TERM = (461.124352e6 + 23.230976e6) / 13284
+# DRAM bytes (read + write) of one launch of the bf16 tensor-core coupling from
+# an ncu capture of that kernel on the 1280-triangle sphere at N = 256, with
+# the capture's far rank terms and how many of them took the single product
+# (None: no capture of the current kernel).  The traffic is the bf16 images
+# (hi and lo planes, 32 KB, of a three-product term; the 16 KB hi plane of a
+# single-product one) read once, plus d_t, xhat and the partial tiles, which
+# grow with the rank terms: the bench counts the workload's image bytes and
+# scales the rest per rank term.
+TC2_CAPTURE = None
 TC2_DRAM_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of k_far_coupling_tc2 (1280-triangle "
-                   "sphere, N = 256), per far rank term, scaled to this workload's terms")
+                   "sphere, N = 256): this workload's image bytes plus the capture's other bytes per rank term")
+
+
+def tc2_image_bytes(terms, single):
+    return 32768.0 * (terms - single) + 16384.0 * single
+
+
+def tc2_traffic(info):
+    """DRAM bytes of one launch of the tensor-core coupling on this workload,
+    from the capture (None without one)."""
+    c = TC2_CAPTURE
+    if not c:
+        return None
+    rest = (c["dram"] - tc2_image_bytes(c["terms"], c["single"])) / c["terms"]
+    terms = info["rank_sum_far"]
+    return tc2_image_bytes(terms, info.get("tc_single_terms", 0)) + rest * terms
 
 
 def tf32_peak():
@@ -254,22 +270,35 @@ def kernel_models(info, Ls, p, tensor_cores, tf32=None, sinfo=None, launches_per
         models["far_coupling"] = dict(
             bound="tensor", peak=bf16, unit="TFLOP/s", work=8.0 * cmac_far,
             peak_source=f"{src} cuBLAS bf16 GEMM, sustained (MEASURED_PEAKS.json bf16_tflops_sustained)",
-            what=("complex MAC on tcgen05 bf16 (useful flops; the hi/lo three-product split "
-                  "executes 3x, and frequencies are padded to 128-row chunks)"),
-            traffic=TC2_DRAM_BYTES_PER_RANK_TERM * info["rank_sum_far"] if TC2_DRAM_BYTES_PER_RANK_TERM else None,
+            what=("complex MAC on tcgen05 bf16 at all Ls frequencies of every apply (useful flops; the "
+                  "hi/lo three-product split executes 3x for the leading rank terms and 1x for the "
+                  f"{info.get('tc_single_terms', 0)} trailing ones, frequencies are padded to 128-row chunks, "
+                  "and converged frequencies are computed with the rest)"),
+            traffic=tc2_traffic(info),
             traffic_source=TC2_DRAM_SOURCE)
     pk, src = _peaks()
     hbm = dict(bound="hbm", peak=pk["hbm_gbs"], unit="GB/s",
                peak_source=f"{src} STREAM-style copy, MEASURED_PEAKS.json hbm_gbs")
-    entries = info["near_entries"] * Ls
+    # The streaming kernels skip converged frequencies: the inner applies (one
+    # per Arnoldi step) read the active ones, the FP64-accurate applies (one
+    # per restart after the first) those not converged at an earlier restart.
+    f_inner, f_exact, note_i, note_e = Ls, Ls, "", ""
+    if sinfo and sinfo.get("iterations") and sinfo.get("arnoldi_freq_steps"):
+        f_inner = sinfo["arnoldi_freq_steps"] / sinfo["iterations"]
+        note_i = f", {f_inner:.1f} active frequencies per apply on average"
+    if sinfo and sinfo.get("restarts") and sinfo.get("restart_freq_applies"):
+        f_exact = sinfo["restart_freq_applies"] / sinfo["restarts"]
+        note_e = f", {f_exact:.1f} unconverged frequencies per apply on average"
     if info.get("near_expanded"):
-        models["near_apply"] = dict(hbm, work=8.0 * entries,
-                                    what="expanded FP32 near field streamed (8 B per entry and frequency)")
-        models["near_exact"] = dict(hbm, work=16.0 * entries,
-                                    what="expanded float-float near field streamed (16 B per entry and frequency)")
+        models["near_apply"] = dict(hbm, work=8.0 * info["near_entries"] * f_inner,
+                                    what="expanded FP32 near field streamed (8 B per entry and frequency" + note_i + ")")
+        models["near_exact"] = dict(hbm, work=16.0 * info["near_entries"] * f_exact,
+                                    what="expanded float-float near field streamed (16 B per entry and frequency"
+                                    + note_e + ")")
     if info.get("far_expanded"):
-        models["far_exact"] = dict(hbm, work=16.0 * info["far_coupling"] * Ls,
-                                   what="expanded float-float far couplings streamed (16 B per entry and frequency)")
+        models["far_exact"] = dict(hbm, work=16.0 * info["far_coupling"] * f_exact,
+                                   what="expanded float-float far couplings streamed (16 B per entry and frequency"
+                                   + note_e + ")")
     lps = launches_per_step or {}
     issue = dict(bound="alu", peak=FP32_ISSUE_PEAK_T, unit="Tinst/s",
                  peak_source="FP32 issue: unit counts x max SM clock (152 SMs x 128 lanes x 2.07 GHz)")
@@ -485,6 +514,8 @@ def run_ours(args):
                    "bdf": 2, "eta": W["eta"], "cheb_m": W["cheb_m"], "leaf": W["n_min"],
                    "aca_eps": W["aca_eps"], "mode": "h2maca", "parallelism": f"replicas{world}",
                    "far_coupling": {1: "tcgen05 bf16 x3", 2: "tcgen05 tf32 x3"}.get(inf["tensor_cores"], "fp32 simt"),
+                   "far_single_product_terms": (f"{inf.get('tc_single_terms', 0)} of {inf['rank_sum_far']} "
+                                                "(trailing terms <= 1e-3 of the largest far term at every frequency)"),
                    "l2": "256 MB buffer written between timed steps; working set "
                          f"{inf['device_bytes'] / 2**30:.1f} GiB > L2"},
         "latency_ms": {"p50": 1e3 * lat[len(lat) // 2],
@@ -501,7 +532,8 @@ def run_ours(args):
                                            "rank_max", "t_tree_ms", "t_bases_ms", "t_assembly_ms",
                                            "near_expanded", "far_expanded")},
                       total_ms=inf["t_geometry_ms"] + inf["t_tree_ms"] + inf["t_bases_ms"] + inf["t_assembly_ms"]),
-        "solve": dict({k: sinfos[-1][k] for k in ("iterations", "restarts", "t_gmres_ms", "arnoldi_freq_steps")},
+        "solve": dict({k: sinfos[-1][k] for k in ("iterations", "restarts", "t_gmres_ms", "arnoldi_freq_steps",
+                                                 "restart_freq_applies")},
                       total_ms=sinfos[-1]["t_forward_ms"] + sinfos[-1]["t_gmres_ms"] + sinfos[-1]["t_inverse_ms"]),
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(L * M * 8 + m.xyz.nbytes + m.tri.nbytes),

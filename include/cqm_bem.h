@@ -138,6 +138,15 @@ typedef struct cqm_params {
                              (~47 bits) on the FP32 pipes, exp(-s r0) of each pair's
                              distance bound in FP64; 0 = FP64 throughout   [1]   */
   const cqm_allocator* allocator; /* NULL: stream-ordered CUDA pool        [NULL] */
+  double tc_single_ratio; /* with tensor_cores = 1: the trailing rank terms of a far
+                             block whose size ||C_t||_F |d_t(l)| is at most this
+                             fraction of the largest far term at every frequency l
+                             take one bf16 product (hi*hi) instead of the
+                             three-product split, and their lo planes are not read;
+                             the rounding of a term this small (~2^-8 of it) stays
+                             below the inner operator's other errors.  Only the
+                             inner iterations see it (restarts are FP64-accurate).
+                             0 = three products throughout                 [1e-3] */
 } cqm_params;
 
 /* Setup product summary. */
@@ -162,6 +171,9 @@ typedef struct cqm_setup_info {
    * pair at all Ls frequencies.  Slices are counted exactly (the ranks times
    * the block's points); fibres with each block's mean points per pair. */
   int64_t maca_slice_evals, maca_fibre_evals;
+  /* tensor_cores = 1: far rank terms that take the single-product MMAs
+   * (tc_single_ratio), out of rank_sum_far */
+  int64_t tc_single_terms;
 } cqm_setup_info;
 
 /* Per-solve summary. */
@@ -177,6 +189,10 @@ typedef struct cqm_solve_info {
   /* Arnoldi work: sum over steps and active frequencies of the basis vectors
    * the step orthogonalises against (j + 1 at step j), and of 1. */
   int64_t arnoldi_vectors, arnoldi_freq_steps;
+  /* FP64-accurate operator applies of the restarts after the first, in
+   * frequencies: each recomputes the residual of the frequencies not converged
+   * at an earlier restart. */
+  int64_t restart_freq_applies;
 } cqm_solve_info;
 
 typedef struct cqm_handle cqm_handle;

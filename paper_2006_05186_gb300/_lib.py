@@ -63,6 +63,7 @@ class cqm_params(C.Structure):
         ("expand_far", C.c_int32),
         ("maca_ff", C.c_int32),
         ("allocator", C.POINTER(cqm_allocator)),
+        ("tc_single_ratio", C.c_double),
     ]
 
 
@@ -77,6 +78,7 @@ class cqm_setup_info(C.Structure):
         ("t_assembly_ms", C.c_double), ("near_rank_entries", C.c_int64),
         ("near_expanded", C.c_int32), ("far_expanded", C.c_int32),
         ("maca_slice_evals", C.c_int64), ("maca_fibre_evals", C.c_int64),
+        ("tc_single_terms", C.c_int64),
     ]
 
 
@@ -86,6 +88,7 @@ class cqm_solve_info(C.Structure):
         ("Ls", C.c_int32), ("max_rel_residual", C.c_double), ("max_imag", C.c_double),
         ("t_forward_ms", C.c_double), ("t_gmres_ms", C.c_double), ("t_inverse_ms", C.c_double),
         ("arnoldi_vectors", C.c_int64), ("arnoldi_freq_steps", C.c_int64),
+        ("restart_freq_applies", C.c_int64),
     ]
 
 

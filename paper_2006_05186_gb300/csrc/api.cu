@@ -87,6 +87,7 @@ int cqm_params_default(cqm_params* p) {
   p->maca_ff = 1;
   p->tensor_cores = 1;
   p->allocator = nullptr;
+  p->tc_single_ratio = 1e-3;
   return CQM_OK;
 }
 
@@ -112,7 +113,7 @@ int cqm_bem_destroy(cqm_handle* h) {
   h->diam.free(A); h->flag.free(A); h->near_pt.free(A);
   h->exp_t2_ff.free(A); h->exp_cs_ff.free(A); h->pt_r0.free(A);
   h->fpt_d.free(A); h->fpt_c.free(A); h->fpt_r0.free(A);
-  h->tc2_first.free(A); h->tc2_img.free(A); h->tc2_tail.free(A);
+  h->tc2_first.free(A); h->tc2_img.free(A); h->tc2_tail.free(A); h->tc2_t1.free(A);
   for (int t = 0; t < 3; ++t) { h->ss_pt[t].free(A); h->ss_w[t].free(A); }
   h->s.free(A); h->Vd.free(A); h->exp_t2.free(A); h->exp_cs.free(A);
   h->perm.free(A); h->node_begin.free(A); h->node_end.free(A); h->node_son0.free(A);
@@ -177,7 +178,7 @@ int cqm_bem_setup(const cqm_mesh* mesh, double dt, int32_t N, int32_t bdf_order,
       p.cheb_m < 1 || p.cheb_m > 4 || !(p.aca_eps > 0.0) || p.rank_cap < 1 || p.rank_cap > 64 ||
       (p.mode == CQM_MODE_H2MACA && p.n_min > 32) ||
       p.gmres_restart < 1 || p.gmres_max_iter < 1 || !(p.gmres_tol > 0.0) ||
-      !(p.inner_rtol >= 0.0 && p.inner_rtol < 1.0)) {
+      !(p.inner_rtol >= 0.0 && p.inner_rtol < 1.0) || !(p.tc_single_ratio >= 0.0)) {
     set_last_error("parameter out of range");
     return CQM_EINVAL;
   }

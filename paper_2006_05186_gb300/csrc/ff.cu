@@ -363,10 +363,14 @@ __global__ void __launch_bounds__(256) k_far_expand_ff(int Ls, int p, int cap, c
   }
   __syncthreads();
   const int pp = p * p;
-  // thread e -> (nu, mu) with mu fastest: consecutive threads write consecutive
-  // entries of the column-major table
-  for (int e = threadIdx.x; e < pp; e += blockDim.x) {
-    const int nu = e / p, mu = e - nu * p;
+  // 16 x 16 tiles of (mu, nu), nu fastest across the threads: a warp reads
+  // two runs of 16 consecutive factor entries (row-major C_t) and writes 16
+  // pairs of consecutive table entries (column-major S); blockDim.x = 256
+  const int nt16 = (p + 15) / 16;
+  for (int tile = 0; tile < nt16 * nt16; ++tile) {
+    const int mu = (tile / nt16) * 16 + (int)(threadIdx.x >> 4);
+    const int nu = (tile % nt16) * 16 + (int)(threadIdx.x & 15);
+    if (mu >= p || nu >= p) continue;
     ffc acc[FAR_NF];
 #pragma unroll
     for (int f = 0; f < FAR_NF; ++f) acc[f] = ffc_zero();
@@ -377,7 +381,7 @@ __global__ void __launch_bounds__(256) k_far_expand_ff(int Ls, int p, int cap, c
     }
     for (int f = 0; f < nf; ++f) {
       ffc_renorm(acc[f]);
-      S[((size_t)b * Ls + l0 + f) * pp + e] = acc[f];
+      S[((size_t)b * Ls + l0 + f) * pp + (size_t)nu * p + mu] = acc[f];
     }
   }
 }

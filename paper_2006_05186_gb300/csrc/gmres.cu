@@ -76,10 +76,13 @@ __global__ void k_restart(int M, int m, const double2* __restrict__ b, const dou
   for (int i = threadIdx.x; i < M; i += blockDim.x) v0[i] = cscale(rl[i], inv);
 }
 
-// need[l] = !converged[l]
-__global__ void k_not(int n, const int* __restrict__ a, int* __restrict__ b) {
+// need[l] = !converged[l]; *count += the number of such l
+__global__ void k_not(int n, const int* __restrict__ a, int* __restrict__ b, unsigned long long* count) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) b[i] = a[i] ? 0 : 1;
+  const int v = i < n && !a[i];
+  if (i < n) b[i] = v;
+  const int c = __popc(__ballot_sync(0xffffffffu, v));
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, (unsigned long long)c);
 }
 
 // Reference norms of the convergence test: bnorm_l <- max(bnorm_l, floor *
@@ -353,7 +356,7 @@ int gmres_solve(cqm_handle* h, const double2* d_b, double2* d_x, cqm_solve_info*
   GM_TRY(W.kdim.allocate(A, Ls));
   GM_TRY(W.converged.allocate(A, Ls));
   GM_TRY(W.counters.allocate(A, 4));
-  GM_TRY(W.work.allocate(A, 2));
+  GM_TRY(W.work.allocate(A, 3));
   GM_TRY(W.need.allocate(A, Ls));
   // row chunks per frequency for the Arnoldi kernels: about 4 blocks per SM in
   // all, at least 256 rows per chunk
@@ -377,7 +380,7 @@ int gmres_solve(cqm_handle* h, const double2* d_b, double2* d_x, cqm_solve_info*
     return CQM_OK;
   };
   GM_TRY(cu(cudaMemsetAsync(d_x, 0, sizeof(double2) * Ls * M, S)));
-  GM_TRY(cu(cudaMemsetAsync(W.work.p, 0, 2 * sizeof(unsigned long long), S)));
+  GM_TRY(cu(cudaMemsetAsync(W.work.p, 0, 3 * sizeof(unsigned long long), S)));
   GM_TRY(clear_wait_flag(h));
   GM_TRY(cu(cudaEventCreate(&e0)));
   GM_TRY(cu(cudaEventCreate(&e1)));
@@ -390,7 +393,7 @@ int gmres_solve(cqm_handle* h, const double2* d_b, double2* d_x, cqm_solve_info*
     double2* Ax = W.Vb.p + (size_t)1 * Ls * M;  // scratch: basis slot 1
     if (!first) {
       // the residual only of the frequencies not converged at an earlier restart
-      k_not<<<grid_for(Ls, 256), 256, 0, S>>>(Ls, W.converged.p, W.need.p);
+      k_not<<<grid_for(Ls, 256), 256, 0, S>>>(Ls, W.converged.p, W.need.p, W.work.p + 2);
       h->exact_active = W.need.p;
       const int ast = apply_operator(h, d_x, Ax);
       h->exact_active = nullptr;
@@ -471,7 +474,7 @@ int gmres_solve(cqm_handle* h, const double2* d_b, double2* d_x, cqm_solve_info*
   // beta_l = ||ghat_l - V_l qhat_l|| at the returned solution
   std::vector<double> rel(Ls), bn(Ls);
   std::vector<int> conv(Ls);
-  unsigned long long work[2] = {0, 0};
+  unsigned long long work[3] = {0, 0, 0};
   GM_TRY(cu(cudaMemcpyAsync(work, W.work.p, sizeof(work), cudaMemcpyDeviceToHost, S)));
   GM_TRY(cu(cudaMemcpyAsync(rel.data(), W.beta.p, sizeof(double) * Ls, cudaMemcpyDeviceToHost, S)));
   GM_TRY(cu(cudaMemcpyAsync(bn.data(), W.bnorm.p, sizeof(double) * Ls, cudaMemcpyDeviceToHost, S)));
@@ -496,6 +499,7 @@ int gmres_solve(cqm_handle* h, const double2* d_b, double2* d_x, cqm_solve_info*
     info->t_gmres_ms = ms;
     info->arnoldi_vectors = (int64_t)work[0];
     info->arnoldi_freq_steps = (int64_t)work[1];
+    info->restart_freq_applies = (int64_t)work[2];
   }
   cleanup();
 #undef GM_TRY

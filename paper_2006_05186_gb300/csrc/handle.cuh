@@ -127,6 +127,8 @@ struct cqm_handle {
   // couplings of its tail frequencies
   cqm::DArray<int64_t> tc2_first;
   cqm::DArray<unsigned char> tc2_img;
+  // first term of each far block from which the pairs take one product
+  cqm::DArray<int> tc2_t1;
   cqm::DArray<float2> tc2_tail;
   int n_sm = 1;  // multiprocessors of the handle's device (persistent grids)
   cqm::DArray<float> Uleaf_f, Etr_f;

@@ -931,7 +931,7 @@ int mot_solve(cqm_handle* h, const double* d_b, double* d_q, cqm_solve_info* inf
     info->t_forward_ms = h->mot_setup_ms;  // weights of the first call (0 after)
     info->t_gmres_ms = ms;
     info->t_inverse_ms = 0.0;
-    info->arnoldi_vectors = info->arnoldi_freq_steps = 0;
+    info->arnoldi_vectors = info->arnoldi_freq_steps = info->restart_freq_applies = 0;
   }
   h->mot_setup_ms = 0.0;
   return CQM_OK;

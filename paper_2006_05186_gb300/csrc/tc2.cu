@@ -18,7 +18,10 @@
 // alone with N = 64.  Operands are split as hi + lo in bf16 and the products
 // hi*hi + hi*lo + lo*hi are accumulated in fp32 (about 2^-17 per product; the
 // inner operator only steers GMRES, whose restarts recompute the residual in
-// float-float).
+// float-float).  The trailing terms of a block that stay below a set fraction
+// of the largest far term at every frequency (k_tc2_single_from) take the
+// hi*hi product alone, and their lo planes are not copied: a single bf16
+// product rounds such a term to ~2^-8 of itself, below the other errors.
 //
 // Layout and roles (one CTA per work item: a row cluster and a run of its far
 // blocks; 1 CTA per SM, which owns the 512 TMEM columns):
@@ -34,9 +37,9 @@
 //     groups 2048 bytes apart), so the two hi (lo) planes of a stage are one
 //     operand of 128 rows.
 //   warps 8-11 build A for each block from xhat_c (one lane per frequency);
-//   warp 12 (one thread) issues 24 MMAs into slot 0 and 24 into slot 1 per
-//     pair and frees each B stage, accumulator slot and A buffer with
-//     tcgen05.commit;
+//   warp 12 (one thread) issues 24 MMAs (8 for a single-product pair) into
+//     slot 0 and as many into slot 1 per pair and frees each B stage,
+//     accumulator slot and A buffer with tcgen05.commit;
 //   warps 0-7 (two per TMEM lane quadrant, 32 mu each) read each slot (one
 //     lane per frequency), multiply by d_t[l] and d_{t+1}[l] (loaded two pairs
 //     ahead) and keep the row's sum over all terms in registers, then write
@@ -113,6 +116,80 @@ __global__ void __launch_bounds__(256) k_tc2_images(int cap, int nt, const int* 
     const uint32_t o = bimg_off(mu, k);
     *(uint16_t*)(dst + o) = hi;
     *(uint16_t*)(dst + BPLANE + o) = lo;
+  }
+}
+
+// Sizes of the far rank terms for the choice of their product count:
+// n_t(l) = ||C_t||_F |d_t(l)| is the size of term t of block b at frequency l.
+// One CTA per block writes ||C_t||_F and raises ref[l] to the largest n_t(l)
+// of the block (ref holds the bits of non-negative floats, which order as
+// integers).
+__global__ void __launch_bounds__(256) k_tc2_term_sizes(int Ls, int cap, const int* __restrict__ rank,
+                                                        const double2* __restrict__ C,
+                                                        const double2* __restrict__ D, float* __restrict__ cn,
+                                                        unsigned int* __restrict__ ref) {
+  __shared__ float cs[64];
+  __shared__ double red[8];
+  const int b = blockIdx.x, rk = rank[b];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int t = 0; t < rk; ++t) {
+    const double2* Ct = C + ((size_t)b * cap + t) * TP * TP;
+    double a = 0.0;
+    for (int e = threadIdx.x; e < TP * TP; e += blockDim.x) a += Ct[e].x * Ct[e].x + Ct[e].y * Ct[e].y;
+    for (int o = 16; o; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (lane == 0) red[w] = a;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double tot = 0.0;
+      for (int v = 0; v < 8; ++v) tot += red[v];
+      cs[t] = (float)sqrt(tot);
+      cn[(size_t)b * cap + t] = cs[t];
+    }
+    __syncthreads();
+  }
+  for (int l = threadIdx.x; l < Ls; l += blockDim.x) {
+    float mx = 0.f;
+    for (int t = 0; t < rk; ++t) {
+      const double2 d = D[((size_t)b * cap + t) * Ls + l];
+      mx = fmaxf(mx, cs[t] * (float)hypot(d.x, d.y));
+    }
+    atomicMax(&ref[l], __float_as_uint(mx));
+  }
+}
+
+// First term of each far block from which its pairs take one product: the
+// block's trailing terms with n_t(l) <= ratio * ref[l] at every frequency l,
+// ref[l] the largest term of any far block at l (so the rounding of a single
+// bf16 product, ~2^-8 of such a term, is measured against the far field's
+// scale at that frequency).  t1[b] is the first such term, rounded up to the
+// next pair (even t); rank[b] when none (or ratio = 0).  One CTA per block;
+// *count gets the number of single-product terms.
+__global__ void __launch_bounds__(256) k_tc2_single_from(int Ls, int cap, double ratio,
+                                                         const int* __restrict__ rank,
+                                                         const double2* __restrict__ D,
+                                                         const float* __restrict__ cn,
+                                                         const unsigned int* __restrict__ ref,
+                                                         int* __restrict__ t1, int* __restrict__ count) {
+  __shared__ unsigned int rho[64];
+  const int b = blockIdx.x, rk = rank[b];
+  for (int t = threadIdx.x; t < rk; t += blockDim.x) rho[t] = 0u;
+  __syncthreads();
+  for (int l = threadIdx.x; l < Ls; l += blockDim.x) {
+    const float r = __uint_as_float(ref[l]);
+    if (!(r > 0.f)) continue;
+    for (int t = 0; t < rk; ++t) {
+      const double2 d = D[((size_t)b * cap + t) * Ls + l];
+      atomicMax(&rho[t], __float_as_uint(cn[(size_t)b * cap + t] * (float)hypot(d.x, d.y) / r));
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int f = rk;
+    if (ratio > 0.0)
+      while (f > 0 && (double)__uint_as_float(rho[f - 1]) <= ratio) --f;
+    f = min(rk, (f + 1) & ~1);
+    t1[b] = f;
+    if (rk > f) atomicAdd(count, rk - f);
   }
 }
 
@@ -250,7 +327,8 @@ __device__ __forceinline__ float2 term_d(const Seq& q, int j, const float2* __re
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_far_coupling_tc2(int Ls, int nch, int cap, int n_items, const int4* __restrict__ items,
                        const int* __restrict__ order, const int2* __restrict__ blocks, const int* __restrict__ rank,
-                       const int64_t* __restrict__ first, const unsigned char* __restrict__ img,
+                       const int64_t* __restrict__ first, const int* __restrict__ t1,
+                       const unsigned char* __restrict__ img,
                        const float2* __restrict__ Df, const float2* __restrict__ xhat,
                        float2* __restrict__ part, int* __restrict__ err, uint64_t lim, int probe) {
   using namespace umma;
@@ -302,6 +380,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     while (!q.done()) {
       const int s = (int)(ib % NSTAGE), ab = (int)(ia & 1u);
       const bool two = q.two(), last_pair = q.t + 2 >= rank[q.bi];
+      const int npr = q.t >= t1[q.bi] ? 1 : 3;  // products: hi*hi (+ hi*lo + lo*hi)
       const uint32_t id = two ? ID2 : ID1, idn = two ? ID2N : ID1N;
       const uint32_t a_hi = tmem + 128u * ab, a_lo = a_hi + 64u;
       const uint32_t bh = smem_u32(ring + (size_t)s * BSTAGE), bl = bh + 2u * BPLANE;
@@ -320,6 +399,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             // products hi*hi, hi*lo, lo*hi over K = 128 in 8 steps of 16
 #pragma unroll
             for (int pr = 0; pr < 3; ++pr) {
+              if (pr >= npr) break;
               const uint32_t aa = pr == 2 ? a_lo : a_hi;
               const uint32_t bb = pr == 1 ? bl : bh;
 #pragma unroll
@@ -358,15 +438,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         if (n_issued >= NSTAGE &&
             !mbar_wait(&b_empty[s], (n_issued / NSTAGE - 1) & 1u, &abort_sh, err, ERR_TIMEOUT, lim))
           break;
-        const bool two = q.two();
+        const bool two = q.two(), lo = q.t < t1[q.bi];  // single-product pairs read no lo planes
         unsigned char* st = ring + (size_t)s * BSTAGE;
         const unsigned char* src = img + (size_t)(first[q.bi] + q.t) * BIMG;  // [hi t | lo t | hi t+1 | lo t+1]
-        mbar_arrive_expect_tx(&b_full[s], two ? 4u * BPLANE : 2u * BPLANE);
+        mbar_arrive_expect_tx(&b_full[s], (two ? 2u : 1u) * (lo ? 2u : 1u) * BPLANE);
         bulk_g2s(st, src, BPLANE, &b_full[s]);
-        bulk_g2s(st + 2u * BPLANE, src + BPLANE, BPLANE, &b_full[s]);
+        if (lo) bulk_g2s(st + 2u * BPLANE, src + BPLANE, BPLANE, &b_full[s]);
         if (two) {
           bulk_g2s(st + BPLANE, src + 2u * BPLANE, BPLANE, &b_full[s]);
-          bulk_g2s(st + 3u * BPLANE, src + 3u * BPLANE, BPLANE, &b_full[s]);
+          if (lo) bulk_g2s(st + 3u * BPLANE, src + 3u * BPLANE, BPLANE, &b_full[s]);
         }
       }
     }
@@ -558,6 +638,24 @@ int build_tc2(cqm_handle* h) {
         h->rank_cap, nt, h->far_rank.p, h->tc2_first.p, h->farC.p, h->tc2_img.p);
   }
   CQM_CHECK_LAUNCH();
+  // t1 of every block, the number of single-product terms, ref[Ls] and the
+  // norms ||C_t||_F (n_far x cap), all 4-byte words
+  const size_t nw = (size_t)h->n_far + 1 + h->Ls + (size_t)h->n_far * h->rank_cap;
+  CQM_TRY(h->tc2_t1.allocate(h->alloc, nw));
+  int* cnt = h->tc2_t1.p + h->n_far;
+  unsigned int* ref = (unsigned int*)(cnt + 1);
+  float* cn = (float*)(ref + h->Ls);
+  CQM_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(int) * (1 + h->Ls), h->stream));
+  {
+    ProfScope ps_(h, CQM_K_EXPAND);
+    k_tc2_term_sizes<<<h->n_far, 256, 0, h->stream>>>(h->Ls, h->rank_cap, h->far_rank.p, h->farC.p, h->farD.p,
+                                                      cn, ref);
+    k_tc2_single_from<<<h->n_far, 256, 0, h->stream>>>(h->Ls, h->rank_cap, h->params.tc_single_ratio,
+                                                       h->far_rank.p, h->farD.p, cn, ref, h->tc2_t1.p, cnt);
+  }
+  CQM_CHECK_LAUNCH();
+  int n_single = 0;
+  CQM_CUDA_TRY(cudaMemcpyAsync(&n_single, cnt, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   int nch, l_tail, ntail;
   tc2_split(h->Ls, nch, l_tail, ntail);
   if (ntail > 0) {
@@ -568,6 +666,7 @@ int build_tc2(cqm_handle* h) {
     CQM_CHECK_LAUNCH();
   }
   CQM_CUDA_TRY(cudaStreamSynchronize(h->stream));  // `first` goes out of scope
+  h->info.tc_single_terms = n_single;
   return CQM_OK;
 }
 
@@ -580,8 +679,7 @@ int far_coupling_tc2(cqm_handle* h, int* l_tail_out) {
   {
     k_far_coupling_tc2<<<h->n_far_items, NTHREADS, SMEM, h->stream>>>(
         h->Ls, nch, h->rank_cap, h->n_far_items, h->far_items.p, h->far_order.p, h->far_rc.p, h->far_rank.p,
-        h->tc2_first.p,
-        h->tc2_img.p, h->farD_f.p, h->xhat_f.p, h->part_f.p, h->flag.p + 1, h->wait_limit_ns,
+        h->tc2_first.p, h->tc2_t1.p, h->tc2_img.p, h->farD_f.p, h->xhat_f.p, h->part_f.p, h->flag.p + 1, h->wait_limit_ns,
         h->wait_probe ? 1 : 0);
     h->wait_probe = false;  // one-shot
   }

@@ -78,9 +78,17 @@ def test_maca_and_arnoldi_models(bench):
     # basis read four times and w eight times per active frequency and step
     assert m["arnoldi"]["bound"] == "hbm"
     assert m["arnoldi"]["work"] == (4.0 * 20000 + 8.0 * 1200) * 5120 * 16.0 / 100
-    # without counts the models are left out
+    # the streams count the frequencies they read: active ones per Arnoldi
+    # step, unconverged ones per restart
+    assert m["near_apply"]["work"] == pytest.approx(8.0 * INFO["near_entries"] * 1200 / 100)
+    sinfo2 = dict(sinfo, restarts=4, restart_freq_applies=300)
+    m2 = bench.kernel_models(info, Ls=129, p=64, tensor_cores=1, sinfo=sinfo2, launches_per_step=lps)
+    assert m2["near_exact"]["work"] == pytest.approx(16.0 * INFO["near_entries"] * 75.0)
+    assert m2["far_exact"]["work"] == pytest.approx(16.0 * INFO["far_coupling"] * 75.0)
+    # without counts the models are left out, and the streams count every frequency
     m0 = bench.kernel_models(info, Ls=129, p=64, tensor_cores=1)
     assert "maca_slice" not in m0 and "arnoldi" not in m0
+    assert m0["near_apply"]["work"] == 8.0 * INFO["near_entries"] * 129
 
 
 def test_mot_models(bench):
@@ -95,3 +103,15 @@ def test_mot_models(bench):
     assert m["mot_history"]["bound"] == "alu" and m["mot_history"]["unit"] == "Tinst/s"
     assert m["mot_step"]["work"] == pytest.approx(8.0 * 1280 * 1280 * 65 / 65.0)
     assert abs(bench.cqm_R(N) ** (N + 1) - 1e-5) < 1e-12
+
+
+def test_tc2_traffic_scales_image_bytes(bench, monkeypatch):
+    # no capture of the current kernel: no traffic figure
+    monkeypatch.setattr(bench, "TC2_CAPTURE", None)
+    assert bench.tc2_traffic(dict(rank_sum_far=100, tc_single_terms=10)) is None
+    # images counted exactly (32 KB per three-product term, 16 KB per single
+    # one); the capture's other bytes scaled per rank term
+    cap = dict(dram=1000 * 32768.0 + 200 * 16384.0 + 1200 * 100.0, terms=1200, single=200)
+    monkeypatch.setattr(bench, "TC2_CAPTURE", cap)
+    t = bench.tc2_traffic(dict(rank_sum_far=3000, tc_single_terms=1000))
+    assert t == pytest.approx(2000 * 32768.0 + 1000 * 16384.0 + 3000 * 100.0)

@@ -212,6 +212,33 @@ def test_inner_operator_fp32_accuracy(lib, tensor_cores):
     assert np.max(err) < 1e-5, err
 
 
+def test_single_product_terms(lib):
+    """The trailing rank terms that take one bf16 product (tc_single_ratio,
+    default 1e-3 of the largest far term per frequency) leave the inner
+    operator as accurate as the three-product split throughout, frequency by
+    frequency; with the ratio 0 no term takes it."""
+    m = synth.icosphere(4)
+    N, dt = 40, 0.1
+    rng = np.random.default_rng(13)
+    x = None
+    err, single = {}, {}
+    for ratio in (0.0, None):
+        kw = {} if ratio is None else {"tc_single_ratio": ratio}
+        op = _op(m, dt, N, aca_eps=1e-9, **kw)
+        if x is None:
+            x = rng.standard_normal((op.Ls, m.nt)) + 1j * rng.standard_normal((op.Ls, m.nt))
+        y = op.apply(x)
+        yi = op.apply_inner(x)
+        single[ratio] = op.info()["tc_single_terms"]
+        total = op.info()["rank_sum_far"]
+        op.close()
+        err[ratio] = np.linalg.norm(yi - y, axis=1) / np.linalg.norm(y, axis=1)
+    print(f"single-product terms {single[None]} of {total}; max error {np.max(err[0.0]):.2e} (three "
+          f"products) {np.max(err[None]):.2e} (trailing terms single)")
+    assert single[0.0] == 0 and total // 10 < single[None] < total
+    assert np.max(err[None]) < 1e-5 and np.all(err[None] <= 2.0 * err[0.0] + 1e-7)
+
+
 def test_expanded_near_field_equals_factored(lib):
     """The near field and the far couplings expanded per frequency
     (sum_t C_t d_t, near in FP64, far in float-float) are the factored
