@@ -98,7 +98,7 @@ MACA_FF_INSTR_PER_EVAL = 160
 # single-product one) read once, plus d_t, xhat and the partial tiles, which
 # grow with the rank terms: the bench counts the workload's image bytes and
 # scales the rest per rank term.
-TC2_CAPTURE = None
+TC2_CAPTURE = dict(dram=380.197376e6 + 22.704896e6, terms=13284, single=4914)
 TC2_DRAM_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of k_far_coupling_tc2 (1280-triangle "
                    "sphere, N = 256): this workload's image bytes plus the capture's other bytes per rank term")
 
