@@ -143,15 +143,25 @@ __device__ __forceinline__ void chunk_dots(int i0, int i1, int j, size_t stride,
           acc[t].y += vk.x * wi.y - vk.y * wi.x;
         }
     }
+    // the KB sums at once: warp sums, then the eight warps' partials added in
+    // warp order by one thread per sum (one barrier pair per KB vectors)
+    __shared__ double2 red[8][KB];  // blockDim.x = 256
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int t = 0; t < KB; ++t) {
-      if (k0 + t <= j) {
-        const double re = block_sum(acc[t].x, sh);
-        const double im = block_sum(acc[t].y, sh);
-        if (threadIdx.x == 0) out[k0 + t] = make_double2(re, im);
-      }
+      acc[t].x = warp_sum(acc[t].x);
+      acc[t].y = warp_sum(acc[t].y);
+      if (lane == 0) red[warp][t] = acc[t];
     }
+    __syncthreads();
+    if (threadIdx.x < KB && k0 + (int)threadIdx.x <= j) {
+      double2 a = red[0][threadIdx.x];
+      for (int v2 = 1; v2 < 8; ++v2) a = cadd(a, red[v2][threadIdx.x]);
+      out[k0 + threadIdx.x] = a;
+    }
+    __syncthreads();
   }
+  (void)sh;
 }
 
 template <int KB>
