@@ -753,36 +753,79 @@ __global__ void __launch_bounds__(256) k_pair_geometry(const int2* __restrict__ 
   const int rb = begin[c2.x], nr = end[c2.x] - rb, cb = begin[c2.y], nc = end[c2.y] - cb;
   const int64_t base = off[b] / cap;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int e = w; e < nr * nc; e += nw) {
-    const int i = e / nc, j = e - i * nc;
-    if (c2.x == c2.y && i > j) continue;  // diagonal blocks cache their pairs i <= j
-    const int I = perm[rb + i], J = perm[cb + j];
-    const int64_t o = pt_off[base + e] + block_base[b];
-    __syncwarp();
-    if (lane == 0) pt_off[base + e] = o;
-    const int cse = pair_case(g, q, I, J);
+  // The warp's pairs e = w, w + nw, ... in groups of 32, lane kk owning pair
+  // g0 + kk nw: it converts the pair's offset, classifies it and forms r0
+  // (FP64, once per pair with the warp's lanes on 32 pairs).  Regular pairs
+  // (49 points) run four at a time on eight lanes each, which idles fewer
+  // lanes than 49 points on 32; the others one at a time on the whole warp.
+  // Every point is computed as before, so the cache is the same bit for bit.
+  auto emit = [&](int I, int J, int cse, int sub, int nsub, int64_t o, double r0) {
     if (!ff_mode) {
-      pair_points(g, q, I, J, cse, lane, 32, [&](int k, double r, double c) {
+      pair_points(g, q, I, J, cse, sub, nsub, [&](int k, double r, double c) {
         pt_r[o + k] = r;
         pt_c[o + k] = c;
       });
-      continue;
+      return;
     }
-    double r0 = 0.0;
-    if (cse == CASE_REGULAR || cse == CASE_NEAR) {
-      const double* ci = g.cen + 3 * I;
-      const double* cj = g.cen + 3 * J;
-      const double dx = ci[0] - cj[0], dy = ci[1] - cj[1], dz = ci[2] - cj[2];
-      r0 = fmax(0.0, sqrt(dx * dx + dy * dy + dz * dz) * (1.0 - 1e-12) - tri_radius(g, I) - tri_radius(g, J));
-    }
-    if (lane == 0) pt_r0[base + e] = r0;
     float2* pd = (float2*)pt_r;
     float2* pc = (float2*)pt_c;
-    pair_points(g, q, I, J, cse, lane, 32, [&](int k, double r, double c) {
+    pair_points(g, q, I, J, cse, sub, nsub, [&](int k, double r, double c) {
       const ff d = ff_of(fmax(r - r0, 0.0)), cf = ff_of(c);
       pd[o + k] = make_float2(d.h, d.l);
       pc[o + k] = make_float2(cf.h, cf.l);
     });
+  };
+  for (int g0 = w; g0 < nr * nc; g0 += 32 * nw) {
+    const int e = g0 + lane * nw;
+    bool have = e < nr * nc;
+    int i = 0, j = 0;
+    if (have) {
+      i = e / nc;
+      j = e - i * nc;
+      if (c2.x == c2.y && i > j) have = false;  // diagonal blocks cache their pairs i <= j
+    }
+    int I = 0, J = 0, cse = CASE_REGULAR;
+    int64_t o = 0;
+    double r0 = 0.0;
+    if (have) {
+      I = perm[rb + i];
+      J = perm[cb + j];
+      o = pt_off[base + e] + block_base[b];
+      pt_off[base + e] = o;
+      cse = pair_case(g, q, I, J);
+      if (ff_mode) {
+        if (cse == CASE_REGULAR || cse == CASE_NEAR) {
+          const double* ci = g.cen + 3 * I;
+          const double* cj = g.cen + 3 * J;
+          const double dx = ci[0] - cj[0], dy = ci[1] - cj[1], dz = ci[2] - cj[2];
+          r0 = fmax(0.0, sqrt(dx * dx + dy * dy + dz * dz) * (1.0 - 1e-12) - tri_radius(g, I) - tri_radius(g, J));
+        }
+        pt_r0[base + e] = r0;
+      }
+    }
+    const unsigned small = __ballot_sync(0xffffffffu, have && cse == CASE_REGULAR);
+    unsigned big = __ballot_sync(0xffffffffu, have && cse != CASE_REGULAR);
+    const int sg = lane >> 3, sl = lane & 7, nsmall = __popc(small);
+    for (int it = 0; 4 * it < nsmall; ++it) {
+      const int idx = 4 * it + sg;  // the regular pair of this eight-lane group
+      unsigned mm = small;
+      for (int k = 0; k < idx && mm; ++k) mm &= mm - 1u;
+      const int src = idx < nsmall ? __ffs(mm) - 1 : 0;
+      // every lane takes part in the shuffles; idle groups emit nothing
+      const int sI = __shfl_sync(0xffffffffu, I, src), sJ = __shfl_sync(0xffffffffu, J, src);
+      const int64_t so = __shfl_sync(0xffffffffu, o, src);
+      const double sr0 = __shfl_sync(0xffffffffu, r0, src);
+      if (idx < nsmall) emit(sI, sJ, CASE_REGULAR, sl, 8, so, sr0);
+    }
+    while (big) {
+      const int kk = __ffs(big) - 1;
+      big &= big - 1u;
+      const int sI = __shfl_sync(0xffffffffu, I, kk), sJ = __shfl_sync(0xffffffffu, J, kk);
+      const int scse = __shfl_sync(0xffffffffu, cse, kk);
+      const int64_t so = __shfl_sync(0xffffffffu, o, kk);
+      const double sr0 = __shfl_sync(0xffffffffu, r0, kk);
+      emit(sI, sJ, scse, lane, 32, so, sr0);
+    }
   }
 }
 
