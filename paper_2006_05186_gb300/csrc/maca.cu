@@ -133,7 +133,7 @@ __device__ __forceinline__ double2 kernel_value(double r, double2 s, const Quad&
 }
 
 // Slice G[:,:,k] of every active block into slot rank[b].
-__global__ void __launch_bounds__(256) k_maca_slice(MacaBlocks B, Geom g, Quad q,
+__global__ void __launch_bounds__(256, 4) k_maca_slice(MacaBlocks B, Geom g, Quad q,
                                                     const double2* __restrict__ s) {
   const int b = blockIdx.x;
   if (!B.active[b]) return;
@@ -395,7 +395,7 @@ __global__ void __launch_bounds__(256) k_maca_pivot(MacaBlocks B) {
 }
 
 // Fibre G[i_l, j_l, :] of every active block into D slot rank[b] (raw).
-__global__ void __launch_bounds__(256) k_maca_fibre(MacaBlocks B, Geom g, Quad q,
+__global__ void __launch_bounds__(256, 2) k_maca_fibre(MacaBlocks B, Geom g, Quad q,
                                                     const double2* __restrict__ s) {
   const int b = blockIdx.x;
   if (!B.active[b]) return;
