@@ -30,6 +30,10 @@ based on Hierarchical Matrices and Adaptive Cross Approximation") step by step:
 * ``dlayer``     -- the P0 Galerkin double layer (Sec. 2.2), its H^2 column
                     basis, and the direct formulation of the Dirichlet problem
                     (Sec. 7.2, eq. cqmdir) decoupled in frequency.
+* ``mixed``      -- P1 elements, the adjoint double layer and the hypersingular
+                    operator (Maue's form), and the mixed boundary-value problem
+                    (Sec. 2.3 eq. wavegalform, Sec. 3.2 eq. cqmgalapx) decoupled
+                    in frequency.
 
 Parity pins: every module is checked in ``tests/test_oracle_*.py`` against
 closed forms, invariants or brute force.  The conventions the paper leaves
