@@ -268,6 +268,23 @@ int cqm_bem_solve_dirichlet(cqm_handle* h, const double* g, double* q, int32_t m
  * cqm_bem_solve_dirichlet).  x, y: Ls x nt complex in `mem` memory. */
 int cqm_bem_apply_double_layer(cqm_handle* h, const double* x, double* y, int32_t mem);
 
+/* Galerkin matrices with piecewise linear functions for mixed boundary
+ * conditions (Sec. 2.3 eq. wavegalform; the matrices K_l, K'_l, D_l of
+ * Sec. 3.2 with the spaces of constants per triangle and of vertex hats),
+ * dense, at the Ls solved frequencies of the handle:
+ *   K1[l][m][v] = <phi0_m, K_l phi1_v>   (Ls x nt x nv), double layer, P1 trial;
+ *   Kp[l][v][i] = <phi1_v, K'_l phi0_i>  (Ls x nv x nt), adjoint double layer;
+ *   D[l][u][v]  = <phi1_u, D_l phi1_v>   (Ls x nv x nv), hypersingular operator in
+ *                 Maue's form int int G [curl phi_u . curl phi_v + s^2 (n_x . n_y) phi_u phi_v].
+ * Complex, interleaved (re, im) float64, row-major, in `mem` memory, owned by
+ * the caller; overwritten.  The single layer's quadrature rules (test
+ * triangle first, no symmetrisation), outward normals of counter-clockwise
+ * triangles, FP64.  Dense: O(nt^2 Ls) work and the sizes above (meant for
+ * small meshes and checks).  Either mode.
+ * Errors: CQM_EINVAL (NULL, mem), CQM_ENOMEM (host-memory outputs need device
+ * staging of the same size), CQM_ECUDA. */
+int cqm_bem_p1_matrices(cqm_handle* h, double* K1, double* Kp, double* D, int32_t mem);
+
 /* Galerkin data of the plane-wave pulse u(x,t) = exp(-((t - delay - d.x)/width)^2)
  * at t_n = n dt, n = 0..N, with Radon's 7-point rule per triangle.
  * dir: 3 doubles (host, normalised inside).  rhs: (N+1) x nt float64 in `mem`. */

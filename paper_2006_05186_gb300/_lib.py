@@ -33,7 +33,7 @@ EXPORTED = [
     "cqm_cluster_tree_noalloc", "cqm_bem_set_wait_limit",
     "cqm_bem_estimate_bytes", "cqm_server_create", "cqm_bem_submit", "cqm_bem_poll",
     "cqm_server_load", "cqm_server_destroy", "cqm_bem_solve_mot", "cqm_bem_mot_weight",
-    "cqm_bem_solve_dirichlet", "cqm_bem_apply_double_layer",
+    "cqm_bem_solve_dirichlet", "cqm_bem_apply_double_layer", "cqm_bem_p1_matrices",
 ]
 K_COUNT = 32
 
@@ -154,6 +154,7 @@ def load(build_if_missing: bool = False):
         "cqm_bem_mot_weight": (C.c_int, [vp, i32, vp, i32]),
         "cqm_bem_solve_dirichlet": (C.c_int, [vp, vp, vp, i32, C.POINTER(cqm_solve_info)]),
         "cqm_bem_apply_double_layer": (C.c_int, [vp, vp, vp, i32]),
+        "cqm_bem_p1_matrices": (C.c_int, [vp, vp, vp, vp, i32]),
         "cqm_bem_forward_transform": (C.c_int, [vp, vp, vp, i32]),
         "cqm_bem_inverse_transform": (C.c_int, [vp, vp, vp, i32]),
         "cqm_bem_profile": (C.c_int, [vp, i32]),
@@ -448,6 +449,24 @@ class CqmBem:
         po, _ = _ptr(out)
         _check(self._lib.cqm_bem_apply_double_layer(self._h, px, po, mem), "apply_double_layer")
         return out
+
+    def p1_matrices(self, device: bool = False):
+        """Dense K1 (Ls, nt, nv), Kp (Ls, nv, nt) and D (Ls, nv, nv) with P1
+        functions (mixed boundary conditions), complex; torch CUDA tensors
+        when device, else numpy arrays."""
+        nv = len(self._xyz)
+        shapes = [(self.Ls, self.M, nv), (self.Ls, nv, self.M), (self.Ls, nv, nv)]
+        if device:
+            import torch
+            outs = [torch.empty(sh, dtype=torch.complex128, device=self.device) for sh in shapes]
+            ptrs = [o.data_ptr() for o in outs]
+            mem = 1
+        else:
+            outs = [np.zeros(sh, dtype=np.complex128) for sh in shapes]
+            ptrs = [o.ctypes.data for o in outs]
+            mem = 0
+        _check(self._lib.cqm_bem_p1_matrices(self._h, *ptrs, mem), "p1_matrices")
+        return tuple(outs)
 
     def mot_weight(self, n):
         """Dense CQM weight Vhat_n of the compressed operator (M x M, host)."""

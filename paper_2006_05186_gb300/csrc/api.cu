@@ -485,6 +485,27 @@ int cqm_bem_apply_double_layer(cqm_handle* h, const double* x, double* y, int32_
   return CQM_OK;
 }
 
+int cqm_bem_p1_matrices(cqm_handle* h, double* K1, double* Kp, double* D, int32_t mem) {
+  if (!h || !K1 || !Kp || !D || (mem != CQM_MEM_HOST && mem != CQM_MEM_DEVICE)) return CQM_EINVAL;
+  set_last_error("");
+  const size_t nk = (size_t)h->Ls * h->M * h->nv, nd = (size_t)h->Ls * h->nv * h->nv;
+  Scratch S(&h->alloc);
+  double2 *dK1 = (double2*)K1, *dKp = (double2*)Kp, *dD = (double2*)D;
+  if (mem == CQM_MEM_HOST) {
+    CQM_TRY(S.get(&dK1, nk));
+    CQM_TRY(S.get(&dKp, nk));
+    CQM_TRY(S.get(&dD, nd));
+  }
+  CQM_TRY(p1_matrices(h, dK1, dKp, dD));
+  if (mem == CQM_MEM_HOST) {
+    CQM_CUDA_TRY(cudaMemcpyAsync(K1, dK1, nk * sizeof(double2), cudaMemcpyDeviceToHost, h->stream));
+    CQM_CUDA_TRY(cudaMemcpyAsync(Kp, dKp, nk * sizeof(double2), cudaMemcpyDeviceToHost, h->stream));
+    CQM_CUDA_TRY(cudaMemcpyAsync(D, dD, nd * sizeof(double2), cudaMemcpyDeviceToHost, h->stream));
+  }
+  CQM_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  return CQM_OK;
+}
+
 int cqm_bem_solve_dirichlet(cqm_handle* h, const double* g, double* q, int32_t mem, cqm_solve_info* info) {
   if (!h || !g || !q || (mem != CQM_MEM_HOST && mem != CQM_MEM_DEVICE)) return CQM_EINVAL;
   set_last_error("");

@@ -220,6 +220,8 @@ int far_coupling_ff(cqm_handle* h);
 int factors_to_ff(cqm_handle* h);  // after every FP64 reader of the C factors at setup
 
 // near_dense.cu (expanded near field)
+// dense Galerkin matrices with P1 functions (mixed boundary conditions), device
+int p1_matrices(cqm_handle* h, double2* K1, double2* Kp, double2* D);
 int build_near_expanded(cqm_handle* h);  // after the near MACA, before factors_to_ff
 int near_apply_expanded(cqm_handle* h, const double2* x, double2* y, bool fp64);
 // ff.cu (expanded far couplings of the FP64-accurate apply)
