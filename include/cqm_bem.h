@@ -285,6 +285,26 @@ int cqm_bem_apply_double_layer(cqm_handle* h, const double* x, double* y, int32_
  * staging of the same size), CQM_ECUDA. */
 int cqm_bem_p1_matrices(cqm_handle* h, double* K1, double* Kp, double* D, int32_t mem);
 
+/* Mixed boundary conditions (Sec. 2.3 eq. wavegalform; Sec. 3.2 eq.
+ * cqmgalapx, decoupled in frequency like cqm_bem_solve): Dirichlet data on the
+ * triangles with dmask[m] != 0 (Gamma_D), Neumann data on the others
+ * (Gamma_N).  dmask: nt int32 (host).  gD: (N+1) x nv float64, vertex values
+ * of the Dirichlet data (only the vertices of Gamma_D's triangles are used);
+ * gN: (N+1) x nt float64, P0 coefficients of the Neumann data (only Gamma_N's
+ * triangles are used).  Results: q (N+1) x nt, the Neumann data on Gamma_D
+ * (0 on Gamma_N); u (N+1) x nv, the Dirichlet data in the hats of the
+ * vertices that touch no Gamma_D triangle (0 at the others).  All in `mem`
+ * memory.  Per solved frequency the dense system
+ *   [ V_DD -K1_DN ; Kp_ND D_NN ] [qhat ; uhat] =
+ *   [ (-1/2 I + K1) gDhat - V gNhat ; (-1/2 I' - Kp) gNhat - D gDhat ]
+ * (the matrices of cqm_bem_p1_matrices, I the P0 x P1 mass matrix) by
+ * Gaussian elimination with partial pivoting on the GPU, then the inverse
+ * transform.  CQM_MODE_DENSE only (the dense V_l).
+ * Errors: CQM_EINVAL (NULL, mem, not the dense mode, no unknowns), CQM_ENOMEM,
+ * CQM_ECUDA. */
+int cqm_bem_solve_mixed(cqm_handle* h, const int32_t* dmask, const double* gD, const double* gN, double* q,
+                        double* u, int32_t mem);
+
 /* Galerkin data of the plane-wave pulse u(x,t) = exp(-((t - delay - d.x)/width)^2)
  * at t_n = n dt, n = 0..N, with Radon's 7-point rule per triangle.
  * dir: 3 doubles (host, normalised inside).  rhs: (N+1) x nt float64 in `mem`. */

@@ -34,6 +34,7 @@ EXPORTED = [
     "cqm_bem_estimate_bytes", "cqm_server_create", "cqm_bem_submit", "cqm_bem_poll",
     "cqm_server_load", "cqm_server_destroy", "cqm_bem_solve_mot", "cqm_bem_mot_weight",
     "cqm_bem_solve_dirichlet", "cqm_bem_apply_double_layer", "cqm_bem_p1_matrices",
+    "cqm_bem_solve_mixed",
 ]
 K_COUNT = 32
 
@@ -155,6 +156,7 @@ def load(build_if_missing: bool = False):
         "cqm_bem_solve_dirichlet": (C.c_int, [vp, vp, vp, i32, C.POINTER(cqm_solve_info)]),
         "cqm_bem_apply_double_layer": (C.c_int, [vp, vp, vp, i32]),
         "cqm_bem_p1_matrices": (C.c_int, [vp, vp, vp, vp, i32]),
+        "cqm_bem_solve_mixed": (C.c_int, [vp, vp, vp, vp, vp, vp, i32]),
         "cqm_bem_forward_transform": (C.c_int, [vp, vp, vp, i32]),
         "cqm_bem_inverse_transform": (C.c_int, [vp, vp, vp, i32]),
         "cqm_bem_profile": (C.c_int, [vp, i32]),
@@ -467,6 +469,21 @@ class CqmBem:
             mem = 0
         _check(self._lib.cqm_bem_p1_matrices(self._h, *ptrs, mem), "p1_matrices")
         return tuple(outs)
+
+    def solve_mixed(self, dmask, gD, gN):
+        """Mixed boundary conditions (dense mode): q (N+1, nt), the Neumann data
+        on the triangles with dmask set, and u (N+1, nv), the Dirichlet data
+        at the vertices that touch none of them (host arrays)."""
+        nv = len(self._xyz)
+        dm = np.ascontiguousarray(np.asarray(dmask) != 0, dtype=np.int32)
+        gd = np.ascontiguousarray(gD, dtype=np.float64)
+        gn = np.ascontiguousarray(gN, dtype=np.float64)
+        assert dm.shape == (self.M,) and gd.shape == (self.L, nv) and gn.shape == (self.L, self.M)
+        q = np.zeros((self.L, self.M))
+        u = np.zeros((self.L, nv))
+        _check(self._lib.cqm_bem_solve_mixed(self._h, dm.ctypes.data, gd.ctypes.data, gn.ctypes.data,
+                                             q.ctypes.data, u.ctypes.data, 0), "solve_mixed")
+        return q, u
 
     def mot_weight(self, n):
         """Dense CQM weight Vhat_n of the compressed operator (M x M, host)."""

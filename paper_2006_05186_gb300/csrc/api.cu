@@ -506,6 +506,35 @@ int cqm_bem_p1_matrices(cqm_handle* h, double* K1, double* Kp, double* D, int32_
   return CQM_OK;
 }
 
+int cqm_bem_solve_mixed(cqm_handle* h, const int32_t* dmask, const double* gD, const double* gN, double* q,
+                        double* u, int32_t mem) {
+  if (!h || !dmask || !gD || !gN || !q || !u || (mem != CQM_MEM_HOST && mem != CQM_MEM_DEVICE))
+    return CQM_EINVAL;
+  set_last_error("");
+  const size_t nD = (size_t)h->L * h->nv, nN = (size_t)h->L * h->M;
+  Scratch S(&h->alloc);
+  const double *dgD = gD, *dgN = gN;
+  double *dq = q, *du = u;
+  if (mem == CQM_MEM_HOST) {
+    double *t1, *t2;
+    CQM_TRY(S.get(&t1, nD));
+    CQM_TRY(S.get(&t2, nN));
+    CQM_CUDA_TRY(cudaMemcpyAsync(t1, gD, nD * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    CQM_CUDA_TRY(cudaMemcpyAsync(t2, gN, nN * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    dgD = t1;
+    dgN = t2;
+    CQM_TRY(S.get(&dq, nN));
+    CQM_TRY(S.get(&du, nD));
+  }
+  CQM_TRY(mixed_solve(h, dmask, dgD, dgN, dq, du));
+  if (mem == CQM_MEM_HOST) {
+    CQM_CUDA_TRY(cudaMemcpyAsync(q, dq, nN * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CQM_CUDA_TRY(cudaMemcpyAsync(u, du, nD * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  }
+  CQM_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  return CQM_OK;
+}
+
 int cqm_bem_solve_dirichlet(cqm_handle* h, const double* g, double* q, int32_t mem, cqm_solve_info* info) {
   if (!h || !g || !q || (mem != CQM_MEM_HOST && mem != CQM_MEM_DEVICE)) return CQM_EINVAL;
   set_last_error("");

@@ -177,6 +177,10 @@ int rhs_plane_wave(cqm_handle* h, const double dir[3], double width, double dela
 // transform.cu
 int forward_transform(cqm_handle* h, const double* d_b, double2* d_ghat);
 int inverse_transform(cqm_handle* h, const double2* d_qhat, double* d_q);
+int forward_transform_cols(cqm_handle* h, int ncol, const double* d_b, double2* d_ghat);
+int inverse_transform_cols(cqm_handle* h, int ncol, const double2* d_qhat, double* d_q);
+// mixed boundary conditions, dense mode: q (N+1 x nt) on Gamma_D, u (N+1 x nv) on Gamma_N's space
+int mixed_solve(cqm_handle* h, const int* dmask, const double* gD, const double* gN, double* q, double* u);
 
 // entries.cu
 int build_quad_tables(cqm_handle* h);

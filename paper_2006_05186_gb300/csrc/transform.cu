@@ -100,30 +100,39 @@ static int opt_in(K kernel, size_t sh) {
   return CQM_OK;
 }
 
-int forward_transform(cqm_handle* h, const double* d_b, double2* d_ghat) {
+// The transforms of ncol columns (nt for the P0 data, nv for vertex data).
+int forward_transform_cols(cqm_handle* h, int ncol, const double* d_b, double2* d_ghat) {
   constexpr int FT = 8;
-  dim3 grid(grid_for(h->M, 128), grid_for(h->Ls, FT));
+  dim3 grid(grid_for(ncol, 128), grid_for(h->Ls, FT));
   const size_t sh = table_bytes(h->L);
   CQM_TRY(opt_in(k_forward<FT>, sh));
   {
     ProfScope ps_(h, CQM_K_FORWARD_DFT);
-    k_forward<FT><<<grid, 128, sh, h->stream>>>(h->M, h->L, h->Ls, h->R, d_b, d_ghat);
+    k_forward<FT><<<grid, 128, sh, h->stream>>>(ncol, h->L, h->Ls, h->R, d_b, d_ghat);
   }
   CQM_CHECK_LAUNCH();
   return CQM_OK;
 }
 
-int inverse_transform(cqm_handle* h, const double2* d_qhat, double* d_q) {
+int inverse_transform_cols(cqm_handle* h, int ncol, const double2* d_qhat, double* d_q) {
   constexpr int NT = 8;
-  dim3 grid(grid_for(h->M, 128), grid_for(h->L, NT));
+  dim3 grid(grid_for(ncol, 128), grid_for(h->L, NT));
   const size_t sh = table_bytes(h->L);
   CQM_TRY(opt_in(k_inverse<NT>, sh));
   {
     ProfScope ps_(h, CQM_K_INVERSE_DFT);
-    k_inverse<NT><<<grid, 128, sh, h->stream>>>(h->M, h->L, h->Ls, h->R, d_qhat, d_q);
+    k_inverse<NT><<<grid, 128, sh, h->stream>>>(ncol, h->L, h->Ls, h->R, d_qhat, d_q);
   }
   CQM_CHECK_LAUNCH();
   return CQM_OK;
+}
+
+int forward_transform(cqm_handle* h, const double* d_b, double2* d_ghat) {
+  return forward_transform_cols(h, h->M, d_b, d_ghat);
+}
+
+int inverse_transform(cqm_handle* h, const double2* d_qhat, double* d_q) {
+  return inverse_transform_cols(h, h->M, d_qhat, d_q);
 }
 
 }  // namespace cqm

@@ -36,3 +36,29 @@ def test_p1_matrices_equal_oracle(level, N, dt):
         print(f"level {level}: {name} vs oracle {err:.2e}")
         assert err < 1e-10, (name, err)
         assert _rel(b, a) < 1e-13, name    # the device-memory outputs are the same sums
+
+
+def test_mixed_solve_equals_oracle():
+    """The mixed solve on the GPU (dense mode) equals the oracle's on the
+    spherical wave of the oracle's convergence test: Dirichlet data on the
+    upper, Neumann data on the lower half of the 80-triangle sphere."""
+    from oracle import dlayer, galerkin
+    from paper_2006_05186_gb300 import CqmBem, build
+    build.build()
+    m = synth.icosphere(1)
+    N, dt = 24, 0.2
+    x0 = np.array([0.1, -0.2, 0.15])
+    _, _, cen, _ = galerkin.element_geometry(m.xyz, m.tri)
+    dmask = cen[:, 2] > 0.0
+    _, qn = dlayer.point_source(m.xyz, m.tri, N, dt, x0, 0.6, 2.5)
+    uv = mixed.point_source_vertices(m.xyz, N, dt, x0, 0.6, 2.5)
+    op = CqmBem(m.xyz, m.tri, dt, N, 2, mode="dense")
+    q, u = op.solve_mixed(dmask, uv, qn)
+    op.close()
+    q_ref, u_ref, info = mixed.solve_mixed(m.xyz, m.tri, N, dt, 2, dmask, uv, qn)
+    ED, VN = info["ED"], info["VN"]
+    eq, eu = _rel(q[:, ED], q_ref), _rel(u[:, VN], u_ref)
+    print(f"mixed solve vs oracle: q {eq:.2e}, u {eu:.2e}")
+    assert eq < 1e-8 and eu < 1e-8, (eq, eu)
+    # outside their parts the results are zero
+    assert np.all(q[:, ~dmask] == 0.0) and np.count_nonzero(u) <= u.shape[0] * len(VN)
