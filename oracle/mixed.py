@@ -296,3 +296,64 @@ def point_source_vertices(xyz, N: int, dt: float, x0, width: float, delay: float
     t = dt * np.arange(N + 1)
     z = (t[:, None] - rho[None] - delay) / width
     return np.exp(-z * z) / (FOUR_PI * rho[None])
+
+
+def solve_mixed_mot(xyz, tri, N: int, dt: float, bdf: int, dmask, gD, gN, R: float | None = None,
+                    qp: QuadParams = QuadParams(), mats_all=None):
+    """The same mixed problem by the paper's own time stepping (Sec. 3.2, eqs.
+    cqmgalapx and cqmrhs): the CQM weights Vhat_n, K1hat_n, Kphat_n, Dhat_n of
+    the matrices at all L frequencies (eq. dft), and per step n the system
+      [ Vhat_0,DD  -K1hat_0,DN ] [q_n]   [ -1/2 I_D: gD_n ]
+      [ Kphat_0,ND  Dhat_0,NN  ] [u_n] = [ -1/2 I'_N: gN_n ]
+          + sum_{k<=n} [ -Vhat_{n-k} gN_k + K1hat_{n-k} gD_k ; -Kphat_{n-k} gN_k - Dhat_{n-k} gD_k ]
+          - sum_{k<n}  [ Vhat_{n-k} q_k - K1hat_{n-k} u_k ; Kphat_{n-k} q_k + Dhat_{n-k} u_k ],
+    rows restricted to Gamma_D's triangles and Gamma_N's vertices, with one
+    LU of the step matrix (a library primitive; the paper's Schur complement
+    of Vhat_0 is the same elimination in two stages).  mats_all: optional
+    (V, K1, Kp, D) at all L frequencies.  Returns (q, u, info) like
+    solve_mixed; exactly causal, it differs from the decoupled solve by the
+    wrap-around terms weighted by R^L."""
+    from scipy.linalg import lu_factor, lu_solve
+    from .mot import convolution_weights
+    if R is None:
+        R = cqm.default_R(N)
+    L = N + 1
+    s = cqm.frequencies(N, dt, bdf, R)
+    tri = np.asarray(tri)
+    M, nv = len(tri), len(xyz)
+    ED, EN, VN = mixed_spaces(tri, nv, dmask)
+    if mats_all is None:
+        V = dense_matrices(xyz, tri, s, qp)
+        K1, Kp, D = p1_matrices(xyz, tri, s, qp)
+    else:
+        V, K1, Kp, D = mats_all
+    Vh, i1 = convolution_weights(V, R)
+    K1h, i2 = convolution_weights(K1, R)
+    Kph, i3 = convolution_weights(Kp, R)
+    Dh, i4 = convolution_weights(D, R)
+    Im = mass_p0p1(xyz, tri)
+    gD = np.array(gD, dtype=np.float64)
+    gN = np.array(gN, dtype=np.float64)
+    keepD = np.zeros(nv, dtype=bool)
+    keepD[tri[ED].ravel()] = True
+    gD[:, ~keepD] = 0.0
+    gN[:, ED] = 0.0
+    nD, nN = len(ED), len(VN)
+    A0 = np.block([[Vh[0][np.ix_(ED, ED)], -K1h[0][np.ix_(ED, VN)]],
+                   [Kph[0][np.ix_(VN, ED)], Dh[0][np.ix_(VN, VN)]]])
+    lu = lu_factor(A0)
+    q = np.zeros((L, nD))
+    u = np.zeros((L, nN))
+    for n in range(L):
+        fD = -0.5 * Im[ED] @ gD[n]
+        fN = -0.5 * Im.T[VN] @ gN[n]
+        for k in range(n + 1):
+            fD += -Vh[n - k][ED] @ gN[k] + K1h[n - k][ED] @ gD[k]
+            fN += -Kph[n - k][VN] @ gN[k] - Dh[n - k][VN] @ gD[k]
+        for k in range(n):
+            fD -= Vh[n - k][np.ix_(ED, ED)] @ q[k] - K1h[n - k][np.ix_(ED, VN)] @ u[k]
+            fN -= Kph[n - k][np.ix_(VN, ED)] @ q[k] + Dh[n - k][np.ix_(VN, VN)] @ u[k]
+        x = lu_solve(lu, np.concatenate([fD, fN]))
+        q[n] = x[:nD]
+        u[n] = x[nD:]
+    return q, u, {"imag_rel": max(i1, i2, i3, i4), "ED": ED, "EN": EN, "VN": VN}

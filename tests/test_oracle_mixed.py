@@ -16,7 +16,9 @@ against what the mathematics fixes:
 * a spherical wave from a source inside the sphere with Dirichlet data on the
   upper and Neumann data on the lower half: the unknown Neumann and Dirichlet
   data converge to the exact traces, and flipping the sign of K' or of D (a
-  plausible mistake) does not.
+  plausible mistake) does not;
+* the paper's own time stepping of the mixed system (eqs. cqmgalapx and
+  cqmrhs) is exactly causal and agrees with the decoupled solve to R^L.
 """
 import numpy as np
 import pytest
@@ -123,3 +125,30 @@ def test_mixed_spherical_wave_converges():
     assert q1 / q2 > 3.0 and u1 / u2 > 3.0, (e1, e2)
     # a sign error in K' or in D leaves the solution far from the traces
     assert e1["Kp"][1] > 1.0 and e1["D"][1] > 1.0, e1
+
+
+def test_marching_on_in_time_agrees_with_the_decoupled_solve():
+    """The paper's own time stepping of the mixed system (eqs. cqmgalapx and
+    cqmrhs, the weights of eq. dft) is exactly causal and agrees with the
+    decoupled frequency-domain solve to the order R^L of the wrap-around."""
+    m = synth.icosphere(1)
+    N, dt = 24, 0.2
+    _, _, cen, _ = galerkin.element_geometry(m.xyz, m.tri)
+    dmask = cen[:, 2] > 0.0
+    _, qn = dlayer.point_source(m.xyz, m.tri, N, dt, X0, 0.6, 2.5)
+    uv = mixed.point_source_vertices(m.xyz, N, dt, X0, 0.6, 2.5)
+    s = cqm.frequencies(N, dt, 2)
+    mats = (galerkin.dense_matrices(m.xyz, m.tri, s),) + mixed.p1_matrices(m.xyz, m.tri, s)
+    Ls = cqm.n_solved(N + 1)
+    qd, ud, _ = mixed.solve_mixed(m.xyz, m.tri, N, dt, 2, dmask, uv, qn, mats=[a[:Ls] for a in mats])
+    qm, um, info = mixed.solve_mixed_mot(m.xyz, m.tri, N, dt, 2, dmask, uv, qn, mats_all=mats)
+    RL = cqm.default_R(N) ** (N + 1)
+    assert info["imag_rel"] < 1e-9
+    assert _rel(qm, qd) < RL and _rel(um, ud) < RL, (_rel(qm, qd), _rel(um, ud))
+    # causality: data from step 10 on do not change the first ten steps
+    qn2, uv2 = qn.copy(), uv.copy()
+    qn2[10:] *= 2.0
+    uv2[10:] += 1.0
+    qm2, um2, _ = mixed.solve_mixed_mot(m.xyz, m.tri, N, dt, 2, dmask, uv2, qn2, mats_all=mats)
+    assert np.array_equal(qm2[:10], qm[:10]) and np.array_equal(um2[:10], um[:10])
+    assert _rel(qm2[10:], qm[10:]) > 0.1
