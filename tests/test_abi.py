@@ -79,7 +79,8 @@ def test_setup_rejects_bad_arguments_on_host(lib):
     tri = np.array([[0, 1, 2]], np.int32)
     mesh = _lib.cqm_mesh(3, xyz.ctypes.data, 1, tri.ctypes.data)
     for field, value in [("rank_cap", 65), ("rank_cap", 0), ("cheb_m", 5), ("cheb_m", 0),
-                         ("n_min", 33), ("inner_rtol", 1.0), ("eta", 0.0), ("g_sing", 13)]:
+                         ("n_min", 33), ("inner_rtol", 1.0), ("eta", 0.0), ("g_sing", 13),
+                         ("tc_single_ratio", -1.0)]:
         prm = _lib.cqm_params()
         assert lib.cqm_params_default(C.byref(prm)) == 0
         setattr(prm, field, value)
@@ -88,3 +89,9 @@ def test_setup_rejects_bad_arguments_on_host(lib):
         assert h.value is None
     assert lib.cqm_bem_destroy(None) == 0
     assert len(lib.cqm_bem_last_error()) >= 0
+    # the P1 and mixed-boundary calls check their arguments before any device work
+    buf = np.zeros(4)
+    p = buf.ctypes.data
+    assert lib.cqm_bem_p1_matrices(None, p, p, p, 0) == _lib.CQM_EINVAL
+    dm = np.zeros(1, np.int32)
+    assert lib.cqm_bem_solve_mixed(None, dm.ctypes.data, p, p, p, p, 0) == _lib.CQM_EINVAL
