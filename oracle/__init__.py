@@ -31,9 +31,9 @@ based on Hierarchical Matrices and Adaptive Cross Approximation") step by step:
                     basis, and the direct formulation of the Dirichlet problem
                     (Sec. 7.2, eq. cqmdir) decoupled in frequency.
 * ``mixed``      -- P1 elements, the adjoint double layer and the hypersingular
-                    operator (Maue's form), and the mixed boundary-value problem
-                    (Sec. 2.3 eq. wavegalform, Sec. 3.2 eq. cqmgalapx) decoupled
-                    in frequency.
+                    operator (Maue's form), dense and in H^2 form, and the mixed
+                    boundary-value problem (Sec. 2.3 eq. wavegalform, Sec. 3.2 eq.
+                    cqmgalapx) decoupled in frequency and by marching on in time.
 
 Parity pins: every module is checked in ``tests/test_oracle_*.py`` against
 closed forms, invariants or brute force.  The conventions the paper leaves

@@ -124,20 +124,21 @@ def curls(xyz, tri):
     return out
 
 
-def p1_matrices(xyz, tri, s, qp: QuadParams = QuadParams()):
-    """Dense K1 (len(s), M, nv), Kp (len(s), nv, M) and D (len(s), nv, nv)."""
+def p1_local(xyz, tri, I, J, s, qp: QuadParams = QuadParams()):
+    """Local values of the triangle pairs (I[k] test, J[k] trial) at every
+    frequency in s: K1 (ns, pairs, 3) over the trial triangle's vertices, Kp
+    (ns, pairs, 3) over the test triangle's vertices, D (ns, pairs, 3, 3)."""
     xyz = np.asarray(xyz, dtype=np.float64)
     tri = np.asarray(tri)
+    I = np.asarray(I, dtype=np.int64)
+    J = np.asarray(J, dtype=np.int64)
     s = np.atleast_1d(np.asarray(s, dtype=np.complex128))
-    M, nv, ns = len(tri), len(xyz), len(s)
+    ns = len(s)
     nrm = normals(xyz, tri)
     cu = curls(xyz, tri)
-    I, J = np.meshgrid(np.arange(M), np.arange(M), indexing="ij")
-    I = I.ravel()
-    J = J.ravel()
-    K1 = np.zeros((ns, M, nv), dtype=np.complex128)
-    Kp = np.zeros((ns, nv, M), dtype=np.complex128)
-    D = np.zeros((ns, nv, nv), dtype=np.complex128)
+    K1l = np.zeros((ns, len(I), 3), dtype=np.complex128)
+    Kpl = np.zeros((ns, len(I), 3), dtype=np.complex128)
+    Dl = np.zeros((ns, len(I), 3, 3), dtype=np.complex128)
     for c, kk, X, Y, lx, ly, w in _pair_points(xyz, tri, I, J, qp):
         i, j = I[kk], J[kk]
         d = X - Y                                                  # x - y
@@ -146,25 +147,47 @@ def p1_matrices(xyz, tri, s, qp: QuadParams = QuadParams()):
         dnx = -np.einsum("pqk,pk->pq", d, nrm[i])                  # (y - x) . n_x
         # contractions over the points as batched products (pairs first)
         ht = np.moveaxis(h, 0, 1)                                  # (pairs, ns, points)
-        kl = np.moveaxis(np.matmul(ht * (w * dny)[:, None, :], ly), 1, 0)   # K1 local: (ns, pairs, 3)
-        kpl = np.moveaxis(np.matmul(ht * (w * dnx)[:, None, :], lx), 1, 0)  # Kp local
+        kl = np.moveaxis(np.matmul(ht * (w * dny)[:, None, :], ly), 1, 0)   # (ns, pairs, 3)
+        kpl = np.moveaxis(np.matmul(ht * (w * dnx)[:, None, :], lx), 1, 0)
         if c == 4:  # identical flat triangles: (x - y) . n = 0
             kl[:] = 0.0
             kpl[:] = 0.0
         gw = np.moveaxis(g, 0, 1) * w[:, None, :]                  # (pairs, ns, points)
         g0 = np.moveaxis(gw.sum(axis=2), 1, 0)                     # int int G: (ns, pairs)
         lxy = (lx[:, :, :, None] * ly[:, :, None, :]).reshape(lx.shape[0], lx.shape[1], 9)
-        gl = np.moveaxis(np.matmul(gw, lxy), 1, 0).reshape(len(s), lx.shape[0], 3, 3)  # int int G lx_a ly_b
+        gl = np.moveaxis(np.matmul(gw, lxy), 1, 0).reshape(ns, lx.shape[0], 3, 3)  # int int G lx_a ly_b
         cc = np.einsum("pak,pbk->pab", cu[i], cu[j])               # curl . curl
         nn = np.einsum("pk,pk->p", nrm[i], nrm[j])
-        dl = g0[:, :, None, None] * cc[None] + (s ** 2)[:, None, None, None] * nn[None, :, None, None] * gl
-        for a in range(3):
-            va = tri[j, a]
-            np.add.at(K1, (slice(None), i, va), kl[:, :, a])
-            np.add.at(Kp, (slice(None), tri[i, a], j), kpl[:, :, a])
-            for b in range(3):
-                np.add.at(D, (slice(None), tri[i, a], tri[j, b]), dl[:, :, a, b])
-    return K1, Kp, D
+        K1l[:, kk] = kl
+        Kpl[:, kk] = kpl
+        Dl[:, kk] = g0[:, :, None, None] * cc[None] + (s ** 2)[:, None, None, None] * nn[None, :, None, None] * gl
+    return K1l, Kpl, Dl
+
+
+def _scatter(tri, nv, I, J, K1l, Kpl, Dl, out):
+    """Adds the local values of the pairs (I, J) into out = (K1, Kp, D)."""
+    tri = np.asarray(tri)
+    K1, Kp, D = out
+    for a in range(3):
+        np.add.at(K1, (slice(None), I, tri[J, a]), K1l[:, :, a])
+        np.add.at(Kp, (slice(None), tri[I, a], J), Kpl[:, :, a])
+        for b in range(3):
+            np.add.at(D, (slice(None), tri[I, a], tri[J, b]), Dl[:, :, a, b])
+
+
+def p1_matrices(xyz, tri, s, qp: QuadParams = QuadParams()):
+    """Dense K1 (len(s), M, nv), Kp (len(s), nv, M) and D (len(s), nv, nv)."""
+    s = np.atleast_1d(np.asarray(s, dtype=np.complex128))
+    M, nv, ns = len(tri), len(xyz), len(s)
+    out = (np.zeros((ns, M, nv), dtype=np.complex128), np.zeros((ns, nv, M), dtype=np.complex128),
+           np.zeros((ns, nv, nv), dtype=np.complex128))
+    I, J = np.meshgrid(np.arange(M), np.arange(M), indexing="ij")
+    I = I.ravel()
+    J = J.ravel()
+    for k0 in range(0, len(I), 65536):
+        sl = slice(k0, k0 + 65536)
+        _scatter(tri, nv, I[sl], J[sl], *p1_local(xyz, tri, I[sl], J[sl], s, qp), out)
+    return out
 
 
 def mass_p0p1(xyz, tri):
@@ -357,3 +380,90 @@ def solve_mixed_mot(xyz, tri, N: int, dt: float, bdf: int, dmask, gD, gN, R: flo
         q[n] = x[:nD]
         u[n] = x[nD:]
     return q, u, {"imag_rel": max(i1, i2, i3, i4), "ED": ED, "EN": EN, "VN": VN}
+
+
+# ---- H^2 form (Sec. 4, eqs. degexp, uniformlr) of the P1 operators --------
+# A far block b = r x c of triangle clusters carries, with the interpolation
+# G(x - y) ~ sum_{mu, nu} L_{r,mu}(x) S_b[mu, nu] L_{c,nu}(y) (S_b of
+# oracle.h2.coupling), the local values
+#   K1 (test t in r, trial slot (t', a) in c):  U_r S_b W1_c^T,
+#   Kp (test slot (t, a) in r, trial t' in c):  W1_r S_b U_c^T,
+#   D  (slots (t, a) in r, (t', b) in c):       sum_k C_{r,k} S_b C_{c,k}^T + s^2 sum_k N_{r,k} S_b N_{c,k}^T,
+# with the bases over the local vertex slots (t, a) of a cluster's triangles
+#   W1[(t, a), nu] = int_t (n_t . grad L_nu) lambda_a,   U1[(t, a), nu] = int_t L_nu lambda_a,
+#   C_k[(t, a), nu] = (curl lambda_a)_k int_t L_nu,      N_k[(t, a), nu] = n_{t,k} U1[(t, a), nu]
+# (Radon's rule on each triangle, as for the P0 bases).  Near blocks keep the
+# Galerkin values.
+
+def p1_cluster_bases(xyz, tri, tree, c: int, m: int):
+    """(W1, U1, C, N) of cluster c: W1, U1 (#c, 3, p); C, N (3, #c, 3, p) over
+    the components k; triangles in the order of tree.indices(c)."""
+    from .h2 import cheb_nodes, lagrange_1d, lagrange_3d
+    from .dlayer import lagrange_1d_deriv
+    P, area, _, _ = element_geometry(xyz, tri)
+    nrm = normals(xyz, tri)
+    cu = curls(xyz, tri)
+    idx = tree.indices(c)
+    nodes = cheb_nodes(tree.lo[c], tree.hi[c], m)
+    X = np.einsum("qa,pad->pqd", Q.RADON7_BARY, P[idx]).reshape(-1, 3)
+    p = m ** 3
+    Lv = lagrange_3d(nodes, X).reshape(len(idx), 7, p)
+    l = [lagrange_1d(nodes[a], X[:, a]) for a in range(3)]
+    dl = [lagrange_1d_deriv(nodes[a], X[:, a]) for a in range(3)]
+    g = [np.einsum("an,bn,cn->ncba", *(dl[k] if k == ax else l[k] for k in range(3))).reshape(len(X), p)
+         for ax in range(3)]
+    nrep = np.repeat(nrm[idx], 7, axis=0)
+    dn = (nrep[:, 0:1] * g[0] + nrep[:, 1:2] * g[1] + nrep[:, 2:3] * g[2]).reshape(len(idx), 7, p)
+    wb = Q.RADON7_W[:, None] * Q.RADON7_BARY                  # (7, 3): w_q lambda_a(q)
+    W1 = area[idx][:, None, None] * np.einsum("qa,tqn->tan", wb, dn)
+    U1 = area[idx][:, None, None] * np.einsum("qa,tqn->tan", wb, Lv)
+    U0 = area[idx][:, None] * np.einsum("q,tqn->tn", Q.RADON7_W, Lv)
+    C = np.einsum("tak,tn->ktan", cu[idx], U0)
+    N = np.einsum("tk,tan->ktan", nrm[idx], U1)
+    return W1, U1, C, N
+
+
+def h2_p1_matrices(xyz, tri, s, tree, near, far, m: int, qp: QuadParams = QuadParams()):
+    """H^2-expanded K1 (ns, M, nv), Kp (ns, nv, M), D (ns, nv, nv): near
+    blocks of triangle clusters with the Galerkin values, far blocks with the
+    interpolated kernel (module comment above)."""
+    from .h2 import cluster_basis, coupling
+    s = np.atleast_1d(np.asarray(s, dtype=np.complex128))
+    tri = np.asarray(tri)
+    M, nv, ns = len(tri), len(xyz), len(s)
+    out = (np.zeros((ns, M, nv), dtype=np.complex128), np.zeros((ns, nv, M), dtype=np.complex128),
+           np.zeros((ns, nv, nv), dtype=np.complex128))
+    if len(near):
+        I, J = [], []
+        for r, c in near:
+            a, b = np.meshgrid(tree.indices(r), tree.indices(c), indexing="ij")
+            I.append(a.ravel())
+            J.append(b.ravel())
+        I = np.concatenate(I)
+        J = np.concatenate(J)
+        for k0 in range(0, len(I), 65536):
+            sl = slice(k0, k0 + 65536)
+            _scatter(tri, nv, I[sl], J[sl], *p1_local(xyz, tri, I[sl], J[sl], s, qp), out)
+    cache = {}
+
+    def bases(c):
+        if c not in cache:
+            cache[c] = (cluster_basis(xyz, tri, tree, c, m),) + p1_cluster_bases(xyz, tri, tree, c, m)
+        return cache[c]
+
+    K1, Kp, D = out
+    for r, c in far:
+        S = coupling(tree, r, c, s, m)                                  # (ns, p, p)
+        Ur, W1r, _, Cr, Nr = bases(r)
+        Uc, W1c, _, Cc, Nc = bases(c)
+        ir, ic = tree.indices(r), tree.indices(c)
+        k1 = np.einsum("tm,lmn,uan->ltua", Ur, S, W1c)                 # test t, trial slot (u, a)
+        kp = np.einsum("tam,lmn,un->ltau", W1r, S, Uc)                 # test slot (t, a), trial u
+        dd = (np.einsum("ktam,lmn,kubn->ltaub", Cr, S, Cc)
+              + (s ** 2)[:, None, None, None, None] * np.einsum("ktam,lmn,kubn->ltaub", Nr, S, Nc))
+        for a in range(3):
+            np.add.at(K1, (slice(None), ir[:, None], tri[ic, a][None, :]), k1[:, :, :, a])
+            np.add.at(Kp, (slice(None), tri[ir, a][:, None], ic[None, :]), kp[:, :, a, :])
+            for b in range(3):
+                np.add.at(D, (slice(None), tri[ir, a][:, None], tri[ic, b][None, :]), dd[:, :, a, :, b])
+    return out

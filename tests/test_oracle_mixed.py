@@ -152,3 +152,31 @@ def test_marching_on_in_time_agrees_with_the_decoupled_solve():
     qm2, um2, _ = mixed.solve_mixed_mot(m.xyz, m.tri, N, dt, 2, dmask, uv2, qn2, mats_all=mats)
     assert np.array_equal(qm2[:10], qm[:10]) and np.array_equal(um2[:10], um[:10])
     assert _rel(qm2[10:], qm[10:]) > 0.1
+
+
+def test_h2_p1_operators_converge_with_m():
+    """The H^2 form of the P1 operators (Sec. 4: far blocks of triangle
+    clusters through the interpolated kernel, with the P1 double-layer, curl
+    and normal bases) converges to the Galerkin matrices as the number m of
+    Chebyshev points per axis grows; its hats still sum to one (the P1 double
+    layer on ones is the H^2 P0 double layer on ones), its far blocks keep
+    K' = K^T and the symmetry of D exactly."""
+    from oracle import cluster
+    m = synth.icosphere(2)
+    t = cluster.build_tree(m.xyz, m.tri, 16)
+    near, far = cluster.partition(t, 1.0)
+    assert len(far) > 0
+    s = np.array([1.5, 3.0 + 2.0j])
+    ref = mixed.p1_matrices(m.xyz, m.tri, s)
+    errs = []
+    for mm in (2, 3, 4):
+        h = mixed.h2_p1_matrices(m.xyz, m.tri, s, t, near, far, mm)
+        errs.append([_rel(a, b) for a, b in zip(h, ref)])
+    errs = np.array(errs)                        # (m, operator)
+    assert np.all(errs[1] < errs[0] / 3.0) and np.all(errs[2] < errs[1] / 3.0), errs
+    assert errs[2][0] < 1e-3 and errs[2][2] < 1e-5, errs
+    K1h, Kph, Dh = h
+    K0h = dlayer.h2_dl_matrices(m.xyz, m.tri, s, t, near, far, 4)
+    assert _rel(K1h @ np.ones(len(m.xyz)), K0h @ np.ones(len(m.tri))) < 1e-12
+    assert _rel(Kph, np.transpose(K1h, (0, 2, 1))) < 1e-5
+    assert _rel(Dh, np.transpose(Dh, (0, 2, 1))) < 1e-7
